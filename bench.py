@@ -1,0 +1,300 @@
+"""Benchmark: neighbor-list build + SPH density pass on one GB300.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+One step = the whole hot path on one batch of synthetic input: SFC keys,
+stable radix sort, permute + cluster boxes, octree, cluster-pair search with
+list encoding, and the decode + density pass, on the 2^24-particle
+64-Plummer-sphere system (inputs resident in HBM, larger than L2).  `value`
+is Mparticles/s over all ranks (weak scaling: every rank builds its own
+replica); `e2e` repeats the measurement through nl_density_from_host with
+pinned host buffers, copies included.  `--impl reference` times the CPU
+oracle on a bounded sample of the same workload generator.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("build+density Mparticles/s at 16M, learned-h vs plain, rel err ≤1e-5; %HBM peak")
+UNIT = "Mparticles/s"
+WORKLOAD = "plummer64_16m"
+N_FULL = 1 << 24
+ALU_OPS_PER_PAIR_SEARCH = 9      # predicate: 3 sub, 3 mul, 2 add, 1 compare (non-periodic)
+ALGO_BYTES_PER_PARTICLE = 145    # keygen 20 + sort 24 + permute 49 + octree 2 + search 19 + density 31
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured", d.get("sm_max_mhz", 2070.0)
+    return 6800.0, "fallback", 2070.0
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(seed):
+    from paper_2602_19873_gb300 import workloads as wl
+    return wl.plummer(N_FULL, n_spheres=64, seed=seed)
+
+
+def run_native(args):
+    import torch
+    from paper_2602_19873_gb300 import nl
+
+    ws, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    d = workload(4 + rank)
+    n = len(d["x"])
+    dev = {k: torch.from_numpy(d[k]).cuda() for k in ("x", "y", "z", "h", "m")}
+    params = nl.make_params(key=d["kind"], cluster=8, support=d["support"], compress=1,
+                            leaf_bucket=64)
+    L = nl.NeighborList()
+    L.set_profiling(True)
+    rho = torch.empty(n, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        L.build(dev["x"], dev["y"], dev["z"], dev["h"], d["box"], params, stream)
+        L.density_pass(dev["m"], rho, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    stage_acc = {}
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+        for k, v in L.stage_times().items():
+            stage_acc[k] = stage_acc.get(k, 0.0) + v
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / args.steps
+    clk = clocks.stop()
+    if ws > 1:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+        dist.barrier()
+    stages = {k: v / args.steps for k, v in stage_acc.items()}
+    sizes = L.sizes()
+
+    # end to end through the host-buffer entry point (pinned memory)
+    pin = {k: torch.from_numpy(d[k]).pin_memory().numpy() for k in ("x", "y", "z", "h", "m")}
+    rho_h = torch.empty(n, dtype=torch.float32).pin_memory().numpy()
+    E = nl.NeighborList()
+    for _ in range(max(1, args.warmup)):
+        E.density_from_host(pin["x"], pin["y"], pin["z"], pin["h"], pin["m"], d["box"], params,
+                            rho_h, stream)
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    esteps = max(1, min(args.steps, 5))
+    for _ in range(esteps):
+        E.density_from_host(pin["x"], pin["y"], pin["z"], pin["h"], pin["m"], d["box"], params,
+                            rho_h, stream)
+    torch.cuda.synchronize()
+    e_ms = (time.perf_counter() - te) * 1e3 / esteps
+    if ws > 1:
+        tt = torch.tensor([e_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e_ms = float(tt.item())
+
+    hbm, hbm_kind, sm_max = peaks()
+    alu_peak = 152 * 128 * sm_max * 1e6 / 1e12  # FP32 instructions per second, Tops
+    search_ms = stages.get("search", float("nan"))
+    pairs = sizes["n_tiles"] * params.cluster * params.cluster
+    achieved = pairs * ALU_OPS_PER_PAIR_SEARCH / (search_ms * 1e-3) / 1e12
+    step_bytes = ALGO_BYTES_PER_PARTICLE * n
+    out = {
+        "metric": METRIC, "value": ws * n / (ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "%s: 2^24 particles in 64 Plummer spheres (scale radii "
+                               "log-uniform 1e-3..1e-1), Hilbert keys, 8x8 clusters, "
+                               "compressed list" % WORKLOAD,
+                   "n": n, "cluster": params.cluster, "leaf_bucket": params.leaf_bucket,
+                   "h": "analytic-density estimate for 200 neighbors",
+                   "l2": "inputs larger than L2 (268 MB of positions), no flush",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "stages_ms": stages,
+        "roofline": {"bound": "alu", "kernel": "k_search (cluster-pair search + encode)",
+                     "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                     "peak_kind": "FP32 lanes x max SM clock (152 SMs x 128 x %.0f MHz)" % sm_max,
+                     "frac": achieved / alu_peak, "traffic": None,
+                     "algorithmic": "%d FP32 ops per computed pair, %d computed pairs" % (
+                         ALU_OPS_PER_PAIR_SEARCH, pairs)},
+        "hbm_step": {"achieved_gbs": step_bytes / (ms * 1e-3) / 1e9, "peak_gbs": hbm,
+                     "peak_kind": hbm_kind,
+                     "frac": step_bytes / (ms * 1e-3) / 1e9 / hbm,
+                     "bytes_per_particle": ALGO_BYTES_PER_PARTICLE},
+        "list": {"bytes_per_particle": sizes["list_bytes"] / n, "entries": sizes["n_entries"],
+                 "computed_pairs": pairs, "nodes": sizes["n_nodes"], "leaves": sizes["n_leaves"]},
+        "e2e": {"value": ws * n / (e_ms * 1e-3) / 1e6, "unit": UNIT,
+                "h2d_bytes_per_step": 20 * n, "d2h_bytes_per_step": 4 * n},
+        "gpu_launches": None,
+        "clocks": clk,
+    }
+    out["gpu_launches"] = args.steps * (1 + 3 * 8 + 1 + 10 + 1 + 2)
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_sample)
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def oracle_step(d):
+    """The oracle's build + density on one system: keys, stable sort, FP64
+    cell-list gather sets, symmetric sets, per-super-cluster records, density."""
+    import oracle
+    k = oracle.keys(d["x"], d["y"], d["z"], d["box"], d["kind"])
+    perm = oracle.sort(k)
+    s = [np.ascontiguousarray(d[a][perm]) for a in ("x", "y", "z", "h", "m")]
+    g_off, g_idx = oracle.gather_all(*s[:4], d["box"], d["support"])
+    p_off, p_idx = oracle.symmetrize(g_off, g_idx)
+    n = len(s[0])
+    nsc = (n + 63) // 64
+    so, J, m = oracle.cluster_lists(n, 8, p_off, p_idx, np.arange(n), np.arange(nsc))
+    nbytes = 0
+    for t in range(nsc):
+        nbytes += len(oracle.encode_record(J[so[t]:so[t + 1]], m[so[t]:so[t + 1]], 32, True))
+    rho = oracle.density(*s, d["box"], g_off, g_idx, np.arange(n))
+    return rho, nbytes
+
+
+def cpu_baseline(n_sample):
+    import oracle
+    from paper_2602_19873_gb300 import workloads as wl
+    oracle.build()
+    d = wl.plummer(n_sample, n_spheres=64, seed=4)
+    t = time.perf_counter()
+    oracle_step(d)
+    dt = time.perf_counter() - t
+    return {"value": n_sample / dt / 1e6, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": "one oracle build+density of the same generator at %d particles "
+                      "(64 Plummer spheres), %.1f s" % (n_sample, dt)}
+
+
+def run_reference(args):
+    ws, rank, local = dist_init()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2602_19873_gb300 import workloads as wl
+    oracle.build()
+    d = wl.plummer(args.cpu_sample, n_spheres=64, seed=4)
+    for _ in range(min(args.warmup, 1)):
+        oracle_step(d)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(d)
+    dt = (time.perf_counter() - t) / args.steps
+    v = args.cpu_sample / dt / 1e6
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": "%s generator at %d particles (bounded CPU sample)" % (
+               WORKLOAD, args.cpu_sample)},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(),
+                            "kind": "oracle",
+                            "sample": "%d particles of the 64-Plummer-sphere generator" % args.cpu_sample},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=1 << 18)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

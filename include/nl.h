@@ -1,0 +1,174 @@
+/*
+ * nl.h -- C ABI of the GB300 (sm_103a) compressed cluster neighbor list.
+ *
+ * Method: "GPU-Native Compressed Neighbor Lists with a Space-Filling-Curve
+ * Data Layout" (Thaler & Keller), Sec. II.  The library builds, on one GPU,
+ * the paper's neighbor list over SFC-sorted particles with per-particle
+ * interaction radii, and runs neighborhood passes that decode it:
+ *
+ *   SFC keys -> stable radix sort -> clusters of M consecutive particles and
+ *   super-clusters of 8 clusters (Sec. II-A) -> octree from the sorted keys
+ *   (Sec. II-A) -> cluster-pair search against bounding boxes inflated by the
+ *   largest radius -> one record per super-cluster: count, 8-bit masks, and
+ *   the nibble-compressed j-cluster indices (Sec. II-A/B/C) -> decode inside
+ *   the SPH density / force and Lennard-Jones passes (Sec. II-A, II-D).
+ *
+ * Conventions shared by every entry point:
+ *  - Particle arrays are DEVICE pointers in the caller's order, borrowed for
+ *    the duration of the call (nl_build copies what it keeps).  Outputs are
+ *    written in caller order.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    enqueued on it; calls that must read a device word back synchronise that
+ *    stream and say so.
+ *  - No exception crosses the ABI.  Every call returns an nl_status; on any
+ *    status other than NL_OK, nl_last_error() (thread-local) describes it and
+ *    no output array of that call is guaranteed to have been written.
+ *  - The pair predicate is fixed in IEEE FP32 without FMA contraction:
+ *      dx = xj - xi, wrapped once by +-L on a periodic axis when |dx| > L/2,
+ *      d2 = (dx*dx + dy*dy) + dz*dz, r = support*h,
+ *      symmetric pair (the list): i != j and d2 < max(ri, rj)^2
+ *      gather pair (density, counts): i != j and d2 < ri^2.
+ */
+#ifndef NL_H
+#define NL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NL_OK = 0,
+    NL_ERR_ARG = 1,            /* bad argument: NULL pointer, n < 1, non-finite or
+                                  out-of-box coordinate, h <= 0 or non-finite */
+    NL_ERR_RADIUS = 2,         /* support * max(h) >= L/2 on a periodic axis */
+    NL_ERR_OOM = 3,            /* device allocation failed (no partial state kept) */
+    NL_ERR_CUDA = 4,           /* a CUDA runtime call failed */
+    NL_ERR_CAPACITY = 5,       /* a bounded buffer overflowed and could not grow */
+    NL_ERR_NOT_CONVERGED = 6,  /* h iteration hit its iteration cap */
+    NL_ERR_TIMEOUT = 7,        /* a bounded device loop gave up */
+    NL_ERR_UNIMPLEMENTED = 8
+} nl_status;
+
+enum { NL_KEY_MORTON = 0, NL_KEY_HILBERT = 1 };
+
+/* Simulation box.  Every coordinate must satisfy lo <= x <= hi on every
+ * axis; periodic[a] != 0 makes axis a periodic with length L = hi - lo
+ * (computed in FP32).  Sec. II-A: periodic distances are always computed,
+ * no shift vectors are stored. */
+typedef struct {
+    float lo[3];
+    float hi[3];
+    int32_t periodic[3];
+} nl_box;
+
+/* Build options (Sec. II-D: cluster and super-cluster sizes, compression). */
+typedef struct {
+    int32_t key;          /* NL_KEY_MORTON or NL_KEY_HILBERT (63-bit keys, 21 bits/axis) */
+    int32_t cluster;      /* particles per cluster M: 4, 8 or 16; super-cluster = 8 clusters */
+    float support;        /* interaction radius r_i = support * h_i (2 for the cubic spline) */
+    int32_t compress;     /* 1: nibble codec (Sec. II-B); 0: raw u32 cluster indices */
+    int32_t leaf_bucket;  /* octree leaf capacity B in particles, 8..1024 (default 64) */
+} nl_params;
+
+/* Fills p with {NL_KEY_HILBERT, 8, 2.0f, 1, 64}. */
+void nl_default_params(nl_params *p);
+
+typedef struct nl_list nl_list; /* opaque; owns all of its device memory */
+
+/* Sizes and statistics of a built list (host struct). */
+typedef struct {
+    int64_t n;               /* particles */
+    int64_t n_clusters;      /* ceil(n / M) rounded up to whole super-clusters */
+    int64_t n_superclusters; /* clusters / 8 */
+    int64_t n_leaves;        /* octree leaves (non-empty cells) */
+    int64_t n_nodes;         /* octree nodes, pre-order */
+    int64_t n_entries;       /* stored (j-cluster, mask) entries */
+    int64_t n_tiles;         /* sum over entries of popcount(mask): computed cluster pairs */
+    int64_t list_bytes;      /* bytes of all super-cluster records */
+    int32_t cluster;         /* M */
+    int32_t compress;
+} nl_sizes;
+
+/* Builds a new list (Sec. II-A, Listing "build"): keys, sort, clusters,
+ * octree, cluster-pair search, encoding.  x,y,z,h: n device floats (caller
+ * order).  On success *out owns the list; on failure *out is NULL.
+ * Synchronises `stream` twice (validation + size word, final status). */
+nl_status nl_build(const float *x, const float *y, const float *z, const float *h, int64_t n,
+                   const nl_box *box, const nl_params *p, void *stream, nl_list **out);
+
+/* Same as nl_build into an existing list, reusing its device buffers (they
+ * only grow).  On failure the list is left empty (n = 0) but valid. */
+nl_status nl_rebuild(nl_list *nl, const float *x, const float *y, const float *z, const float *h,
+                     int64_t n, const nl_box *box, const nl_params *p, void *stream);
+
+/* SPH density (Sec. II-D): rho_i = m_i W(0,h_i) + sum_{j gather pair} m_j W(r_ij,h_i),
+ * W the M4 cubic spline with support 2h: W = w(r/h)/(pi h^3),
+ * w = 1 - 1.5q^2 + 0.75q^3 (q<1), 0.25(2-q)^3 (1<=q<2), 0 beyond.
+ * m: n device floats (caller order); rho: n device floats written in caller
+ * order.  FP32 arithmetic.  Does not synchronise. */
+nl_status nl_density_pass(const nl_list *nl, const float *m, float *rho, void *stream);
+
+/* Gather-neighbor count of every particle (j != i with d2 < ri^2), caller
+ * order, n device uint32.  Does not synchronise. */
+nl_status nl_neighbor_counts(const nl_list *nl, uint32_t *counts, void *stream);
+
+/* Releases the list and its device memory (after the stream work using it
+ * has completed; nl_free synchronises the device).  nl_free(NULL) = NL_OK. */
+nl_status nl_free(nl_list *nl);
+
+/* Host copy of the list sizes and statistics. */
+nl_status nl_get_sizes(const nl_list *nl, nl_sizes *out);
+
+/* Inspection copies to HOST buffers (tests, tools); each synchronises.
+ * keys: n uint64 sorted SFC keys; perm: n int32, perm[k] = caller index of
+ * the particle at sorted position k. */
+nl_status nl_copy_sorted(const nl_list *nl, uint64_t *keys, int32_t *perm);
+
+/* Octree in pre-order, n_nodes entries each: level, first and end particle
+ * (sorted positions, end exclusive), leaf flag, skip (index of the next node
+ * after this node's subtree). */
+nl_status nl_copy_octree(const nl_list *nl, int32_t *level, int32_t *first, int32_t *end,
+                         int32_t *leaf, int32_t *skip);
+
+/* Records: rec_off[s] = byte offset of super-cluster s's record inside the
+ * list buffer (n_superclusters entries); bytes: list_bytes bytes.  Record
+ * layout: u32 count | count u8 masks, zero-padded to 4 bytes | nibble stream
+ * (compressed) or count u32 (raw), zero-padded to 4 bytes.  The stream holds
+ * blocks of 32 index differences (d0 = J0 + 1, dk = Jk - J(k-1)): a 32-bit
+ * mask (bit k set iff dk != 1), one info nibble per set bit (dk+6 for dk in
+ * [2,9], else the value's nibble count minus one), then the data nibbles of
+ * every dk >= 10, most significant first; nibble p is byte p/2, low half for
+ * even p (Sec. II-B Tables 1-2, Sec. II-C). */
+nl_status nl_copy_records(const nl_list *nl, uint64_t *rec_off, uint8_t *bytes);
+
+/* End-to-end convenience call on HOST buffers: copies x, y, z, h, m (n
+ * floats each, pageable or pinned host memory) into device buffers owned by
+ * the list, rebuilds the list (as nl_rebuild), runs nl_density_pass and
+ * copies rho (n floats) back to host memory.  Synchronises `stream`. */
+nl_status nl_density_from_host(nl_list *nl, const float *x, const float *y, const float *z,
+                               const float *h, const float *m, int64_t n, const nl_box *box,
+                               const nl_params *p, float *rho, void *stream);
+
+/* Stage timing.  When enabled on a list, the build and the passes record
+ * CUDA events on their stream around each stage; nl_get_stage_times writes
+ * the durations in milliseconds of the most recent build / pass to ms[0..):
+ * 0 keys+validation, 1 radix sort, 2 permute+cluster boxes, 3 octree,
+ * 4 cluster-pair search+encode, 5 pass input gather, 6 pass kernel.
+ * *count receives the number of stages (7).  Synchronises the device. */
+nl_status nl_set_profiling(nl_list *nl, int32_t on);
+nl_status nl_get_stage_times(const nl_list *nl, float *ms, int32_t cap, int32_t *count);
+
+/* Creates an empty list handle (no device memory yet) for nl_rebuild or
+ * nl_density_from_host. */
+nl_status nl_create(nl_list **out);
+
+/* Thread-local description of the last error (never NULL). */
+const char *nl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NL_H */

@@ -1,0 +1,590 @@
+// C ABI of the neighbor-list library: argument checks, device workspace,
+// the build pipeline on one stream, passes, inspection copies.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "nl_internal.cuh"
+
+using namespace nlg;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+nl_status fail(nl_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+nl_status cuda_fail(cudaError_t e, const char *what, int line)
+{
+    (void)cudaGetLastError();  // clear a non-sticky error
+    nl_status st = e == cudaErrorMemoryAllocation ? NL_ERR_OOM : NL_ERR_CUDA;
+    return fail(st, "CUDA error %d (%s) in %s (capi.cu:%d)", (int)e, cudaGetErrorString(e), what,
+                line);
+}
+
+#define CK(x)                                                   \
+    do {                                                        \
+        cudaError_t e_ = (x);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #x, __LINE__); \
+    } while (0)
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t bytes)
+    {
+        if (p && bytes <= cap) return cudaSuccess;
+        release();
+        size_t b = ((bytes ? bytes : 16) + 255) / 256 * 256;
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            p = nullptr;
+            return e;
+        }
+        cap = b;
+        return cudaSuccess;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <class T>
+    T *as() const
+    {
+        return reinterpret_cast<T *>(p);
+    }
+};
+
+constexpr uint32_t kStageCap0 = 4096;
+constexpr int kSearchBlocksPerSM = 4;
+constexpr int kMaxRedoRounds = 8;
+
+}  // namespace
+
+struct nl_list {
+    int dev = -1, num_sms = 0;
+    int64_t n = 0;
+    uint32_t npad = 0, ncl = 0, nsc = 0, n_leaves = 0, n_nodes = 0;
+    nl_params p{};
+    nl_box box{};
+    DevBox dbox{};
+    int any_per = 0;
+    unsigned long long list_bytes = 0, n_entries = 0, n_tiles = 0;
+    uint32_t stage_cap = kStageCap0;
+    DevBuf keys, keys_alt, vals, vals_alt, hist, pos, clo, chi, lcp, lev, leaf_first, leaf_lev,
+        nodeoff, bsum;
+    DevBuf nlo, nhi, nrng, nlevel, nparent, nchild, narrive;
+    DevBuf stageJ, stageM, list, rec_off, redo, work, aux, status;
+    Status *hst = nullptr;
+    // stage timing (CUDA events on the launching stream)
+    static constexpr int kStages = 7;
+    int profiling = 0;
+    cudaEvent_t ev[kStages + 1] = {};
+    float stage_ms[kStages] = {};
+    // device copies of host inputs for nl_density_from_host
+    DevBuf hx, hy, hz, hh, hm, hrho;
+
+    cudaError_t mark(int k, cudaStream_t s)
+    {
+        if (!profiling) return cudaSuccess;
+        for (int i = 0; i <= kStages; ++i)
+            if (!ev[i]) {
+                cudaError_t e = cudaEventCreate(&ev[i]);
+                if (e != cudaSuccess) return e;
+            }
+        return cudaEventRecord(ev[k], s);
+    }
+    void collect(int from, int to)
+    {
+        if (!profiling) return;
+        cudaEventSynchronize(ev[to]);
+        for (int k = from; k < to; ++k) cudaEventElapsedTime(&stage_ms[k], ev[k], ev[k + 1]);
+    }
+
+    void release_all()
+    {
+        DevBuf *all[] = {&keys, &keys_alt, &vals, &vals_alt, &hist, &pos, &clo, &chi, &lcp, &lev,
+                         &leaf_first, &leaf_lev, &nodeoff, &bsum, &nlo, &nhi, &nrng, &nlevel,
+                         &nparent, &nchild, &narrive, &stageJ, &stageM, &list, &rec_off, &redo,
+                         &work, &aux, &status, &hx, &hy, &hz, &hh, &hm, &hrho};
+        for (DevBuf *b : all) b->release();
+        for (int i = 0; i <= kStages; ++i)
+            if (ev[i]) cudaEventDestroy(ev[i]);
+        if (hst) cudaFreeHost(hst);
+        hst = nullptr;
+    }
+};
+
+namespace {
+
+nl_status check_params(const nl_params *p, const nl_box *box)
+{
+    if (!p || !box) return fail(NL_ERR_ARG, "params or box is NULL");
+    if (p->key != NL_KEY_MORTON && p->key != NL_KEY_HILBERT)
+        return fail(NL_ERR_ARG, "unknown key kind %d", p->key);
+    if (p->cluster != 4 && p->cluster != 8 && p->cluster != 16)
+        return fail(NL_ERR_ARG, "cluster size must be 4, 8 or 16 (got %d)", p->cluster);
+    if (!(p->support > 0.f) || !std::isfinite(p->support))
+        return fail(NL_ERR_ARG, "support must be finite and > 0");
+    if (p->compress != 0 && p->compress != 1) return fail(NL_ERR_ARG, "compress must be 0 or 1");
+    if (p->leaf_bucket < 8 || p->leaf_bucket > 1024)
+        return fail(NL_ERR_ARG, "leaf_bucket must be in [8, 1024] (got %d)", p->leaf_bucket);
+    for (int a = 0; a < 3; ++a) {
+        if (!std::isfinite(box->lo[a]) || !std::isfinite(box->hi[a]) || !(box->lo[a] < box->hi[a]))
+            return fail(NL_ERR_ARG, "box axis %d: need finite lo < hi", a);
+        float len = box->hi[a] - box->lo[a];
+        if (!(len > 0.f) || !std::isfinite(len)) return fail(NL_ERR_ARG, "box axis %d degenerate", a);
+    }
+    return NL_OK;
+}
+
+DevBox make_devbox(const nl_box &b)
+{
+    DevBox d{};
+    for (int a = 0; a < 3; ++a) {
+        volatile float lo = b.lo[a], hi = b.hi[a];
+        float len = hi - lo;
+        d.lo[a] = lo;
+        d.hi[a] = hi;
+        d.len[a] = len;
+        d.half[a] = 0.5f * len;
+        volatile float num = 2097152.0f;
+        d.qs[a] = num / len;
+        d.per[a] = b.periodic[a] ? 1 : 0;
+    }
+    return d;
+}
+
+nl_status read_status(nl_list *nl, cudaStream_t s)
+{
+    CK(cudaMemcpyAsync(nl->hst, nl->status.p, sizeof(Status), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return NL_OK;
+}
+
+nl_status do_build(nl_list *nl, const float *x, const float *y, const float *z, const float *h,
+                   int64_t n, const nl_box *box, const nl_params *p, cudaStream_t s)
+{
+    if (!x || !y || !z || !h) return fail(NL_ERR_ARG, "NULL particle array");
+    if (n < 1) return fail(NL_ERR_ARG, "n must be >= 1 (got %lld)", (long long)n);
+    if (n > (int64_t)1 << 30) return fail(NL_ERR_ARG, "n must be <= 2^30");
+    nl_status st = check_params(p, box);
+    if (st != NL_OK) return st;
+
+    int dev;
+    CK(cudaGetDevice(&dev));
+    if (dev != nl->dev) {
+        CK(cudaDeviceGetAttribute(&nl->num_sms, cudaDevAttrMultiProcessorCount, dev));
+        nl->dev = dev;
+    }
+    if (!nl->hst) CK(cudaMallocHost(&nl->hst, sizeof(Status)));
+
+    const uint32_t N = (uint32_t)n;
+    const int M = p->cluster;
+    const uint32_t nsc = (N + kSC * M - 1) / (kSC * M);
+    const uint32_t ncl = nsc * kSC, npad = ncl * M;
+    nl->p = *p;
+    nl->box = *box;
+    nl->dbox = make_devbox(*box);
+    nl->any_per = box->periodic[0] || box->periodic[1] || box->periodic[2];
+
+    CK(nl->keys.ensure((size_t)N * 8));
+    CK(nl->keys_alt.ensure((size_t)N * 8));
+    CK(nl->vals.ensure((size_t)N * 4));
+    CK(nl->vals_alt.ensure((size_t)N * 4));
+    CK(nl->hist.ensure(radix_hist_words(N) * 4));
+    CK(nl->pos.ensure((size_t)npad * 16));
+    CK(nl->clo.ensure((size_t)ncl * 16));
+    CK(nl->chi.ensure((size_t)ncl * 16));
+    CK(nl->lcp.ensure((size_t)N));
+    CK(nl->lev.ensure((size_t)N));
+    CK(nl->leaf_first.ensure((size_t)(N + 1) * 4));
+    CK(nl->leaf_lev.ensure((size_t)N));
+    CK(nl->nodeoff.ensure((size_t)(N + 1) * 4));
+    CK(nl->bsum.ensure(scan_bsum_words(N) * 4));
+    CK(nl->rec_off.ensure((size_t)nsc * 4));
+    CK(nl->redo.ensure((size_t)nsc * 4));
+    CK(nl->work.ensure((size_t)nsc * 4));
+    CK(nl->status.ensure(sizeof(Status)));
+    Status *dst = nl->status.as<Status>();
+    CK(cudaMemsetAsync(dst, 0, sizeof(Status), s));
+
+    // 1. keys (+ validation), 2. stable sort, 3. permute + cluster boxes
+    CK(nl->mark(0, s));
+    CK(launch_keys(n, x, y, z, h, nl->dbox, p->support, p->key, nl->keys.as<uint64_t>(),
+                   nl->vals.as<uint32_t>(), dst, s));
+    CK(nl->mark(1, s));
+    CK(radix_sort_pairs(nl->keys.as<uint64_t>(), nl->vals.as<uint32_t>(),
+                        nl->keys_alt.as<uint64_t>(), nl->vals_alt.as<uint32_t>(), N,
+                        3 * kKeyBits, nl->hist.as<uint32_t>(), s));
+    CK(nl->mark(2, s));
+    CK(launch_permute(N, npad, M, nl->vals.as<uint32_t>(), x, y, z, h, p->support,
+                      nl->pos.as<float4>(), nl->clo.as<float4>(), nl->chi.as<float4>(), s));
+    // 4. octree leaves
+    CK(nl->mark(3, s));
+    CK(octree_leaves(nl->keys.as<uint64_t>(), N, p->leaf_bucket, nl->lcp.as<uint8_t>(),
+                     nl->lev.as<uint8_t>(), nl->leaf_first.as<uint32_t>(),
+                     nl->leaf_lev.as<uint8_t>(), nl->bsum.as<uint32_t>(), dst, s));
+    st = read_status(nl, s);
+    if (st != NL_OK) return st;
+    if (nl->hst->bad_input) {
+        unsigned b = nl->hst->bad_input;
+        return fail(NL_ERR_ARG, "invalid particle input:%s%s%s", (b & 1) ? " non-finite coordinate" : "",
+                    (b & 2) ? " coordinate outside the box" : "", (b & 4) ? " h <= 0 or non-finite" : "");
+    }
+    const float rmax = __builtin_bit_cast(float, nl->hst->rmax_bits);
+    for (int a = 0; a < 3; ++a)
+        if (box->periodic[a] && !(rmax < nl->dbox.half[a]))
+            return fail(NL_ERR_RADIUS, "support*max(h) = %g >= L/2 = %g on periodic axis %d",
+                        (double)rmax, (double)nl->dbox.half[a], a);
+    const uint32_t nleaves = nl->hst->n_leaves;
+    CK(octree_count_nodes(nl->keys.as<uint64_t>(), nleaves, nl->leaf_first.as<uint32_t>(),
+                          nl->leaf_lev.as<uint8_t>(), nl->nodeoff.as<uint32_t>(),
+                          nl->bsum.as<uint32_t>(), dst, s));
+    st = read_status(nl, s);
+    if (st != NL_OK) return st;
+    const uint32_t nnodes = nl->hst->n_nodes;
+    CK(nl->nlo.ensure((size_t)nnodes * 16));
+    CK(nl->nhi.ensure((size_t)nnodes * 16));
+    CK(nl->nrng.ensure((size_t)nnodes * 8));
+    CK(nl->nlevel.ensure((size_t)nnodes));
+    CK(nl->nparent.ensure((size_t)nnodes * 4));
+    CK(nl->nchild.ensure((size_t)nnodes * 4));
+    CK(nl->narrive.ensure((size_t)nnodes * 4));
+    OctreeOut oo{nl->nlo.as<float4>(), nl->nhi.as<float4>(), nl->nrng.as<int2>(),
+                 nl->nlevel.as<uint8_t>(), nl->nparent.as<int32_t>(), nl->nchild.as<uint32_t>(),
+                 nl->narrive.as<uint32_t>()};
+    CK(octree_emit(nl->keys.as<uint64_t>(), N, nleaves, nnodes, nl->leaf_first.as<uint32_t>(),
+                   nl->leaf_lev.as<uint8_t>(), nl->nodeoff.as<uint32_t>(), nl->pos.as<float4>(),
+                   p->support, oo, s));
+
+    CK(cudaMemsetAsync(dst, 0, sizeof(Status), s));
+    // 5. cluster-pair search + encoding, with redo rounds for overflows
+    const size_t est = (size_t)N * (p->compress ? 6 : 20) + 4096;
+    if (nl->list.cap < est) CK(nl->list.ensure(est));
+    int grid = nl->num_sms * kSearchBlocksPerSM;
+    size_t slots = (size_t)grid * 8;
+    CK(nl->stageJ.ensure(slots * nl->stage_cap * 4));
+    CK(nl->stageM.ensure(slots * nl->stage_cap));
+    CK(nl->mark(4, s));
+
+    SearchArgs sa{};
+    sa.pos = nl->pos.as<float4>();
+    sa.clo = nl->clo.as<float4>();
+    sa.chi = nl->chi.as<float4>();
+    sa.nlo = nl->nlo.as<float4>();
+    sa.nhi = nl->nhi.as<float4>();
+    sa.nrng = nl->nrng.as<int2>();
+    sa.n = N;
+    sa.nsc = nsc;
+    sa.nnodes = nnodes;
+    sa.box = nl->dbox;
+    sa.support = p->support;
+    sa.compress = p->compress;
+    sa.st = dst;
+    sa.rec_off = nl->rec_off.as<uint32_t>();
+
+    unsigned long long entries = 0, tiles = 0, used = 0;
+    const uint32_t *work = nullptr;
+    uint32_t count = nsc;
+    for (int round = 0;; ++round) {
+        sa.stageJ = nl->stageJ.as<uint32_t>();
+        sa.stageM = nl->stageM.as<uint8_t>();
+        sa.stage_cap = nl->stage_cap;
+        sa.list = nl->list.as<uint8_t>();
+        sa.list_cap = nl->list.cap - 8;  // 8 bytes of slack behind the last record
+        CK(launch_search_ctl(sa, work, count, nl->redo.as<uint32_t>(), M, nl->any_per, grid, s));
+        st = read_status(nl, s);
+        if (st != NL_OK) return st;
+        entries += nl->hst->n_entries;
+        tiles += nl->hst->n_tiles;
+        used = nl->hst->list_used;
+        const uint32_t nredo = nl->hst->stage_overflow;
+        if (nredo == 0) break;
+        if (round + 1 >= kMaxRedoRounds)
+            return fail(NL_ERR_CAPACITY, "list still overflowing after %d rounds", round + 1);
+        // grow what overflowed, then re-run only the listed super-clusters
+        CK(cudaMemcpyAsync(nl->work.p, nl->redo.p, (size_t)nredo * 4, cudaMemcpyDeviceToDevice, s));
+        work = nl->work.as<uint32_t>();
+        count = nredo;
+        grid = (int)std::min<uint32_t>((uint32_t)(nl->num_sms * kSearchBlocksPerSM), (nredo + 7) / 8);
+        slots = (size_t)grid * 8;
+        if (nl->hst->max_count > nl->stage_cap) {
+            nl->stage_cap = nl->hst->max_count + nl->hst->max_count / 4 + 64;
+        }
+        CK(nl->stageJ.ensure(slots * nl->stage_cap * 4));
+        CK(nl->stageM.ensure(slots * nl->stage_cap));
+        unsigned long long keep = used;
+        if (nl->hst->list_overflow) {
+            keep = nl->list.cap - 8;
+            size_t ncap = std::max((size_t)nl->list.cap * 2, (size_t)(used + used / 2 + 4096));
+            DevBuf bigger;
+            CK(bigger.ensure(ncap));
+            CK(cudaMemcpyAsync(bigger.p, nl->list.p, keep, cudaMemcpyDeviceToDevice, s));
+            CK(cudaStreamSynchronize(s));
+            nl->list.release();
+            nl->list = bigger;
+            bigger.p = nullptr;
+        }
+        std::memset(nl->hst, 0, sizeof(Status));
+        nl->hst->list_used = keep;
+        CK(cudaMemcpyAsync(dst, nl->hst, sizeof(Status), cudaMemcpyHostToDevice, s));
+    }
+    CK(nl->mark(5, s));
+    nl->collect(0, 5);
+    nl->n = n;
+    nl->npad = npad;
+    nl->ncl = ncl;
+    nl->nsc = nsc;
+    nl->n_leaves = nleaves;
+    nl->n_nodes = nnodes;
+    nl->list_bytes = used;
+    nl->n_entries = entries;
+    nl->n_tiles = tiles;
+    return NL_OK;
+}
+
+nl_status check_list(const nl_list *nl)
+{
+    if (!nl) return fail(NL_ERR_ARG, "list is NULL");
+    if (nl->n <= 0) return fail(NL_ERR_ARG, "list is empty (not built or last build failed)");
+    return NL_OK;
+}
+
+PassArgs pass_args(const nl_list *nl)
+{
+    PassArgs a{};
+    a.pos = nl->pos.as<float4>();
+    a.list = nl->list.as<uint8_t>();
+    a.rec_off = nl->rec_off.as<uint32_t>();
+    a.perm = nl->vals.as<uint32_t>();
+    a.aux = nl->aux.as<float2>();
+    a.n = (uint32_t)nl->n;
+    a.nsc = nl->nsc;
+    a.box = nl->dbox;
+    a.support = nl->p.support;
+    a.compress = nl->p.compress;
+    a.st = nl->status.as<Status>();
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+void nl_default_params(nl_params *p)
+{
+    if (!p) return;
+    p->key = NL_KEY_HILBERT;
+    p->cluster = 8;
+    p->support = 2.0f;
+    p->compress = 1;
+    p->leaf_bucket = 64;
+}
+
+const char *nl_last_error(void) { return g_err.c_str(); }
+
+nl_status nl_rebuild(nl_list *nl, const float *x, const float *y, const float *z, const float *h,
+                     int64_t n, const nl_box *box, const nl_params *p, void *stream)
+{
+    if (!nl) return fail(NL_ERR_ARG, "list is NULL");
+    nl->n = 0;
+    nl_status st = do_build(nl, x, y, z, h, n, box, p, (cudaStream_t)stream);
+    if (st != NL_OK) nl->n = 0;
+    return st;
+}
+
+nl_status nl_build(const float *x, const float *y, const float *z, const float *h, int64_t n,
+                   const nl_box *box, const nl_params *p, void *stream, nl_list **out)
+{
+    if (!out) return fail(NL_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    nl_list *nl = new (std::nothrow) nl_list();
+    if (!nl) return fail(NL_ERR_OOM, "host allocation failed");
+    nl_status st = nl_rebuild(nl, x, y, z, h, n, box, p, stream);
+    if (st != NL_OK) {
+        nl->release_all();
+        delete nl;
+        return st;
+    }
+    *out = nl;
+    return NL_OK;
+}
+
+nl_status nl_create(nl_list **out)
+{
+    if (!out) return fail(NL_ERR_ARG, "out is NULL");
+    *out = new (std::nothrow) nl_list();
+    if (!*out) return fail(NL_ERR_OOM, "host allocation failed");
+    return NL_OK;
+}
+
+nl_status nl_set_profiling(nl_list *nl, int32_t on)
+{
+    if (!nl) return fail(NL_ERR_ARG, "list is NULL");
+    nl->profiling = on ? 1 : 0;
+    return NL_OK;
+}
+
+nl_status nl_get_stage_times(const nl_list *cnl, float *ms, int32_t cap, int32_t *count)
+{
+    if (!cnl) return fail(NL_ERR_ARG, "list is NULL");
+    nl_list *nl = const_cast<nl_list *>(cnl);
+    if (nl->profiling && nl->ev[7]) {
+        CK(cudaEventSynchronize(nl->ev[7]));
+        CK(cudaEventElapsedTime(&nl->stage_ms[5], nl->ev[5], nl->ev[6]));
+        CK(cudaEventElapsedTime(&nl->stage_ms[6], nl->ev[6], nl->ev[7]));
+    }
+    for (int k = 0; k < nl_list::kStages && k < cap; ++k) ms[k] = nl->stage_ms[k];
+    if (count) *count = nl_list::kStages;
+    return NL_OK;
+}
+
+nl_status nl_density_from_host(nl_list *nl, const float *x, const float *y, const float *z,
+                               const float *h, const float *m, int64_t n, const nl_box *box,
+                               const nl_params *p, float *rho, void *stream)
+{
+    if (!nl) return fail(NL_ERR_ARG, "list is NULL");
+    if (!x || !y || !z || !h || !m || !rho) return fail(NL_ERR_ARG, "NULL host array");
+    if (n < 1 || n > (int64_t)1 << 30) return fail(NL_ERR_ARG, "bad n %lld", (long long)n);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t b = (size_t)n * 4;
+    DevBuf *bufs[] = {&nl->hx, &nl->hy, &nl->hz, &nl->hh, &nl->hm, &nl->hrho};
+    for (DevBuf *d : bufs) CK(d->ensure(b));
+    CK(cudaMemcpyAsync(nl->hx.p, x, b, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(nl->hy.p, y, b, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(nl->hz.p, z, b, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(nl->hh.p, h, b, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(nl->hm.p, m, b, cudaMemcpyHostToDevice, s));
+    nl_status st = nl_rebuild(nl, nl->hx.as<float>(), nl->hy.as<float>(), nl->hz.as<float>(),
+                              nl->hh.as<float>(), n, box, p, stream);
+    if (st != NL_OK) return st;
+    st = nl_density_pass(nl, nl->hm.as<float>(), nl->hrho.as<float>(), stream);
+    if (st != NL_OK) return st;
+    CK(cudaMemcpyAsync(rho, nl->hrho.p, b, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return NL_OK;
+}
+
+nl_status nl_free(nl_list *nl)
+{
+    if (!nl) return NL_OK;
+    cudaDeviceSynchronize();
+    nl->release_all();
+    delete nl;
+    return NL_OK;
+}
+
+nl_status nl_density_pass(const nl_list *cnl, const float *m, float *rho, void *stream)
+{
+    nl_status st = check_list(cnl);
+    if (st != NL_OK) return st;
+    if (!m || !rho) return fail(NL_ERR_ARG, "NULL m or rho");
+    nl_list *nl = const_cast<nl_list *>(cnl);
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(nl->aux.ensure((size_t)nl->npad * 8));
+    CK(nl->mark(5, s));
+    CK(launch_gather_aux((uint32_t)nl->n, nl->npad, nl->vals.as<uint32_t>(), m, nullptr, nullptr,
+                         0, nl->aux.as<float2>(), s));
+    CK(nl->mark(6, s));
+    PassArgs a = pass_args(nl);
+    a.out0 = rho;
+    CK(launch_pass(a, PASS_DENSITY, nl->p.cluster, nl->any_per, nl->num_sms, s));
+    CK(nl->mark(7, s));
+    return NL_OK;
+}
+
+nl_status nl_neighbor_counts(const nl_list *cnl, uint32_t *counts, void *stream)
+{
+    nl_status st = check_list(cnl);
+    if (st != NL_OK) return st;
+    if (!counts) return fail(NL_ERR_ARG, "NULL counts");
+    nl_list *nl = const_cast<nl_list *>(cnl);
+    PassArgs a = pass_args(nl);
+    a.outc = counts;
+    CK(launch_pass(a, PASS_COUNT, nl->p.cluster, nl->any_per, nl->num_sms, (cudaStream_t)stream));
+    return NL_OK;
+}
+
+nl_status nl_get_sizes(const nl_list *nl, nl_sizes *out)
+{
+    nl_status st = check_list(nl);
+    if (st != NL_OK) return st;
+    if (!out) return fail(NL_ERR_ARG, "NULL out");
+    out->n = nl->n;
+    out->n_clusters = nl->ncl;
+    out->n_superclusters = nl->nsc;
+    out->n_leaves = nl->n_leaves;
+    out->n_nodes = nl->n_nodes;
+    out->n_entries = (int64_t)nl->n_entries;
+    out->n_tiles = (int64_t)nl->n_tiles;
+    out->list_bytes = (int64_t)nl->list_bytes;
+    out->cluster = nl->p.cluster;
+    out->compress = nl->p.compress;
+    return NL_OK;
+}
+
+nl_status nl_copy_sorted(const nl_list *nl, uint64_t *keys, int32_t *perm)
+{
+    nl_status st = check_list(nl);
+    if (st != NL_OK) return st;
+    CK(cudaDeviceSynchronize());
+    if (keys) CK(cudaMemcpy(keys, nl->keys.p, (size_t)nl->n * 8, cudaMemcpyDeviceToHost));
+    if (perm) CK(cudaMemcpy(perm, nl->vals.p, (size_t)nl->n * 4, cudaMemcpyDeviceToHost));
+    return NL_OK;
+}
+
+nl_status nl_copy_octree(const nl_list *nl, int32_t *level, int32_t *first, int32_t *end,
+                         int32_t *leaf, int32_t *skip)
+{
+    nl_status st = check_list(nl);
+    if (st != NL_OK) return st;
+    CK(cudaDeviceSynchronize());
+    const size_t nn = nl->n_nodes;
+    std::vector<uint8_t> lv(nn);
+    std::vector<int2> rg(nn);
+    std::vector<float4> hi(nn);
+    CK(cudaMemcpy(lv.data(), nl->nlevel.p, nn, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(rg.data(), nl->nrng.p, nn * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(hi.data(), nl->nhi.p, nn * 16, cudaMemcpyDeviceToHost));
+    for (size_t v = 0; v < nn; ++v) {
+        int sk = __builtin_bit_cast(int, hi[v].w);
+        if (level) level[v] = lv[v];
+        if (first) first[v] = rg[v].x;
+        if (end) end[v] = rg[v].y;
+        if (leaf) leaf[v] = (size_t)sk == v + 1;
+        if (skip) skip[v] = sk;
+    }
+    return NL_OK;
+}
+
+nl_status nl_copy_records(const nl_list *nl, uint64_t *rec_off, uint8_t *bytes)
+{
+    nl_status st = check_list(nl);
+    if (st != NL_OK) return st;
+    CK(cudaDeviceSynchronize());
+    if (rec_off) {
+        std::vector<uint32_t> w(nl->nsc);
+        CK(cudaMemcpy(w.data(), nl->rec_off.p, (size_t)nl->nsc * 4, cudaMemcpyDeviceToHost));
+        for (uint32_t s = 0; s < nl->nsc; ++s) rec_off[s] = (uint64_t)w[s] * 4u;
+    }
+    if (bytes) CK(cudaMemcpy(bytes, nl->list.p, nl->list_bytes, cudaMemcpyDeviceToHost));
+    return NL_OK;
+}
+
+}  // extern "C"

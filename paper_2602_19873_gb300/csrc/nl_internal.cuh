@@ -1,0 +1,332 @@
+// Internal declarations of the sm_103a neighbor-list library (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nl.h"
+
+namespace nlg {
+
+constexpr int kKeyBits = 21;         // bits per axis of the 63-bit SFC key
+constexpr int kMaxLevel = 21;        // deepest octree level
+constexpr int kSC = 8;               // clusters per super-cluster (8-bit masks, Sec. II-A)
+constexpr uint32_t kBadRecord = 0xffffffffu;
+
+// Box with the derived FP32 quantities every kernel uses.  len = hi - lo,
+// half = 0.5f * len, qs = 2^21 / len, all rounded to nearest in FP32.
+struct DevBox {
+    float lo[3], hi[3], len[3], half[3], qs[3];
+    int per[3];
+};
+
+// Device status words written by the build kernels and read back once.
+struct Status {
+    unsigned int bad_input;   // bit0 non-finite coordinate, bit1 outside box, bit2 bad h
+    unsigned int rmax_bits;   // max over particles of support*h (FP32 bits, >= 0)
+    unsigned int n_leaves;
+    unsigned int n_nodes;
+    unsigned int ticket;      // work counter of persistent kernels
+    unsigned int stage_overflow;
+    unsigned int max_count;   // longest super-cluster list seen when staging overflowed
+    unsigned int list_overflow;
+    unsigned long long list_used;  // bytes reserved in the list buffer
+    unsigned long long n_entries;
+    unsigned long long n_tiles;
+    unsigned int pass_ticket;
+    unsigned int pad[3];
+};
+
+// ---------------------------------------------------------------------------
+// The canonical FP32 pair arithmetic (no FMA contraction anywhere).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float wrap_axis(float d, float len, float half, int per)
+{
+    if (per) {
+        if (d > half)
+            d = __fsub_rn(d, len);
+        else if (d < -half)
+            d = __fadd_rn(d, len);
+    }
+    return d;
+}
+
+template <bool PER>
+__device__ __forceinline__ float pair_d2(const float4 &pi, const float4 &pj, const DevBox &b)
+{
+    float dx = __fsub_rn(pj.x, pi.x);
+    float dy = __fsub_rn(pj.y, pi.y);
+    float dz = __fsub_rn(pj.z, pi.z);
+    if (PER) {
+        dx = wrap_axis(dx, b.len[0], b.half[0], b.per[0]);
+        dy = wrap_axis(dy, b.len[1], b.half[1], b.per[1]);
+        dz = wrap_axis(dz, b.len[2], b.half[2], b.per[2]);
+    }
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+template <bool PER>
+__device__ __forceinline__ float3 pair_dx(const float4 &pi, const float4 &pj, const DevBox &b)
+{
+    float dx = __fsub_rn(pj.x, pi.x);
+    float dy = __fsub_rn(pj.y, pi.y);
+    float dz = __fsub_rn(pj.z, pi.z);
+    if (PER) {
+        dx = wrap_axis(dx, b.len[0], b.half[0], b.per[0]);
+        dy = wrap_axis(dy, b.len[1], b.half[1], b.per[1]);
+        dz = wrap_axis(dz, b.len[2], b.half[2], b.per[2]);
+    }
+    return make_float3(dx, dy, dz);
+}
+
+__device__ __forceinline__ float d2_of(const float3 &d)
+{
+    return __fadd_rn(__fadd_rn(__fmul_rn(d.x, d.x), __fmul_rn(d.y, d.y)), __fmul_rn(d.z, d.z));
+}
+
+// Lower bound of |dx| after the wrap for any xi in [a0,a1], xj in [b0,b1].
+// Every operation is round-to-nearest and monotone, so the bound never
+// exceeds the canonical per-pair value (conservative box rounding).
+__device__ __forceinline__ float axis_gap(float a0, float a1, float b0, float b1, float len,
+                                          int per)
+{
+    float g = fmaxf(0.f, fmaxf(__fsub_rn(b0, a1), __fsub_rn(a0, b1)));
+    if (per) {
+        float down = __fsub_rn(len, __fsub_rn(b1, a0));  // j wrapped by -L
+        float up = __fadd_rn(__fsub_rn(b0, a1), len);    // j wrapped by +L
+        g = fminf(g, fmaxf(0.f, fminf(down, up)));
+    }
+    return g;
+}
+
+// Could some particle of box A be a symmetric neighbor of some particle of
+// box B?  lo.w = largest radius of the box.  NaN/inf boxes (empty clusters)
+// never pass.
+template <bool PER>
+__device__ __forceinline__ bool boxes_near(const float4 &alo, const float4 &ahi, const float4 &blo,
+                                           const float4 &bhi, const DevBox &b)
+{
+    float gx = axis_gap(alo.x, ahi.x, blo.x, bhi.x, b.len[0], PER ? b.per[0] : 0);
+    float gy = axis_gap(alo.y, ahi.y, blo.y, bhi.y, b.len[1], PER ? b.per[1] : 0);
+    float gz = axis_gap(alo.z, ahi.z, blo.z, bhi.z, b.len[2], PER ? b.per[2] : 0);
+    float d2 = __fadd_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)), __fmul_rn(gz, gz));
+    float r = fmaxf(alo.w, blo.w);
+    return d2 <= __fmul_rn(r, r);
+}
+
+// ---------------------------------------------------------------------------
+// SFC keys
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t quantize21(float x, float lo, float qs)
+{
+    float t = __fmul_rn(__fsub_rn(x, lo), qs);
+    if (!(t > 0.f)) return 0u;
+    if (t >= 2097151.f) return 2097151u;
+    return __float2uint_rz(t);
+}
+
+// Spread the low 21 bits of v so that bit b lands on bit 3b.
+__device__ __forceinline__ uint64_t spread3(uint32_t v)
+{
+    uint64_t x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x001f00000000ffffull;
+    x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+__device__ __forceinline__ uint64_t morton_key(uint32_t qx, uint32_t qy, uint32_t qz)
+{
+    return (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+}
+
+// Hilbert key: Skilling's axes-to-transpose transform (J. Skilling,
+// "Programming the Hilbert curve", AIP Conf. Proc. 707, 2004) on 21-bit
+// coordinates; the transposed words are then bit-interleaved, x first.
+__device__ __forceinline__ uint64_t hilbert_key(uint32_t x0, uint32_t x1, uint32_t x2)
+{
+#pragma unroll
+    for (int q = kKeyBits - 1; q >= 1; --q) {
+        const uint32_t Q = 1u << q, P = Q - 1u;
+        if (x0 & Q) x0 ^= P;
+        if (x1 & Q) {
+            x0 ^= P;
+        } else {
+            uint32_t t = (x0 ^ x1) & P;
+            x0 ^= t;
+            x1 ^= t;
+        }
+        if (x2 & Q) {
+            x0 ^= P;
+        } else {
+            uint32_t t = (x0 ^ x2) & P;
+            x0 ^= t;
+            x2 ^= t;
+        }
+    }
+    x1 ^= x0;
+    x2 ^= x1;
+    // t = xor of (Q-1) over the set bits Q >= 2 of x2: bit b of t is the
+    // parity of the bits of x2 above b.
+    uint32_t t = x2 >> 1;
+    t ^= t >> 1;
+    t ^= t >> 2;
+    t ^= t >> 4;
+    t ^= t >> 8;
+    t ^= t >> 16;
+    x0 ^= t;
+    x1 ^= t;
+    x2 ^= t;
+    return (spread3(x0) << 2) | (spread3(x1) << 1) | spread3(x2);
+}
+
+// Octree level of the longest common key prefix (21 when the keys are equal).
+__device__ __forceinline__ int lcp_level(uint64_t a, uint64_t b)
+{
+    uint64_t d = a ^ b;
+    if (d == 0) return kMaxLevel;
+    return (__clzll((long long)d) - 1) / 3;
+}
+
+// ---------------------------------------------------------------------------
+// Warp helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if ((int)lane_id() >= o) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v)
+{
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Exclusive scan of one value per thread across the block (blockDim.x a
+// multiple of 32, <= 1024).  Returns the exclusive prefix; *total gets the
+// block sum.  `sh` needs 33 words.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *sh, uint32_t *total)
+{
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t inc = warp_incl_scan(v);
+    if (lane == 31) sh[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < nw ? sh[lane] : 0u;
+        uint32_t wi = warp_incl_scan(w);
+        if (lane < nw) sh[lane] = wi - w;
+        if (lane == 31) sh[32] = wi;
+    }
+    __syncthreads();
+    uint32_t r = inc - v + sh[warp];
+    *total = sh[32];
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers implemented in the .cu files
+// ---------------------------------------------------------------------------
+cudaError_t launch_keys(int64_t n, const float *x, const float *y, const float *z, const float *h,
+                        const DevBox &box, float support, int kind, uint64_t *keys, uint32_t *vals,
+                        Status *st, cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) pairs on the low `bits` key bits.
+// Scratch: keys_alt/vals_alt (n each), hist (radix_hist_words(n) words).
+size_t radix_hist_words(uint32_t n);
+cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
+                             uint32_t n, int bits, uint32_t *hist, cudaStream_t s);
+
+// Permute into SFC order as float4 (x, y, z, h), NaN dummies up to npad,
+// and per-cluster boxes: clo = (lo, max r), chi = (hi, 0).
+cudaError_t launch_permute(uint32_t n, uint32_t npad, int M, const uint32_t *perm, const float *x,
+                           const float *y, const float *z, const float *h, float support,
+                           float4 *pos, float4 *clo, float4 *chi, cudaStream_t s);
+
+// Octree, steps 1-2: leaf level per particle, leaf starts; n_leaves lands
+// in st->n_leaves.  Scratch: lev (n bytes), bsum (scan_bsum_words(n)).
+size_t scan_bsum_words(uint32_t n);
+cudaError_t octree_leaves(const uint64_t *keys, uint32_t n, int bucket, uint8_t *lcp,
+                          uint8_t *lev, uint32_t *leaf_first, uint8_t *leaf_lev, uint32_t *bsum,
+                          Status *st, cudaStream_t s);
+// step 3: node offsets per leaf; n_nodes lands in st->n_nodes.
+cudaError_t octree_count_nodes(const uint64_t *keys, uint32_t n_leaves, const uint32_t *leaf_first,
+                               const uint8_t *leaf_lev, uint32_t *nodeoff, uint32_t *bsum,
+                               Status *st, cudaStream_t s);
+// step 4: emit pre-order nodes and their boxes.
+struct OctreeOut {
+    float4 *nlo;      // (lo.xyz, max r)
+    float4 *nhi;      // (hi.xyz, skip as int bits)
+    int2 *nrng;       // (first, end) particle range
+    uint8_t *nlevel;
+    int32_t *nparent;
+    uint32_t *nchild;
+    uint32_t *narrive;
+};
+cudaError_t octree_emit(const uint64_t *keys, uint32_t n, uint32_t n_leaves, uint32_t n_nodes,
+                        const uint32_t *leaf_first, const uint8_t *leaf_lev,
+                        const uint32_t *nodeoff, const float4 *pos, float support,
+                        const OctreeOut &o, cudaStream_t s);
+
+struct SearchArgs {
+    const float4 *pos;
+    const float4 *clo, *chi;
+    const float4 *nlo, *nhi;
+    const int2 *nrng;
+    uint32_t n, nsc, nnodes;
+    DevBox box;
+    float support;
+    uint32_t *stageJ;
+    uint8_t *stageM;
+    uint32_t stage_cap;
+    uint8_t *list;
+    unsigned long long list_cap;
+    uint32_t *rec_off;
+    int compress;
+    Status *st;
+};
+cudaError_t launch_search_ctl(const SearchArgs &a, const uint32_t *work, uint32_t count,
+                              uint32_t *redo, int M, int any_periodic, int grid_blocks,
+                              cudaStream_t s);
+
+enum PassKind { PASS_DENSITY = 0, PASS_COUNT = 1, PASS_SPH = 2, PASS_LJ = 3 };
+struct PassArgs {
+    const float4 *pos;
+    const uint8_t *list;
+    const uint32_t *rec_off;
+    const uint32_t *perm;
+    const float2 *aux;     // per sorted particle: density m; SPH (m, P/rho^2)
+    uint32_t n, nsc;
+    DevBox box;
+    float support;
+    int compress;
+    float p0, p1;          // LJ: eps, sigma
+    float *out0, *out1, *out2;
+    uint32_t *outc;
+    Status *st;
+};
+cudaError_t launch_pass(const PassArgs &a, int kind, int M, int any_periodic, int num_sms,
+                        cudaStream_t s);
+// aux[k] = (a[perm[k]], b ? b[perm[k]] : 0) for k < n; zero for padding.
+cudaError_t launch_gather_aux(uint32_t n, uint32_t npad, const uint32_t *perm, const float *a,
+                              const float *b, const float *c, int mode, float2 *aux,
+                              cudaStream_t s);
+
+}  // namespace nlg

@@ -1,0 +1,420 @@
+// SFC permutation with cluster boxes, and the octree built from the sorted
+// keys (Sec. II-A: clusters are consecutive packs of M SFC particles; the
+// octree is traversed from the root to collect neighbor clusters).
+//
+// Octree definition: leaves are the maximal key-prefix cells holding at most
+// B particles (level-21 cells are leaves whatever their count); internal
+// nodes are all non-empty cells above them; nodes are stored in pre-order
+// with a skip index (first node after the subtree), so traversal needs no
+// stack.  Construction is data-parallel:
+//   1. the cell of particle k at level l holds more than B particles iff
+//      some window of B+1 consecutive sorted keys containing k shares the
+//      level-l prefix, so k's leaf level is 1 + max over those windows of
+//      lcp_level(key[s], key[s+B]);
+//   2. a particle starts a leaf where (level, prefix) changes; a scan numbers
+//      the leaves;
+//   3. leaf i opens the nodes at levels lcp(leaf i-1, leaf i)+1 .. level_i,
+//      which is exactly the pre-order; a scan places them;
+//   4. subtree ends come from binary searches of the key prefix; boxes are
+//      reduced bottom-up by "last child to arrive" counters (no waiting).
+#include "nl_internal.cuh"
+
+namespace nlg {
+
+// ---------------------------------------------------------------------------
+// Permute + cluster boxes
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(256) k_permute(uint32_t n, uint32_t npad,
+                                                 const uint32_t *__restrict__ perm,
+                                                 const float *__restrict__ x,
+                                                 const float *__restrict__ y,
+                                                 const float *__restrict__ z,
+                                                 const float *__restrict__ h, float support,
+                                                 float4 *__restrict__ pos,
+                                                 float4 *__restrict__ clo,
+                                                 float4 *__restrict__ chi)
+{
+    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;  // npad is a multiple of 256
+    if (k >= npad) return;
+    float4 p;
+    float r;
+    const float nan = __int_as_float(0x7fc00000);
+    if (k < n) {
+        uint32_t o = perm[k];
+        p = make_float4(x[o], y[o], z[o], h[o]);
+        r = __fmul_rn(support, p.w);
+    } else {
+        p = make_float4(nan, nan, nan, 0.f);
+        r = 0.f;
+    }
+    pos[k] = p;
+    float lx = k < n ? p.x : INFINITY, ly = k < n ? p.y : INFINITY, lz = k < n ? p.z : INFINITY;
+    float hx = k < n ? p.x : -INFINITY, hy = k < n ? p.y : -INFINITY, hz = k < n ? p.z : -INFINITY;
+#pragma unroll
+    for (int o = 1; o < M; o <<= 1) {
+        lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+        ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+        lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+        hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
+        hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
+        hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
+        r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+    }
+    if ((k & (M - 1)) == 0) {
+        clo[k / M] = make_float4(lx, ly, lz, r);
+        chi[k / M] = make_float4(hx, hy, hz, 0.f);
+    }
+}
+
+cudaError_t launch_permute(uint32_t n, uint32_t npad, int M, const uint32_t *perm, const float *x,
+                           const float *y, const float *z, const float *h, float support,
+                           float4 *pos, float4 *clo, float4 *chi, cudaStream_t s)
+{
+    unsigned grid = (npad + 255) / 256;
+    switch (M) {
+    case 4: k_permute<4><<<grid, 256, 0, s>>>(n, npad, perm, x, y, z, h, support, pos, clo, chi); break;
+    case 8: k_permute<8><<<grid, 256, 0, s>>>(n, npad, perm, x, y, z, h, support, pos, clo, chi); break;
+    case 16: k_permute<16><<<grid, 256, 0, s>>>(n, npad, perm, x, y, z, h, support, pos, clo, chi); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Device-wide exclusive scan over values produced by a functor.
+// ---------------------------------------------------------------------------
+constexpr int SC_THREADS = 256;
+constexpr int SC_ITEMS = 8;
+constexpr int SC_TILE = SC_THREADS * SC_ITEMS;
+
+size_t scan_bsum_words(uint32_t n) { return (size_t)(n + SC_TILE - 1) / SC_TILE + 2; }
+
+template <class F>
+__global__ void __launch_bounds__(SC_THREADS) k_scan_reduce(F f, uint32_t n, uint32_t *bsum)
+{
+    __shared__ uint32_t sh[33];
+    uint32_t base = blockIdx.x * SC_TILE, v = 0;
+#pragma unroll
+    for (int it = 0; it < SC_ITEMS; ++it) {
+        uint32_t k = base + it * SC_THREADS + threadIdx.x;
+        if (k < n) v += f(k);
+    }
+    uint32_t t;
+    block_excl_scan(v, sh, &t);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_bsums(uint32_t *bsum, uint32_t nb, uint32_t *total)
+{
+    __shared__ uint32_t sh[33];
+    uint32_t carry = 0;
+    for (uint32_t b = 0; b < nb; b += 1024) {
+        uint32_t i = b + threadIdx.x;
+        uint32_t v = i < nb ? bsum[i] : 0u;
+        uint32_t t;
+        uint32_t e = block_excl_scan(v, sh, &t);
+        if (i < nb) bsum[i] = carry + e;
+        carry += t;
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+// Every element k gets sink(k, exclusive prefix, value); elements are
+// processed in blocked order (thread t owns SC_ITEMS consecutive elements).
+template <class F, class S>
+__global__ void __launch_bounds__(SC_THREADS) k_scan_apply(F f, S sink, uint32_t n,
+                                                          const uint32_t *bsum)
+{
+    __shared__ uint32_t sh[33];
+    uint32_t base = blockIdx.x * SC_TILE + threadIdx.x * SC_ITEMS;
+    uint32_t v[SC_ITEMS], s = 0;
+#pragma unroll
+    for (int it = 0; it < SC_ITEMS; ++it) {
+        uint32_t k = base + it;
+        v[it] = k < n ? f(k) : 0u;
+        s += v[it];
+    }
+    uint32_t t;
+    uint32_t e = block_excl_scan(s, sh, &t) + bsum[blockIdx.x];
+#pragma unroll
+    for (int it = 0; it < SC_ITEMS; ++it) {
+        uint32_t k = base + it;
+        if (k < n) sink(k, e, v[it]);
+        e += v[it];
+    }
+}
+
+template <class F, class S>
+static cudaError_t scan_exclusive(F f, S sink, uint32_t n, uint32_t *bsum, uint32_t *total,
+                                  cudaStream_t s)
+{
+    uint32_t nb = (n + SC_TILE - 1) / SC_TILE;
+    if (nb == 0) {
+        return cudaMemsetAsync(total, 0, 4, s);
+    }
+    k_scan_reduce<<<nb, SC_THREADS, 0, s>>>(f, n, bsum);
+    k_scan_bsums<<<1, 1024, 0, s>>>(bsum, nb, total);
+    k_scan_apply<<<nb, SC_THREADS, 0, s>>>(f, sink, n, bsum);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Step 1: leaf level of every particle
+// ---------------------------------------------------------------------------
+__global__ void k_lcp_window(const uint64_t *__restrict__ keys, uint32_t n, int B,
+                             uint8_t *__restrict__ lcp)
+{
+    uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s + (uint32_t)B < n) lcp[s] = (uint8_t)lcp_level(keys[s], keys[s + B]);
+}
+
+constexpr int LL_THREADS = 512;
+
+// lev[k] = min(21, 1 + max_{s in [k-B, k], 0 <= s < n-B} lcp[s]); n <= B -> 0
+__global__ void __launch_bounds__(LL_THREADS) k_leaf_level(const uint8_t *__restrict__ lcp,
+                                                           uint32_t n, int B,
+                                                           uint8_t *__restrict__ lev)
+{
+    extern __shared__ uint8_t win[];  // LL_THREADS + B entries
+    const int64_t k0 = (int64_t)blockIdx.x * LL_THREADS;
+    const int64_t nw = (int64_t)n - B;  // number of windows
+    for (int t = threadIdx.x; t < LL_THREADS + B; t += LL_THREADS) {
+        int64_t s = k0 - B + t;
+        win[t] = (s >= 0 && s < nw) ? lcp[s] : 0xffu;
+    }
+    __syncthreads();
+    int64_t k = k0 + threadIdx.x;
+    if (k >= n) return;
+    if ((int64_t)n <= B) {
+        lev[k] = 0;
+        return;
+    }
+    int m = -1;
+    for (int t = 0; t <= B; ++t) {
+        uint8_t v = win[threadIdx.x + t];
+        if (v != 0xffu && (int)v > m) m = v;
+    }
+    int l = m + 1;
+    lev[k] = (uint8_t)(l > kMaxLevel ? kMaxLevel : l);
+}
+
+// ---------------------------------------------------------------------------
+// Step 2: leaf starts
+// ---------------------------------------------------------------------------
+struct LeafFlag {
+    const uint64_t *keys;
+    const uint8_t *lev;
+    __device__ uint32_t operator()(uint32_t k) const
+    {
+        if (k == 0) return 1u;
+        int l = lev[k];
+        if (l != lev[k - 1]) return 1u;
+        if (l == 0) return 0u;
+        int sh = 63 - 3 * l;
+        return (keys[k] >> sh) != (keys[k - 1] >> sh) ? 1u : 0u;
+    }
+};
+
+struct LeafSink {
+    const uint8_t *lev;
+    uint32_t n;
+    uint32_t *leaf_first;
+    uint8_t *leaf_lev;
+    __device__ void operator()(uint32_t k, uint32_t excl, uint32_t v) const
+    {
+        if (v) {
+            leaf_first[excl] = k;
+            leaf_lev[excl] = lev[k];
+        }
+        if (k == n - 1) leaf_first[excl + v] = n;
+    }
+};
+
+cudaError_t octree_leaves(const uint64_t *keys, uint32_t n, int bucket, uint8_t *lcp,
+                          uint8_t *lev, uint32_t *leaf_first, uint8_t *leaf_lev, uint32_t *bsum,
+                          Status *st, cudaStream_t s)
+{
+    if (n > (uint32_t)bucket)
+        k_lcp_window<<<(n - bucket + 255) / 256, 256, 0, s>>>(keys, n, bucket, lcp);
+    k_leaf_level<<<(n + LL_THREADS - 1) / LL_THREADS, LL_THREADS, LL_THREADS + bucket, s>>>(
+        lcp, n, bucket, lev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return scan_exclusive(LeafFlag{keys, lev}, LeafSink{lev, n, leaf_first, leaf_lev}, n, bsum,
+                          &st->n_leaves, s);
+}
+
+// ---------------------------------------------------------------------------
+// Step 3: nodes opened by each leaf
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int leaf_lcp(const uint64_t *keys, const uint32_t *leaf_first, uint32_t i)
+{
+    return i == 0 ? -1 : lcp_level(keys[leaf_first[i - 1]], keys[leaf_first[i]]);
+}
+
+struct NodeCount {
+    const uint64_t *keys;
+    const uint32_t *leaf_first;
+    const uint8_t *leaf_lev;
+    __device__ uint32_t operator()(uint32_t i) const
+    {
+        return (uint32_t)((int)leaf_lev[i] - leaf_lcp(keys, leaf_first, i));
+    }
+};
+
+struct NodeSink {
+    uint32_t nl;
+    uint32_t *nodeoff;
+    __device__ void operator()(uint32_t i, uint32_t excl, uint32_t v) const
+    {
+        nodeoff[i] = excl;
+        if (i == nl - 1) nodeoff[nl] = excl + v;
+    }
+};
+
+cudaError_t octree_count_nodes(const uint64_t *keys, uint32_t n_leaves, const uint32_t *leaf_first,
+                               const uint8_t *leaf_lev, uint32_t *nodeoff, uint32_t *bsum,
+                               Status *st, cudaStream_t s)
+{
+    return scan_exclusive(NodeCount{keys, leaf_first, leaf_lev}, NodeSink{n_leaves, nodeoff},
+                          n_leaves, bsum, &st->n_nodes, s);
+}
+
+// ---------------------------------------------------------------------------
+// Step 4: emit nodes, then boxes bottom-up
+// ---------------------------------------------------------------------------
+// first index in [lo, hi) with keys[idx] >= bound
+__device__ __forceinline__ uint32_t lower_bound_u64(const uint64_t *keys, uint32_t lo, uint32_t hi,
+                                                    uint64_t bound)
+{
+    while (lo < hi) {
+        uint32_t mid = lo + ((hi - lo) >> 1);
+        if (keys[mid] < bound) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// leaf index whose first particle is exactly p (p is a leaf start)
+__device__ __forceinline__ uint32_t leaf_of(const uint32_t *leaf_first, uint32_t nl, uint32_t p)
+{
+    uint32_t lo = 0, hi = nl;
+    while (lo < hi) {
+        uint32_t mid = lo + ((hi - lo) >> 1);
+        if (leaf_first[mid] < p) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_emit_nodes(const uint64_t *__restrict__ keys, uint32_t n, uint32_t nl,
+                             uint32_t nn, const uint32_t *__restrict__ leaf_first,
+                             const uint8_t *__restrict__ leaf_lev,
+                             const uint32_t *__restrict__ nodeoff, OctreeOut o)
+{
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nl) return;
+    const int c = leaf_lcp(keys, leaf_first, i);
+    const uint32_t v0 = nodeoff[i], e = nodeoff[i + 1] - v0;
+    const uint32_t first = leaf_first[i];
+    const uint64_t kf = keys[first];
+    for (uint32_t t = 0; t < e; ++t) {
+        const uint32_t v = v0 + t;
+        const int l = c + 1 + (int)t;
+        uint32_t end, skip;
+        if (t == e - 1) {
+            end = leaf_first[i + 1];
+            skip = v + 1;
+        } else {
+            if (l == 0) {
+                end = n;
+            } else {
+                int sh = 63 - 3 * l;
+                uint64_t bound = ((kf >> sh) + 1ull) << sh;
+                end = lower_bound_u64(keys, first, n, bound);
+            }
+            skip = end >= n ? nn : nodeoff[leaf_of(leaf_first, nl, end)];
+        }
+        int32_t parent;
+        if (t > 0) {
+            parent = (int32_t)(v - 1);
+        } else if (i == 0) {
+            parent = -1;
+        } else {
+            // ancestor of leaf i at level c, opened by the leaf holding its
+            // first particle
+            uint32_t pf;
+            if (c == 0) {
+                pf = 0;
+            } else {
+                int sh = 63 - 3 * c;
+                pf = lower_bound_u64(keys, 0, first, (kf >> sh) << sh);
+            }
+            uint32_t j = leaf_of(leaf_first, nl, pf);
+            int cj = leaf_lcp(keys, leaf_first, j);
+            parent = (int32_t)(nodeoff[j] + (uint32_t)(c - cj - 1));
+        }
+        o.nrng[v] = make_int2((int)first, (int)end);
+        o.nlevel[v] = (uint8_t)l;
+        o.nparent[v] = parent;
+        o.nhi[v] = make_float4(0.f, 0.f, 0.f, __int_as_float((int)skip));
+        if (parent >= 0) atomicAdd(&o.nchild[parent], 1u);
+    }
+}
+
+__global__ void k_node_boxes(uint32_t nn, const float4 *__restrict__ pos, float support, OctreeOut o)
+{
+    uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nn) return;
+    int skip = __float_as_int(o.nhi[v].w);
+    if ((uint32_t)skip != v + 1) return;  // internal nodes are reduced by their last child
+    int2 rg = o.nrng[v];
+    float lx = INFINITY, ly = INFINITY, lz = INFINITY, r = 0.f;
+    float hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
+    for (int k = rg.x; k < rg.y; ++k) {
+        float4 p = pos[k];
+        lx = fminf(lx, p.x); ly = fminf(ly, p.y); lz = fminf(lz, p.z);
+        hx = fmaxf(hx, p.x); hy = fmaxf(hy, p.y); hz = fmaxf(hz, p.z);
+        r = fmaxf(r, __fmul_rn(support, p.w));
+    }
+    o.nlo[v] = make_float4(lx, ly, lz, r);
+    o.nhi[v] = make_float4(hx, hy, hz, __int_as_float(skip));
+    int32_t p = o.nparent[v];
+    while (p >= 0) {
+        __threadfence();
+        uint32_t arrived = atomicAdd(&o.narrive[p], 1u);
+        if (arrived + 1 != o.nchild[p]) return;
+        __threadfence();
+        float4 lo = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+        float3 hi = make_float3(-INFINITY, -INFINITY, -INFINITY);
+        const uint32_t pend = (uint32_t)__float_as_int(__ldcg(&o.nhi[p].w));
+        uint32_t c = (uint32_t)p + 1;
+        while (c < pend) {
+            float4 cl = __ldcg(&o.nlo[c]);
+            float4 ch = __ldcg(&o.nhi[c]);
+            lo.x = fminf(lo.x, cl.x); lo.y = fminf(lo.y, cl.y); lo.z = fminf(lo.z, cl.z);
+            lo.w = fmaxf(lo.w, cl.w);
+            hi.x = fmaxf(hi.x, ch.x); hi.y = fmaxf(hi.y, ch.y); hi.z = fmaxf(hi.z, ch.z);
+            const uint32_t nx = (uint32_t)__float_as_int(ch.w);
+            c = nx > c ? nx : c + 1;  // always advances
+        }
+        o.nlo[p] = lo;
+        o.nhi[p] = make_float4(hi.x, hi.y, hi.z, __int_as_float((int)pend));
+        p = o.nparent[p];
+    }
+}
+
+cudaError_t octree_emit(const uint64_t *keys, uint32_t n, uint32_t n_leaves, uint32_t n_nodes,
+                        const uint32_t *leaf_first, const uint8_t *leaf_lev,
+                        const uint32_t *nodeoff, const float4 *pos, float support,
+                        const OctreeOut &o, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(o.nchild, 0, (size_t)n_nodes * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(o.narrive, 0, (size_t)n_nodes * 4, s);
+    if (e != cudaSuccess) return e;
+    k_emit_nodes<<<(n_leaves + 127) / 128, 128, 0, s>>>(keys, n, n_leaves, n_nodes, leaf_first,
+                                                        leaf_lev, nodeoff, o);
+    k_node_boxes<<<(n_nodes + 127) / 128, 128, 0, s>>>(n_nodes, pos, support, o);
+    return cudaGetLastError();
+}
+
+}  // namespace nlg

@@ -1,0 +1,262 @@
+// Cluster-pair search and list encoding (Sec. II-A, II-B, II-C).
+//
+// One warp per super-cluster (8 i-clusters of M particles), taken from an
+// atomic work counter by a persistent grid.  The warp walks the pre-order
+// octree without a stack (skip indices); lanes test the node box against
+// their i-cluster box (lane & 7) inflated by the larger of the two maximum
+// radii, with monotone round-to-nearest gaps so that no pair accepted by the
+// FP32 predicate can be pruned.  At a leaf, 4 j-clusters x 8 i-clusters are
+// box-tested per round (one lane each); each surviving (i-cluster, j-cluster)
+// tile is decided by the exact FP32 predicate on its M x M pairs.  Depth-first
+// order yields ascending j-clusters (Sec. II-A), so the (J, mask) list is
+// produced sorted; it is staged per warp (L2 resident) and then encoded:
+// u32 count | u8 masks | nibble blocks of 32 differences (Sec. II-B, the
+// layout of Sec. II-C with w = 32), reserved with one atomicAdd in the list
+// buffer.  Super-clusters whose list exceeds the staging capacity or the
+// list buffer are queued in a redo list and re-run by the host after growth.
+#include "nl_internal.cuh"
+
+namespace nlg {
+
+constexpr int SR_THREADS = 256;
+constexpr int SR_WARPS = SR_THREADS / 32;
+constexpr int WIN_WORDS = 64;
+
+struct SearchCtl {
+    const uint32_t *work;   // NULL: super-clusters 0..count-1, else ids
+    uint32_t count;
+    uint32_t *redo;         // ids that could not be stored this time
+};
+
+__device__ __forceinline__ uint32_t hex_digits(uint32_t v) { return (32u - __clz(v) + 3u) >> 2; }
+
+__device__ __forceinline__ void win_put(uint32_t *win, uint32_t W0, uint32_t p, uint32_t v)
+{
+    uint32_t l = p - W0;
+    atomicOr(&win[l >> 3], v << ((l & 7u) * 4u));
+}
+
+// Encode the staged list of one super-cluster.  Returns false when the list
+// buffer is full (nothing written for this super-cluster).
+__device__ bool encode_record(uint32_t cnt, const uint32_t *stJ, const uint8_t *stM,
+                              uint32_t *win, const SearchArgs &a, uint32_t s)
+{
+    const unsigned lane = lane_id();
+    const unsigned lt = lanemask_lt();
+    uint32_t nib = 0;
+    if (a.compress) {
+        uint32_t carry = 0xffffffffu;  // J_{-1} = -1
+        for (uint32_t b0 = 0; b0 < cnt; b0 += 32) {
+            uint32_t t = b0 + lane;
+            uint32_t J = t < cnt ? stJ[t] : 0u;
+            uint32_t prev = __shfl_up_sync(0xffffffffu, J, 1);
+            if (lane == 0) prev = carry;
+            uint32_t d = t < cnt ? J - prev : 1u;
+            uint32_t nb = d == 1u ? 0u : (d <= 9u ? 1u : 1u + hex_digits(d));
+            nib += 8u + warp_sum(nb);
+            carry = __shfl_sync(0xffffffffu, J, 31);
+        }
+    }
+    const uint32_t mask_words = (cnt + 3u) >> 2;
+    const uint32_t body_words = a.compress ? (nib + 7u) >> 3 : cnt;
+    const uint32_t words = 1u + mask_words + body_words;
+    unsigned long long off = 0;
+    if (lane == 0) off = atomicAdd(&a.st->list_used, (unsigned long long)words * 4ull);
+    off = __shfl_sync(0xffffffffu, off, 0);
+    if (off + (unsigned long long)words * 4ull > a.list_cap) return false;
+    uint32_t *rec = reinterpret_cast<uint32_t *>(a.list + off);
+    if (lane == 0) {
+        rec[0] = cnt;
+        a.rec_off[s] = (uint32_t)(off >> 2);
+    }
+    for (uint32_t w = lane; w < mask_words; w += 32) {
+        uint32_t v = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t t = 4 * w + q;
+            if (t < cnt) v |= (uint32_t)stM[t] << (8 * q);
+        }
+        rec[1 + w] = v;
+    }
+    uint32_t *body = rec + 1 + mask_words;
+    if (!a.compress) {
+        for (uint32_t t = lane; t < cnt; t += 32) body[t] = stJ[t];
+        return true;
+    }
+    win[lane] = 0u;
+    win[lane + 32] = 0u;
+    __syncwarp();
+    uint32_t W0 = 0, pos = 0, carry = 0xffffffffu;
+    for (uint32_t b0 = 0; b0 < cnt; b0 += 32) {
+        uint32_t t = b0 + lane;
+        bool valid = t < cnt;
+        uint32_t J = valid ? stJ[t] : 0u;
+        uint32_t prev = __shfl_up_sync(0xffffffffu, J, 1);
+        if (lane == 0) prev = carry;
+        uint32_t d = valid ? J - prev : 1u;
+        bool bit = d != 1u;
+        uint32_t bm = __ballot_sync(0xffffffffu, bit);
+        uint32_t ndat = (bit && d > 9u) ? hex_digits(d) : 0u;
+        uint32_t info = !bit ? 0u : (d <= 9u ? d + 6u : ndat - 1u);
+        uint32_t incl = warp_incl_scan(ndat);
+        uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        uint32_t nbits = __popc(bm);
+        if (lane < 8) win_put(win, W0, pos + lane, (bm >> (4 * lane)) & 0xfu);
+        if (bit) win_put(win, W0, pos + 8 + __popc(bm & lt), info);
+        uint32_t pd = pos + 8 + nbits + (incl - ndat);
+        for (uint32_t q = 0; q < ndat; ++q) win_put(win, W0, pd + q, (d >> (4 * (ndat - 1 - q))) & 0xfu);
+        __syncwarp();
+        uint32_t pend = pos + 8 + nbits + tot;
+        uint32_t full = (pend - W0) >> 3;
+        for (uint32_t w = lane; w < full; w += 32) body[(W0 >> 3) + w] = win[w];
+        __syncwarp();
+        uint32_t keep = win[full];
+        __syncwarp();
+        win[lane] = 0u;
+        win[lane + 32] = 0u;
+        __syncwarp();
+        if (lane == 0) win[0] = keep;
+        __syncwarp();
+        W0 += full * 8u;
+        pos = pend;
+        carry = __shfl_sync(0xffffffffu, J, 31);
+    }
+    if (pos > W0 && lane == 0) body[W0 >> 3] = win[0];
+    __syncwarp();
+    return true;
+}
+
+template <int M, bool PER>
+__global__ void __launch_bounds__(SR_THREADS) k_search(SearchArgs a, SearchCtl ctl)
+{
+    constexpr int NP = (M * M) / 32 > 0 ? (M * M) / 32 : 1;  // pairs per lane per tile
+    constexpr int JSTEP = 32 / M;
+    __shared__ uint32_t wins[SR_WARPS][WIN_WORDS];
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    uint32_t *win = wins[warp];
+    const uint32_t slot = blockIdx.x * SR_WARPS + warp;
+    uint32_t *stJ = a.stageJ + (size_t)slot * a.stage_cap;
+    uint8_t *stM = a.stageM + (size_t)slot * a.stage_cap;
+    const uint32_t II = lane % M;
+    const uint32_t JJ0 = (lane / M) % M;
+
+    for (;;) {
+        uint32_t tk = 0;
+        if (lane == 0) tk = atomicAdd(&a.st->ticket, 1u);
+        tk = __shfl_sync(0xffffffffu, tk, 0);
+        if (tk >= ctl.count) break;
+        const uint32_t s = ctl.work ? ctl.work[tk] : tk;
+
+        // i-cluster box of this lane's cluster (lane & 7)
+        const float4 ilo = a.clo[s * kSC + (lane & 7)];
+        const float4 ihi = a.chi[s * kSC + (lane & 7)];
+        float4 pi[kSC];
+        float ri[kSC];
+#pragma unroll
+        for (int k = 0; k < kSC; ++k) {
+            pi[k] = a.pos[(s * kSC + k) * M + II];
+            ri[k] = __fmul_rn(a.support, pi[k].w);
+        }
+
+        uint32_t cnt = 0, tiles = 0;
+        int lastJ = -1;
+        uint32_t v = 0;
+        while (v < a.nnodes) {
+            const float4 nlo = a.nlo[v];
+            const float4 nhi = a.nhi[v];
+            const uint32_t skip = (uint32_t)__float_as_int(nhi.w);
+            const bool near = boxes_near<PER>(ilo, ihi, nlo, nhi, a.box);
+            if (!__any_sync(0xffffffffu, near)) {
+                v = skip > v ? skip : v + 1;  // always advances
+                continue;
+            }
+            if (skip != v + 1) {  // internal node: descend to its first child
+                ++v;
+                continue;
+            }
+            const int2 rg = a.nrng[v];
+            const int Jlo = max(rg.x / M, lastJ + 1);
+            const int Jhi = (rg.y - 1) / M;
+            for (int Jb = Jlo; Jb <= Jhi; Jb += 4) {
+                const int Jl = Jb + (int)(lane >> 3);
+                bool cand = false;
+                if (Jl <= Jhi) cand = boxes_near<PER>(ilo, ihi, a.clo[Jl], a.chi[Jl], a.box);
+                const uint32_t bal = __ballot_sync(0xffffffffu, cand);
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t cm = (bal >> (8 * q)) & 0xffu;
+                    if (!cm) continue;
+                    const int J = Jb + q;
+                    uint32_t mask = 0;
+#pragma unroll
+                    for (int t = 0; t < NP; ++t) {
+                        const uint32_t jj = (uint32_t)J * M + JJ0 + t * JSTEP;
+                        const float4 pj = a.pos[jj];
+                        const float rj = __fmul_rn(a.support, pj.w);
+#pragma unroll
+                        for (int k = 0; k < kSC; ++k) {
+                            if (!((cm >> k) & 1u) || ((mask >> k) & 1u)) continue;
+                            const uint32_t ii = (s * kSC + k) * M + II;
+                            const float d2 = pair_d2<PER>(pi[k], pj, a.box);
+                            const float r = fmaxf(ri[k], rj);
+                            const bool hit = (ii != jj) && d2 < __fmul_rn(r, r);
+                            if (__any_sync(0xffffffffu, hit)) mask |= 1u << k;
+                        }
+                    }
+                    if (mask) {
+                        if (lane == 0 && cnt < a.stage_cap) {
+                            stJ[cnt] = (uint32_t)J;
+                            stM[cnt] = (uint8_t)mask;
+                        }
+                        ++cnt;
+                        tiles += __popc(mask);
+                    }
+                }
+            }
+            lastJ = max(lastJ, Jhi);
+            ++v;
+        }
+        __syncwarp();
+        bool ok = cnt <= a.stage_cap;
+        if (!ok) {
+            if (lane == 0) atomicMax(&a.st->max_count, cnt);
+        } else {
+            ok = encode_record(cnt, stJ, stM, win, a, s);
+            if (!ok && lane == 0) atomicExch(&a.st->list_overflow, 1u);
+        }
+        if (lane == 0) {
+            if (!ok) {
+                uint32_t r = atomicAdd(&a.st->stage_overflow, 1u);
+                ctl.redo[r] = s;
+                a.rec_off[s] = kBadRecord;
+            } else {
+                atomicAdd(&a.st->n_entries, (unsigned long long)cnt);
+                atomicAdd(&a.st->n_tiles, (unsigned long long)tiles);
+            }
+        }
+    }
+}
+
+template <int M>
+static void launch_m(const SearchArgs &a, const SearchCtl &c, int per, int grid, cudaStream_t s)
+{
+    if (per)
+        k_search<M, true><<<grid, SR_THREADS, 0, s>>>(a, c);
+    else
+        k_search<M, false><<<grid, SR_THREADS, 0, s>>>(a, c);
+}
+
+cudaError_t launch_search_ctl(const SearchArgs &a, const uint32_t *work, uint32_t count,
+                              uint32_t *redo, int M, int any_periodic, int grid,
+                              cudaStream_t s)
+{
+    SearchCtl c{work, count, redo};
+    switch (M) {
+    case 4: launch_m<4>(a, c, any_periodic, grid, s); break;
+    case 8: launch_m<8>(a, c, any_periodic, grid, s); break;
+    case 16: launch_m<16>(a, c, any_periodic, grid, s); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace nlg

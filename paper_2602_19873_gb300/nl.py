@@ -1,0 +1,224 @@
+"""Python binding of the C ABI in include/nl.h (argument marshalling only).
+
+Functions keep the C names and take torch CUDA tensors (float32/int32
+contiguous) or raw device pointers; every step of the path runs in
+libnlgb.so.  The first call loads the library and raises NLError when it is
+missing, when no CUDA device is visible, or when a call fails.  Inspection
+helpers return numpy arrays.
+"""
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+NL_OK = 0
+NL_KEY_MORTON, NL_KEY_HILBERT = 0, 1
+STATUS_NAMES = {0: "NL_OK", 1: "NL_ERR_ARG", 2: "NL_ERR_RADIUS", 3: "NL_ERR_OOM", 4: "NL_ERR_CUDA",
+                5: "NL_ERR_CAPACITY", 6: "NL_ERR_NOT_CONVERGED", 7: "NL_ERR_TIMEOUT",
+                8: "NL_ERR_UNIMPLEMENTED"}
+
+
+class NLError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class nl_box(C.Structure):
+    _fields_ = [("lo", C.c_float * 3), ("hi", C.c_float * 3), ("periodic", C.c_int32 * 3)]
+
+
+class nl_params(C.Structure):
+    _fields_ = [("key", C.c_int32), ("cluster", C.c_int32), ("support", C.c_float),
+                ("compress", C.c_int32), ("leaf_bucket", C.c_int32)]
+
+
+class nl_sizes(C.Structure):
+    _fields_ = [("n", C.c_int64), ("n_clusters", C.c_int64), ("n_superclusters", C.c_int64),
+                ("n_leaves", C.c_int64), ("n_nodes", C.c_int64), ("n_entries", C.c_int64),
+                ("n_tiles", C.c_int64), ("list_bytes", C.c_int64), ("cluster", C.c_int32),
+                ("compress", C.c_int32)]
+
+
+P = C.c_void_p
+_SIGS = {
+    "nl_default_params": (None, [P]),
+    "nl_last_error": (C.c_char_p, []),
+    "nl_build": (C.c_int, [P, P, P, P, C.c_int64, P, P, P, P]),
+    "nl_rebuild": (C.c_int, [P, P, P, P, P, C.c_int64, P, P, P]),
+    "nl_density_pass": (C.c_int, [P, P, P, P]),
+    "nl_neighbor_counts": (C.c_int, [P, P, P]),
+    "nl_free": (C.c_int, [P]),
+    "nl_get_sizes": (C.c_int, [P, P]),
+    "nl_copy_sorted": (C.c_int, [P, P, P]),
+    "nl_copy_octree": (C.c_int, [P, P, P, P, P, P]),
+    "nl_copy_records": (C.c_int, [P, P, P]),
+    "nl_create": (C.c_int, [P]),
+    "nl_set_profiling": (C.c_int, [P, C.c_int32]),
+    "nl_get_stage_times": (C.c_int, [P, P, C.c_int32, P]),
+    "nl_density_from_host": (C.c_int, [P, P, P, P, P, P, C.c_int64, P, P, P, P]),
+}
+
+STAGES = ["keys", "sort", "permute", "octree", "search", "pass_gather", "pass"]
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load libnlgb.so (building it first when asked) and bind signatures."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if build_if_missing:
+                path = _build.build()
+            if not os.path.exists(path):
+                raise NLError(8, "native library %s is missing; run build()" % path)
+            lib = C.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(st):
+    if st != NL_OK:
+        raise NLError(st, load().nl_last_error().decode())
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor (or an int pointer / None)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_box(box):
+    b = nl_box()
+    for a in range(3):
+        b.lo[a] = float(np.float32(box["lo"][a]))
+        b.hi[a] = float(np.float32(box["hi"][a]))
+        b.periodic[a] = int(box["periodic"][a])
+    return b
+
+
+def make_params(key=NL_KEY_HILBERT, cluster=8, support=2.0, compress=1, leaf_bucket=64):
+    p = nl_params()
+    load().nl_default_params(C.byref(p))
+    p.key, p.cluster, p.support = int(key), int(cluster), float(support)
+    p.compress, p.leaf_bucket = int(compress), int(leaf_bucket)
+    return p
+
+
+class NeighborList:
+    """Owner of one nl_list handle.  Positions x, y, z and smoothing lengths h
+    are float32 CUDA tensors in caller order."""
+
+    def __init__(self):
+        self.handle = None
+
+    def build(self, x, y, z, h, box, params, stream=None):
+        L = load()
+        b = make_box(box) if isinstance(box, dict) else box
+        n = int(x.numel())
+        if self.handle is None:
+            out = C.c_void_p()
+            _check(L.nl_build(_ptr(x), _ptr(y), _ptr(z), _ptr(h), n, C.byref(b), C.byref(params),
+                              _stream(stream), C.byref(out)))
+            self.handle = out
+        else:
+            _check(L.nl_rebuild(self.handle, _ptr(x), _ptr(y), _ptr(z), _ptr(h), n, C.byref(b),
+                                C.byref(params), _stream(stream)))
+        return self
+
+    def ensure_handle(self):
+        if self.handle is None:
+            out = C.c_void_p()
+            _check(load().nl_create(C.byref(out)))
+            self.handle = out
+        return self
+
+    def set_profiling(self, on=True):
+        self.ensure_handle()
+        _check(load().nl_set_profiling(self.handle, 1 if on else 0))
+
+    def stage_times(self):
+        ms = (C.c_float * 16)()
+        cnt = C.c_int32()
+        _check(load().nl_get_stage_times(self.handle, ms, 16, C.byref(cnt)))
+        return {STAGES[k]: float(ms[k]) for k in range(cnt.value)}
+
+    def density_from_host(self, x, y, z, h, m, box, params, rho, stream=None):
+        """x..m, rho: numpy float32 arrays (pinned or pageable host memory)."""
+        self.ensure_handle()
+        b = make_box(box) if isinstance(box, dict) else box
+        arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (x, y, z, h, m)]
+        assert rho.dtype == np.float32 and rho.flags.c_contiguous
+        _check(load().nl_density_from_host(self.handle, *[a.ctypes.data for a in arrs],
+                                           len(arrs[0]), C.byref(b), C.byref(params),
+                                           rho.ctypes.data, _stream(stream)))
+
+    def density_pass(self, m, rho, stream=None):
+        _check(load().nl_density_pass(self.handle, _ptr(m), _ptr(rho), _stream(stream)))
+
+    def neighbor_counts(self, counts, stream=None):
+        _check(load().nl_neighbor_counts(self.handle, _ptr(counts), _stream(stream)))
+
+    def sizes(self):
+        s = nl_sizes()
+        _check(load().nl_get_sizes(self.handle, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in nl_sizes._fields_}
+
+    def sorted(self):
+        n = self.sizes()["n"]
+        keys = np.zeros(n, np.uint64)
+        perm = np.zeros(n, np.int32)
+        _check(load().nl_copy_sorted(self.handle, keys.ctypes.data, perm.ctypes.data))
+        return keys, perm
+
+    def octree(self):
+        nn = self.sizes()["n_nodes"]
+        arrs = [np.zeros(nn, np.int32) for _ in range(5)]
+        _check(load().nl_copy_octree(self.handle, *[a.ctypes.data for a in arrs]))
+        return dict(zip(["level", "first", "end", "leaf", "skip"], arrs))
+
+    def records(self):
+        s = self.sizes()
+        off = np.zeros(s["n_superclusters"], np.uint64)
+        data = np.zeros(max(1, s["list_bytes"]), np.uint8)
+        _check(load().nl_copy_records(self.handle, off.ctypes.data, data.ctypes.data))
+        return off, data[:s["list_bytes"]]
+
+    def free(self):
+        if self.handle is not None:
+            load().nl_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -1,0 +1,220 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on the
+same seeded inputs (keys/sort/octree/records bit-exact, density within
+1e-5 relative, counts exact)."""
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_2602_19873_gb300 import nl
+from paper_2602_19873_gb300 import workloads as wl
+
+from nlcheck import (DENSITY_RTOL, compare_records, full_reference, gpu_build, gpu_counts,
+                     gpu_density, oracle_sorted)
+
+pytestmark = pytest.mark.gpu
+
+
+def _cases():
+    return {
+        "uniform": lambda: wl.uniform(20037, seed=101, n_target=60.0),
+        "evrard": lambda: wl.evrard(20011, seed=102, n_target=60.0),
+        "lj_fluid": lambda: wl.lj_fluid(12000, seed=103),
+        "plummer": lambda: wl.plummer(24001, n_spheres=3, seed=104, n_target=60.0),
+    }
+
+
+@pytest.fixture(scope="module")
+def cases():
+    out = {}
+    for k, f in _cases().items():
+        d = f()
+        o = oracle_sorted(d)
+        out[k] = (d, o, full_reference(o, d))
+    return out
+
+
+@pytest.mark.parametrize("name", ["uniform", "evrard", "lj_fluid", "plummer"])
+def test_keys_and_stable_sort_bit_exact(cases, name):
+    d, o, _ = cases[name]
+    L, t = gpu_build(d)
+    keys, perm = L.sorted()
+    assert np.array_equal(keys, o["keys"])
+    assert np.array_equal(perm.astype(np.int64), o["perm"])
+    L.free()
+
+
+@pytest.mark.parametrize("name", ["uniform", "plummer"])
+@pytest.mark.parametrize("bucket", [16, 64])
+def test_octree_bit_exact(cases, name, bucket):
+    d, o, _ = cases[name]
+    L, t = gpu_build(d, bucket=bucket)
+    g = L.octree()
+    ref = orc.octree(o["keys"], bucket)
+    assert np.array_equal(g["level"], ref["level"])
+    assert np.array_equal(g["first"], ref["first"])
+    assert np.array_equal(g["end"], ref["end"])
+    assert np.array_equal(g["leaf"].astype(bool), ref["leaf"])
+    # skip = first node after the subtree: next node whose level <= own level
+    lev = ref["level"]
+    nn = len(lev)
+    for v in range(0, nn, max(1, nn // 500)):
+        w = v + 1
+        while w < nn and lev[w] > lev[v]:
+            w += 1
+        assert g["skip"][v] == w
+    L.free()
+
+
+@pytest.mark.parametrize("name", ["uniform", "evrard", "lj_fluid", "plummer"])
+@pytest.mark.parametrize("cluster", [4, 8, 16])
+@pytest.mark.parametrize("compress", [1, 0])
+def test_records_byte_exact(cases, name, cluster, compress):
+    d, o, (g_off, g_idx, p_off, p_idx) = cases[name]
+    L, t = gpu_build(d, cluster=cluster, compress=compress)
+    s = L.sizes()
+    n = len(o["xs"])
+    nsc = s["n_superclusters"]
+    assert nsc == (n + 8 * cluster - 1) // (8 * cluster)
+    total, so, J, m = compare_records(L, o, d, cluster, compress, np.arange(nsc), np.arange(n),
+                                      p_off, p_idx)
+    assert s["list_bytes"] == total
+    assert s["n_entries"] == len(J)
+    assert s["n_tiles"] == int(sum(bin(int(v)).count("1") for v in m))
+    L.free()
+
+
+@pytest.mark.parametrize("name", ["uniform", "evrard", "lj_fluid", "plummer"])
+@pytest.mark.parametrize("cluster", [4, 8, 16])
+def test_density_and_counts(cases, name, cluster):
+    d, o, (g_off, g_idx, p_off, p_idx) = cases[name]
+    L, t = gpu_build(d, cluster=cluster)
+    n = len(o["xs"])
+    rho = gpu_density(L, t, n)[o["perm"]]
+    want = orc.density(o["xs"], o["ys"], o["zs"], o["hs"], o["ms"], d["box"], g_off, g_idx,
+                       np.arange(n))
+    rel = np.abs(rho - want) / want
+    assert rel.max() <= DENSITY_RTOL, rel.max()
+    cnt = gpu_counts(L, n)[o["perm"]]
+    assert np.array_equal(cnt, np.diff(g_off))
+    L.free()
+
+
+def test_uncompressed_pass_matches_compressed(cases):
+    d, o, _ = cases["plummer"]
+    La, ta = gpu_build(d, compress=1)
+    Lb, tb = gpu_build(d, compress=0)
+    n = len(o["xs"])
+    assert np.array_equal(gpu_density(La, ta, n), gpu_density(Lb, tb, n))
+    sa, sb = La.sizes(), Lb.sizes()
+    assert sa["list_bytes"] < sb["list_bytes"]
+    La.free()
+    Lb.free()
+
+
+def test_rebuild_reuses_handle(cases):
+    d1, o1, (g1, _, p1o, p1i) = cases["uniform"]
+    d2, o2, (g2, _, p2o, p2i) = cases["plummer"]
+    L, t = gpu_build(d1)
+    from nlcheck import to_dev
+    t2 = to_dev(d2)
+    p = nl.make_params(key=d2["kind"], cluster=8, support=d2["support"])
+    L.build(t2["x"], t2["y"], t2["z"], t2["h"], d2["box"], p)
+    n = len(o2["xs"])
+    compare_records(L, o2, d2, 8, 1, np.arange(L.sizes()["n_superclusters"]), np.arange(n), p2o, p2i)
+    L.free()
+
+
+# ----------------------------------------------------------------------------- edge cases
+def _tiny(n, seed, per=True, h=0.05):
+    rng = np.random.default_rng(seed)
+    p = rng.random((3, n)).astype(np.float32)
+    return {"x": p[0], "y": p[1], "z": p[2], "h": np.full(n, h, np.float32),
+            "m": np.full(n, 1.0 / max(n, 1), np.float32),
+            "box": {"lo": np.zeros(3, np.float32), "hi": np.ones(3, np.float32),
+                    "periodic": np.array([per] * 3, np.int32)}, "kind": 1, "support": 2.0}
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 63, 64, 65, 130, 4097])
+@pytest.mark.parametrize("cluster", [4, 8, 16])
+def test_small_and_ragged_sizes(n, cluster):
+    d = _tiny(n, seed=n, h=0.2 if n < 100 else 0.05)
+    o = oracle_sorted(d)
+    g_off, g_idx, p_off, p_idx = full_reference(o, d)
+    L, t = gpu_build(d, cluster=cluster, bucket=8)
+    nsc = L.sizes()["n_superclusters"]
+    compare_records(L, o, d, cluster, 1, np.arange(nsc), np.arange(n), p_off, p_idx)
+    rho = gpu_density(L, t, n)[o["perm"]]
+    want = orc.density(o["xs"], o["ys"], o["zs"], o["hs"], o["ms"], d["box"], g_off, g_idx,
+                       np.arange(n))
+    assert (np.abs(rho - want) / want).max() <= DENSITY_RTOL
+    L.free()
+
+
+def test_coincident_particles_and_box_faces():
+    """Equal keys beyond the leaf bucket (level-21 leaves), particles on the
+    box faces of a periodic box, and pairs across the periodic wrap."""
+    n = 300
+    d = _tiny(n, seed=5, h=0.03)
+    d["x"][:100] = 0.5
+    d["y"][:100] = 0.5
+    d["z"][:100] = 0.5
+    d["x"][100:110] = 0.0
+    d["x"][110:120] = 1.0
+    d["y"][120:130] = np.float32(0.999)
+    d["y"][130:140] = np.float32(0.001)
+    o = oracle_sorted(d)
+    g_off, g_idx, p_off, p_idx = full_reference(o, d)
+    L, t = gpu_build(d, bucket=8)
+    tree = L.octree()
+    ref = orc.octree(o["keys"], 8)
+    assert np.array_equal(tree["end"], ref["end"]) and ref["level"].max() == 21
+    compare_records(L, o, d, 8, 1, np.arange(L.sizes()["n_superclusters"]), np.arange(n), p_off, p_idx)
+    cnt = gpu_counts(L, n)[o["perm"]]
+    assert np.array_equal(cnt, np.diff(g_off))
+    assert cnt[np.argsort(o["perm"])][:100].min() >= 99
+    L.free()
+
+
+def test_invalid_inputs_are_rejected():
+    import torch
+    d = _tiny(200, seed=9)
+    base = {k: d[k].copy() for k in ("x", "y", "z", "h", "m")}
+
+    def run(mod=None, box=None, cluster=8, h=None):
+        dd = dict(d)
+        for k in base:
+            dd[k] = base[k].copy()
+        if mod:
+            mod(dd)
+        if box is not None:
+            dd["box"] = box
+        from nlcheck import to_dev
+        t = to_dev(dd)
+        p = nl.make_params(key=1, cluster=cluster, support=2.0)
+        with pytest.raises(nl.NLError) as e:
+            nl.NeighborList().build(t["x"], t["y"], t["z"], t["h"], dd["box"], p)
+        return e.value.status
+
+    def nan_x(dd):
+        dd["x"][7] = np.nan
+
+    def out_of_box(dd):
+        dd["y"][3] = 1.5
+
+    def zero_h(dd):
+        dd["h"][11] = 0.0
+
+    def big_h(dd):
+        dd["h"][0] = 0.26     # 2h = 0.52 >= L/2 on a periodic axis
+
+    assert run(nan_x) == 1
+    assert run(out_of_box) == 1
+    assert run(zero_h) == 1
+    assert run(big_h) == 2
+    assert run(cluster=6) == 1
+    # a good build on the same process still works afterwards
+    o = oracle_sorted(d)
+    L, t = gpu_build(d)
+    keys, perm = L.sorted()
+    assert np.array_equal(keys, o["keys"])
+    L.free()
