@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -86,6 +87,7 @@ struct nl_list {
     int any_per = 0;
     unsigned long long list_bytes = 0, n_entries = 0, n_tiles = 0;
     uint32_t stage_cap = kStageCap0;
+    int stage_grown = 0;
     DevBuf keys, keys_alt, vals, vals_alt, hist, pos, clo, chi, lcp, lev, leaf_first, leaf_lev,
         nodeoff, bsum;
     DevBuf nlo, nhi, nrng, nlevel, nparent, nchild, narrive;
@@ -275,12 +277,17 @@ nl_status do_build(nl_list *nl, const float *x, const float *y, const float *z, 
 
     CK(cudaMemsetAsync(dst, 0, sizeof(Status), s));
     // 5. cluster-pair search + encoding, with redo rounds for overflows
-    const size_t est = (size_t)N * (p->compress ? 6 : 20) + 4096;
+    size_t est = (size_t)N * (p->compress ? 12 : 48) + 65536;
+    // test knobs: start from tiny buffers to exercise the overflow rounds
+    if (const char *e = std::getenv("NLGB_LIST_CAP0")) est = std::strtoull(e, nullptr, 10) + 8;
+    if (const char *e = std::getenv("NLGB_STAGE_CAP0"))
+        if (!nl->stage_grown) nl->stage_cap = (uint32_t)std::strtoul(e, nullptr, 10);
     if (nl->list.cap < est) CK(nl->list.ensure(est));
     int grid = nl->num_sms * kSearchBlocksPerSM;
     size_t slots = (size_t)grid * 8;
     CK(nl->stageJ.ensure(slots * nl->stage_cap * 4));
     CK(nl->stageM.ensure(slots * nl->stage_cap));
+    CK(cudaMemsetAsync(&dst->fail_off, 0xff, sizeof(dst->fail_off), s));
     CK(nl->mark(4, s));
 
     SearchArgs sa{};
@@ -326,12 +333,13 @@ nl_status do_build(nl_list *nl, const float *x, const float *y, const float *z, 
         slots = (size_t)grid * 8;
         if (nl->hst->max_count > nl->stage_cap) {
             nl->stage_cap = nl->hst->max_count + nl->hst->max_count / 4 + 64;
+            nl->stage_grown = 1;
         }
         CK(nl->stageJ.ensure(slots * nl->stage_cap * 4));
         CK(nl->stageM.ensure(slots * nl->stage_cap));
         unsigned long long keep = used;
         if (nl->hst->list_overflow) {
-            keep = nl->list.cap - 8;
+            keep = nl->hst->fail_off;
             size_t ncap = std::max((size_t)nl->list.cap * 2, (size_t)(used + used / 2 + 4096));
             DevBuf bigger;
             CK(bigger.ensure(ncap));
@@ -343,6 +351,7 @@ nl_status do_build(nl_list *nl, const float *x, const float *y, const float *z, 
         }
         std::memset(nl->hst, 0, sizeof(Status));
         nl->hst->list_used = keep;
+        nl->hst->fail_off = ~0ull;
         CK(cudaMemcpyAsync(dst, nl->hst, sizeof(Status), cudaMemcpyHostToDevice, s));
     }
     CK(nl->mark(5, s));

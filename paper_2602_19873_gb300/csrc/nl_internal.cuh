@@ -34,7 +34,8 @@ struct Status {
     unsigned long long n_entries;
     unsigned long long n_tiles;
     unsigned int pass_ticket;
-    unsigned int pad[3];
+    unsigned int pad;
+    unsigned long long fail_off;   // lowest failed list reservation (host sets ~0 first)
 };
 
 // ---------------------------------------------------------------------------

@@ -63,7 +63,12 @@ __device__ bool encode_record(uint32_t cnt, const uint32_t *stJ, const uint8_t *
     unsigned long long off = 0;
     if (lane == 0) off = atomicAdd(&a.st->list_used, (unsigned long long)words * 4ull);
     off = __shfl_sync(0xffffffffu, off, 0);
-    if (off + (unsigned long long)words * 4ull > a.list_cap) return false;
+    if (off + (unsigned long long)words * 4ull > a.list_cap) {
+        // reservations only grow, so every record below the lowest failed
+        // offset was stored; the host resumes allocation there
+        if (lane == 0) atomicMin(&a.st->fail_off, off);
+        return false;
+    }
     uint32_t *rec = reinterpret_cast<uint32_t *>(a.list + off);
     if (lane == 0) {
         rec[0] = cnt;

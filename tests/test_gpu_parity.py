@@ -218,3 +218,21 @@ def test_invalid_inputs_are_rejected():
     keys, perm = L.sorted()
     assert np.array_equal(keys, o["keys"])
     L.free()
+
+
+def test_overflow_rounds_keep_records_exact(cases, monkeypatch):
+    """Tiny initial staging and list buffers force the redo rounds (staging
+    growth and list-buffer growth); records stay byte-exact with no holes."""
+    d, o, (g_off, g_idx, p_off, p_idx) = cases["evrard"]
+    monkeypatch.setenv("NLGB_STAGE_CAP0", "40")
+    monkeypatch.setenv("NLGB_LIST_CAP0", "20000")
+    L, t = gpu_build(d)
+    n = len(o["xs"])
+    nsc = L.sizes()["n_superclusters"]
+    total, so, J, m = compare_records(L, o, d, 8, 1, np.arange(nsc), np.arange(n), p_off, p_idx)
+    assert L.sizes()["list_bytes"] == total
+    rho = gpu_density(L, t, n)[o["perm"]]
+    want = orc.density(o["xs"], o["ys"], o["zs"], o["hs"], o["ms"], d["box"], g_off, g_idx,
+                       np.arange(n))
+    assert (np.abs(rho - want) / want).max() <= DENSITY_RTOL
+    L.free()
