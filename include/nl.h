@@ -165,6 +165,35 @@ nl_status nl_get_stage_times(const nl_list *nl, float *ms, int32_t cap, int32_t 
  * nl_density_from_host. */
 nl_status nl_create(nl_list **out);
 
+/* Smoothing-length iteration (not in the paper; the workloads need
+ * per-particle h at a target neighbor count).  Finds for every particle an h
+ * with |#{j != i : d2 < (support*h)^2} - n_target| <= tol, counting with the
+ * canonical FP32 distance.  Counts come from neighbor lists built at search
+ * radius (1 + margin) * support * h; a list is rebuilt only when an h
+ * outgrows it.  Update per particle: bracket the window, step
+ * h * (n_target / count)^(1/3) clamped to [1/2, 2] while one side is open,
+ * then bisect the bracket in h^3.
+ *   start = NL_HSTART_GIVEN: h (device, caller order) holds the initial guess;
+ *   start = NL_HSTART_PLAIN: the initial guess is computed per super-cluster
+ *           from its bounding-box volume, h = 0.5 (3 n_target V / (4 pi count))^(1/3),
+ *           and h's input values are ignored.
+ * On return h holds the iterated values (caller order) and, if converged is
+ * not NULL, converged[i] (device, caller order) is 1 for particles inside the
+ * window.  Returns NL_ERR_NOT_CONVERGED when max_iter passes leave particles
+ * outside (h and flags are still written).  The list is left built at the
+ * search radius: rebuild with the returned h before running passes.
+ * Synchronises `stream` once per iteration. */
+enum { NL_HSTART_GIVEN = 0, NL_HSTART_PLAIN = 1 };
+typedef struct {
+    int32_t iterations;   /* count passes run */
+    int32_t rebuilds;     /* list searches run */
+    int64_t unconverged;  /* particles outside the window at return */
+} nl_hiter_info;
+nl_status nl_iterate_h(nl_list *nl, const float *x, const float *y, const float *z, float *h,
+                       int64_t n, const nl_box *box, const nl_params *p, float n_target, float tol,
+                       int32_t max_iter, float margin, int32_t start, uint8_t *converged,
+                       nl_hiter_info *info, void *stream);
+
 /* Thread-local description of the last error (never NULL). */
 const char *nl_last_error(void);
 

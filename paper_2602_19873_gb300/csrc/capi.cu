@@ -88,6 +88,7 @@ struct nl_list {
     unsigned long long list_bytes = 0, n_entries = 0, n_tiles = 0;
     uint32_t stage_cap = kStageCap0;
     int stage_grown = 0;
+    int64_t n_prepared = 0;
     DevBuf keys, keys_alt, vals, vals_alt, hist, pos, clo, chi, lcp, lev, leaf_first, leaf_lev,
         nodeoff, bsum;
     DevBuf nlo, nhi, nrng, nlevel, nparent, nchild, narrive;
@@ -100,6 +101,8 @@ struct nl_list {
     float stage_ms[kStages] = {};
     // device copies of host inputs for nl_density_from_host
     DevBuf hx, hy, hz, hh, hm, hrho;
+    // h iteration state (sorted order)
+    DevBuf it_hq, it_hlo, it_hhi, it_hs, it_counts, it_conv, it_aflag, it_alist, it_words, it_tmp;
 
     cudaError_t mark(int k, cudaStream_t s)
     {
@@ -123,7 +126,9 @@ struct nl_list {
         DevBuf *all[] = {&keys, &keys_alt, &vals, &vals_alt, &hist, &pos, &clo, &chi, &lcp, &lev,
                          &leaf_first, &leaf_lev, &nodeoff, &bsum, &nlo, &nhi, &nrng, &nlevel,
                          &nparent, &nchild, &narrive, &stageJ, &stageM, &list, &rec_off, &redo,
-                         &work, &aux, &status, &hx, &hy, &hz, &hh, &hm, &hrho};
+                         &work, &aux, &status, &hx, &hy, &hz, &hh, &hm, &hrho, &it_hq,
+                         &it_hlo, &it_hhi, &it_hs, &it_counts, &it_conv, &it_aflag, &it_alist,
+                         &it_words, &it_tmp};
         for (DevBuf *b : all) b->release();
         for (int i = 0; i <= kStages; ++i)
             if (ev[i]) cudaEventDestroy(ev[i]);
@@ -179,8 +184,8 @@ nl_status read_status(nl_list *nl, cudaStream_t s)
     return NL_OK;
 }
 
-nl_status do_build(nl_list *nl, const float *x, const float *y, const float *z, const float *h,
-                   int64_t n, const nl_box *box, const nl_params *p, cudaStream_t s)
+nl_status do_prep(nl_list *nl, const float *x, const float *y, const float *z, const float *h,
+                  int64_t n, const nl_box *box, const nl_params *p, cudaStream_t s)
 {
     if (!x || !y || !z || !h) return fail(NL_ERR_ARG, "NULL particle array");
     if (n < 1) return fail(NL_ERR_ARG, "n must be >= 1 (got %lld)", (long long)n);
@@ -274,9 +279,25 @@ nl_status do_build(nl_list *nl, const float *x, const float *y, const float *z, 
     CK(octree_emit(nl->keys.as<uint64_t>(), N, nleaves, nnodes, nl->leaf_first.as<uint32_t>(),
                    nl->leaf_lev.as<uint8_t>(), nl->nodeoff.as<uint32_t>(), nl->pos.as<float4>(),
                    p->support, oo, s));
+    nl->npad = npad;
+    nl->ncl = ncl;
+    nl->nsc = nsc;
+    nl->n_leaves = nleaves;
+    nl->n_nodes = nnodes;
+    nl->n_prepared = n;
+    return NL_OK;
+}
 
+// Cluster-pair search + encoding over the prepared structures, with redo
+// rounds for overflows.  Sets nl->n on success.
+nl_status do_search(nl_list *nl, cudaStream_t s)
+{
+    nl_status st;
+    const nl_params *p = &nl->p;
+    const uint32_t N = (uint32_t)nl->n_prepared, nsc = nl->nsc, nnodes = nl->n_nodes;
+    const int M = p->cluster;
+    Status *dst = nl->status.as<Status>();
     CK(cudaMemsetAsync(dst, 0, sizeof(Status), s));
-    // 5. cluster-pair search + encoding, with redo rounds for overflows
     size_t est = (size_t)N * (p->compress ? 12 : 48) + 65536;
     // test knobs: start from tiny buffers to exercise the overflow rounds
     if (const char *e = std::getenv("NLGB_LIST_CAP0")) est = std::strtoull(e, nullptr, 10) + 8;
@@ -356,16 +377,19 @@ nl_status do_build(nl_list *nl, const float *x, const float *y, const float *z, 
     }
     CK(nl->mark(5, s));
     nl->collect(0, 5);
-    nl->n = n;
-    nl->npad = npad;
-    nl->ncl = ncl;
-    nl->nsc = nsc;
-    nl->n_leaves = nleaves;
-    nl->n_nodes = nnodes;
+    nl->n = nl->n_prepared;
     nl->list_bytes = used;
     nl->n_entries = entries;
     nl->n_tiles = tiles;
     return NL_OK;
+}
+
+nl_status do_build(nl_list *nl, const float *x, const float *y, const float *z, const float *h,
+                   int64_t n, const nl_box *box, const nl_params *p, cudaStream_t s)
+{
+    nl_status st = do_prep(nl, x, y, z, h, n, box, p, s);
+    if (st != NL_OK) return st;
+    return do_search(nl, s);
 }
 
 nl_status check_list(const nl_list *nl)
@@ -487,6 +511,105 @@ nl_status nl_density_from_host(nl_list *nl, const float *x, const float *y, cons
     if (st != NL_OK) return st;
     CK(cudaMemcpyAsync(rho, nl->hrho.p, b, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    return NL_OK;
+}
+
+nl_status nl_iterate_h(nl_list *nl, const float *x, const float *y, const float *z, float *h,
+                       int64_t n, const nl_box *box, const nl_params *p, float n_target, float tol,
+                       int32_t max_iter, float margin, int32_t start, uint8_t *converged,
+                       nl_hiter_info *info, void *stream)
+{
+    if (!nl) return fail(NL_ERR_ARG, "list is NULL");
+    if (!h) return fail(NL_ERR_ARG, "h is NULL");
+    if (!(n_target >= 1.f) || !(tol >= 0.f) || max_iter < 1 || !(margin >= 0.f) || !(margin < 4.f))
+        return fail(NL_ERR_ARG, "need n_target >= 1, tol >= 0, max_iter >= 1, 0 <= margin < 4");
+    if (start != NL_HSTART_GIVEN && start != NL_HSTART_PLAIN)
+        return fail(NL_ERR_ARG, "unknown start %d", start);
+    if (n < 1 || n > (int64_t)1 << 30) return fail(NL_ERR_ARG, "bad n %lld", (long long)n);
+    cudaStream_t s = (cudaStream_t)stream;
+    nl->n = 0;
+    const uint32_t N = (uint32_t)n;
+    const float *hin = h;
+    if (start != NL_HSTART_GIVEN) {
+        CK(nl->it_tmp.ensure((size_t)N * 4));
+        CK(launch_fill(nl->it_tmp.as<float>(), N, 1e-30f, s));
+        hin = nl->it_tmp.as<float>();
+    }
+    nl_status st = do_prep(nl, x, y, z, hin, n, box, p, s);
+    if (st != NL_OK) return st;
+    const int M = p->cluster;
+    const uint32_t nsc = nl->nsc;
+    CK(nl->it_hq.ensure((size_t)N * 4));
+    CK(nl->it_hlo.ensure((size_t)N * 4));
+    CK(nl->it_hhi.ensure((size_t)N * 4));
+    CK(nl->it_hs.ensure((size_t)N * 4));
+    CK(nl->it_counts.ensure((size_t)N * 4));
+    CK(nl->it_conv.ensure((size_t)N));
+    CK(nl->it_aflag.ensure((size_t)nsc * 4));
+    CK(nl->it_alist.ensure((size_t)nsc * 4));
+    CK(nl->it_words.ensure(16));
+    HIterState hs{nl->it_hq.as<float>(), nl->it_hlo.as<float>(), nl->it_hhi.as<float>(),
+                  nl->it_hs.as<float>(), nl->it_counts.as<uint32_t>(), nl->it_conv.as<uint8_t>(),
+                  nl->it_aflag.as<uint32_t>(), nl->it_alist.as<uint32_t>(),
+                  nl->it_words.as<unsigned int>()};
+    if (start == NL_HSTART_GIVEN)
+        CK(launch_pos_h_to(N, nl->pos.as<float4>(), hs.hq, s));
+    else
+        CK(launch_plain_h0(N, nsc, M, nl->clo.as<float4>(), nl->chi.as<float4>(), n_target, hs.hq, s));
+    CK(cudaMemsetAsync(hs.hlo, 0, (size_t)N * 4, s));
+    CK(launch_fill(hs.hhi, N, INFINITY, s));
+    CK(cudaMemsetAsync(hs.conv, 0, (size_t)N, s));
+    CK(cudaMemsetAsync(hs.active_flag, 0, (size_t)nsc * 4, s));
+    // largest h whose search radius stays below half a periodic box length
+    float hcap = 3.0e38f;
+    for (int a = 0; a < 3; ++a)
+        if (box->periodic[a]) hcap = std::min(hcap, nl->dbox.half[a] / (p->support * (1.f + margin)) * 0.999999f);
+    OctreeOut oo{nl->nlo.as<float4>(), nl->nhi.as<float4>(), nl->nrng.as<int2>(),
+                 nl->nlevel.as<uint8_t>(), nl->nparent.as<int32_t>(), nl->nchild.as<uint32_t>(),
+                 nl->narrive.as<uint32_t>()};
+    bool rebuild = true, first = true;
+    int iters = 0, rebuilds = 0;
+    unsigned int words[4] = {0, 0, 0, 0};
+    for (; iters < max_iter;) {
+        if (rebuild) {
+            CK(launch_hsearch(N, hs.hq, margin, hcap, hs.hs, s));
+            CK(launch_pos_h(N, hs.hs, nl->pos.as<float4>(), s));
+            CK(launch_cluster_boxes(nl->npad, M, nl->pos.as<float4>(), p->support,
+                                    nl->clo.as<float4>(), nl->chi.as<float4>(), s));
+            CK(octree_boxes(nl->n_nodes, nl->pos.as<float4>(), p->support, oo, s));
+            st = do_search(nl, s);
+            if (st != NL_OK) return st;
+            ++rebuilds;
+        }
+        PassArgs a = pass_args(nl);
+        a.outc = hs.counts;
+        a.hq = hs.hq;
+        a.sorted_out = 1;
+        if (!first) {
+            a.work = hs.active_list;
+            a.nwork = words[2];
+        }
+        CK(launch_pass(a, PASS_COUNT, M, nl->any_per, nl->num_sms, s));
+        ++iters;
+        first = false;
+        CK(cudaMemsetAsync(hs.words, 0, 16, s));
+        CK(launch_hupdate(N, M, n_target, tol, hcap, hs, s));
+        CK(launch_active_list(nsc, hs, s));
+        CK(cudaMemcpyAsync(words, hs.words, 16, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (words[0] == 0) break;
+        rebuild = words[1] != 0;
+    }
+    CK(launch_scatter_h(N, nl->vals.as<uint32_t>(), hs.hq, hs.conv, h, converged, s));
+    CK(cudaStreamSynchronize(s));
+    if (info) {
+        info->iterations = iters;
+        info->rebuilds = rebuilds;
+        info->unconverged = words[0];
+    }
+    if (words[0] != 0)
+        return fail(NL_ERR_NOT_CONVERGED, "%u particles outside the neighbor window after %d passes",
+                    words[0], iters);
     return NL_OK;
 }
 

@@ -322,6 +322,10 @@ struct PassArgs {
     float *out0, *out1, *out2;
     uint32_t *outc;
     Status *st;
+    const float *hq;         // optional query h per sorted particle (count pass)
+    int sorted_out;          // write outputs at the sorted index instead of perm[i]
+    const uint32_t *work;    // optional list of super-clusters to process
+    uint32_t nwork;
 };
 cudaError_t launch_pass(const PassArgs &a, int kind, int M, int any_periodic, int num_sms,
                         cudaStream_t s);
@@ -329,5 +333,33 @@ cudaError_t launch_pass(const PassArgs &a, int kind, int M, int any_periodic, in
 cudaError_t launch_gather_aux(uint32_t n, uint32_t npad, const uint32_t *perm, const float *a,
                               const float *b, const float *c, int mode, float2 *aux,
                               cudaStream_t s);
+
+// Octree node boxes only (topology unchanged), e.g. after new radii.
+cudaError_t octree_boxes(uint32_t n_nodes, const float4 *pos, float support, const OctreeOut &o,
+                         cudaStream_t s);
+
+// h iteration helpers (hiter.cu); all arrays in SFC-sorted order.
+cudaError_t launch_fill(float *a, uint32_t n, float v, cudaStream_t s);
+cudaError_t launch_pos_h(uint32_t n, const float *hs, float4 *pos, cudaStream_t s);
+cudaError_t launch_pos_h_to(uint32_t n, const float4 *pos, float *hq, cudaStream_t s);
+cudaError_t launch_cluster_boxes(uint32_t npad, int M, const float4 *pos, float support,
+                                 float4 *clo, float4 *chi, cudaStream_t s);
+cudaError_t launch_plain_h0(uint32_t n, uint32_t nsc, int M, const float4 *clo, const float4 *chi,
+                            float n_target, float *hq, cudaStream_t s);
+cudaError_t launch_hsearch(uint32_t n, const float *hq, float margin, float hcap, float *hs,
+                           cudaStream_t s);
+struct HIterState {
+    float *hq, *hlo, *hhi, *hs;
+    uint32_t *counts;
+    uint8_t *conv;
+    uint32_t *active_flag;   // per super-cluster
+    uint32_t *active_list;
+    unsigned int *words;     // [0] unconverged, [1] rebuild needed, [2] active count
+};
+cudaError_t launch_hupdate(uint32_t n, int M, float n_target, float tol, float hcap,
+                           const HIterState &h, cudaStream_t s);
+cudaError_t launch_active_list(uint32_t nsc, const HIterState &h, cudaStream_t s);
+cudaError_t launch_scatter_h(uint32_t n, const uint32_t *perm, const float *hq, const uint8_t *conv,
+                             float *h_out, uint8_t *conv_out, cudaStream_t s);
 
 }  // namespace nlg

@@ -417,4 +417,13 @@ cudaError_t octree_emit(const uint64_t *keys, uint32_t n, uint32_t n_leaves, uin
     return cudaGetLastError();
 }
 
+cudaError_t octree_boxes(uint32_t n_nodes, const float4 *pos, float support, const OctreeOut &o,
+                         cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(o.narrive, 0, (size_t)n_nodes * 4, s);
+    if (e != cudaSuccess) return e;
+    k_node_boxes<<<(n_nodes + 127) / 128, 128, 0, s>>>(n_nodes, pos, support, o);
+    return cudaGetLastError();
+}
+
 }  // namespace nlg

@@ -68,7 +68,8 @@ __global__ void __launch_bounds__(PS_THREADS) k_pass(PassArgs a)
         uint32_t s = 0;
         if (lane == 0) s = atomicAdd(&a.st->pass_ticket, 1u);
         s = __shfl_sync(0xffffffffu, s, 0);
-        if (s >= a.nsc) break;
+        if (s >= (a.work ? a.nwork : a.nsc)) break;
+        if (a.work) s = a.work[s];
 
         float4 pi[kSC];
         float ri2[kSC], hinv[kSC], ci[kSC], ri[kSC];
@@ -76,7 +77,7 @@ __global__ void __launch_bounds__(PS_THREADS) k_pass(PassArgs a)
         for (int k = 0; k < kSC; ++k) {
             uint32_t i = (s * kSC + k) * M + II;
             pi[k] = a.pos[i];
-            float r = __fmul_rn(a.support, pi[k].w);
+            float r = __fmul_rn(a.support, (KIND == PASS_COUNT && a.hq) ? a.hq[i] : pi[k].w);
             ri[k] = r;
             ri2[k] = __fmul_rn(r, r);
             hinv[k] = 1.f / pi[k].w;
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(PS_THREADS) k_pass(PassArgs a)
             if ((uint32_t)k % G != g) continue;
             const uint32_t i = (s * kSC + k) * M + II;
             if (i >= a.n) continue;
-            const uint32_t o = a.perm[i];
+            const uint32_t o = a.sorted_out ? i : a.perm[i];
             if constexpr (KIND == PASS_DENSITY) {
                 float self = a.aux[i].x;  // m_i w(0) = m_i
                 a.out0[o] = (acc.v[k] + self) * (0.318309886183790672f * hinv[k] * hinv[k] * hinv[k]);

@@ -63,7 +63,15 @@ _SIGS = {
     "nl_set_profiling": (C.c_int, [P, C.c_int32]),
     "nl_get_stage_times": (C.c_int, [P, P, C.c_int32, P]),
     "nl_density_from_host": (C.c_int, [P, P, P, P, P, P, C.c_int64, P, P, P, P]),
+    "nl_iterate_h": (C.c_int, [P, P, P, P, P, C.c_int64, P, P, C.c_float, C.c_float, C.c_int32,
+                               C.c_float, C.c_int32, P, P, P]),
 }
+
+NL_HSTART_GIVEN, NL_HSTART_PLAIN = 0, 1
+
+
+class nl_hiter_info(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("rebuilds", C.c_int32), ("unconverged", C.c_int64)]
 
 STAGES = ["keys", "sort", "permute", "octree", "search", "pass_gather", "pass"]
 
@@ -180,6 +188,23 @@ class NeighborList:
         _check(load().nl_density_from_host(self.handle, *[a.ctypes.data for a in arrs],
                                            len(arrs[0]), C.byref(b), C.byref(params),
                                            rho.ctypes.data, _stream(stream)))
+
+    def iterate_h(self, x, y, z, h, box, params, n_target, tol=2.0, max_iter=40, margin=0.15,
+                  start=NL_HSTART_PLAIN, converged=None, stream=None, check=True):
+        """h: float32 CUDA tensor (in/out, caller order).  Returns the info
+        dict; raises NLError on failure (NL_ERR_NOT_CONVERGED when check)."""
+        self.ensure_handle()
+        b = make_box(box) if isinstance(box, dict) else box
+        info = nl_hiter_info()
+        st = load().nl_iterate_h(self.handle, _ptr(x), _ptr(y), _ptr(z), _ptr(h), int(x.numel()),
+                                 C.byref(b), C.byref(params), float(n_target), float(tol),
+                                 int(max_iter), float(margin), int(start), _ptr(converged),
+                                 C.byref(info), _stream(stream))
+        out = {"iterations": info.iterations, "rebuilds": info.rebuilds,
+               "unconverged": info.unconverged, "status": st}
+        if st != NL_OK and (check or st != 6):
+            _check(st)
+        return out
 
     def density_pass(self, m, rho, stream=None):
         _check(load().nl_density_pass(self.handle, _ptr(m), _ptr(rho), _stream(stream)))
