@@ -115,6 +115,20 @@ __device__ __forceinline__ bool boxes_near(const float4 &alo, const float4 &ahi,
     return d2 <= __fmul_rn(r, r);
 }
 
+// Could particle (x, radius r) be a symmetric neighbor of a particle inside
+// box B (blo.w = largest radius in B)?  Same monotone rounding as above.
+template <bool PER>
+__device__ __forceinline__ bool point_near(const float4 &p, float r, const float4 &blo,
+                                           const float4 &bhi, const DevBox &b)
+{
+    float gx = axis_gap(p.x, p.x, blo.x, bhi.x, b.len[0], PER ? b.per[0] : 0);
+    float gy = axis_gap(p.y, p.y, blo.y, bhi.y, b.len[1], PER ? b.per[1] : 0);
+    float gz = axis_gap(p.z, p.z, blo.z, bhi.z, b.len[2], PER ? b.per[2] : 0);
+    float d2 = __fadd_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)), __fmul_rn(gz, gz));
+    float rr = fmaxf(r, blo.w);
+    return d2 <= __fmul_rn(rr, rr);
+}
+
 // ---------------------------------------------------------------------------
 // SFC keys
 // ---------------------------------------------------------------------------

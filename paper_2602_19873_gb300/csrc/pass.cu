@@ -1,258 +1,26 @@
-// Neighborhood passes over the compressed list (Sec. II-A: loop in parallel
-// over super-clusters, decode the list iteratively as needed, process each
-// cluster-cluster interaction; Sec. II-D: pure pair function + sum).
-//
-// One warp per super-cluster (atomic work counter, persistent grid).  The
-// warp decodes 32 differences at a time: the block mask is read at its
-// nibble offset with a funnel shift, each lane finds its info nibble by
-// popcount and its data nibbles by a warp scan of data lengths, and a warp
-// scan of the differences rebuilds the j-cluster indices.  For every decoded
-// (J, mask) entry the lanes hold one i particle of each of the 8 i-clusters
-// (lane % M) and 1..8 j particles of J, and accumulate per i-cluster in
-// registers; masked-off i-clusters cost nothing (warp-uniform branches).
-// The self pair is excluded on the fly by index (Sec. II-A).
+// Dispatch of the neighborhood passes (kernels in pass_impl.cuh, one
+// translation unit per pass kind) and the gather of pass inputs.
 #include "nl_internal.cuh"
 
 namespace nlg {
 
-constexpr int PS_THREADS = 256;
-constexpr int PS_BLOCKS_PER_SM = 4;
-
-__device__ __forceinline__ uint32_t get_nibble(const uint8_t *body, uint32_t p)
-{
-    uint32_t b = body[p >> 1];
-    return (p & 1u) ? (b >> 4) : (b & 0xfu);
-}
-
-// cubic spline shape w(q) (support q < 2) and its derivative
-__device__ __forceinline__ float spline_w(float q)
-{
-    float a = 2.f - q;
-    float outer = 0.25f * a * a * a;
-    float inner = 1.f - 1.5f * q * q + 0.75f * q * q * q;
-    return q < 1.f ? inner : (q < 2.f ? outer : 0.f);
-}
-
-__device__ __forceinline__ float spline_dw(float q)
-{
-    float a = 2.f - q;
-    float outer = -0.75f * a * a;
-    float inner = -3.f * q + 2.25f * q * q;
-    return q < 1.f ? inner : (q < 2.f ? outer : 0.f);
-}
-
-template <int KIND>
-struct Acc;
-template <>
-struct Acc<PASS_DENSITY> { float v[kSC]; };
-template <>
-struct Acc<PASS_COUNT> { uint32_t v[kSC]; };
-template <>
-struct Acc<PASS_SPH> { float x[kSC], y[kSC], z[kSC]; };
-template <>
-struct Acc<PASS_LJ> { float x[kSC], y[kSC], z[kSC]; };
-
-template <int M, bool PER, int KIND>
-__global__ void __launch_bounds__(PS_THREADS) k_pass(PassArgs a)
-{
-    constexpr int NP = (M * M) / 32 > 0 ? (M * M) / 32 : 1;
-    constexpr int JSTEP = 32 / M;
-    const unsigned lane = lane_id();
-    const unsigned lt = lanemask_lt();
-    const uint32_t II = lane % M;
-    const uint32_t JJ0 = (lane / M) % M;
-    // lanes that hold a distinct (i, j) pair; for M = 4 lanes 16..31 repeat
-    const bool owner = (M * M >= 32) || lane < (uint32_t)(M * M);
-
-    for (;;) {
-        uint32_t s = 0;
-        if (lane == 0) s = atomicAdd(&a.st->pass_ticket, 1u);
-        s = __shfl_sync(0xffffffffu, s, 0);
-        if (s >= (a.work ? a.nwork : a.nsc)) break;
-        if (a.work) s = a.work[s];
-
-        float4 pi[kSC];
-        float ri2[kSC], hinv[kSC], ci[kSC], ri[kSC];
-#pragma unroll
-        for (int k = 0; k < kSC; ++k) {
-            uint32_t i = (s * kSC + k) * M + II;
-            pi[k] = a.pos[i];
-            float r = __fmul_rn(a.support, (KIND == PASS_COUNT && a.hq) ? a.hq[i] : pi[k].w);
-            ri[k] = r;
-            ri2[k] = __fmul_rn(r, r);
-            hinv[k] = 1.f / pi[k].w;
-            ci[k] = (KIND == PASS_SPH) ? a.aux[i].y : 0.f;
-        }
-        Acc<KIND> acc;
-#pragma unroll
-        for (int k = 0; k < kSC; ++k) {
-            if constexpr (KIND == PASS_DENSITY || KIND == PASS_COUNT) {
-                acc.v[k] = 0;
-            } else {
-                acc.x[k] = 0.f; acc.y[k] = 0.f; acc.z[k] = 0.f;
-            }
-        }
-
-        const uint32_t *rec = reinterpret_cast<const uint32_t *>(a.list) + a.rec_off[s];
-        const uint32_t cnt = rec[0];
-        const uint8_t *masks = reinterpret_cast<const uint8_t *>(rec + 1);
-        const uint32_t *body = rec + 1 + ((cnt + 3u) >> 2);
-        const uint8_t *bodyb = reinterpret_cast<const uint8_t *>(body);
-        uint32_t pos = 0;
-        uint32_t prevJ = 0xffffffffu;
-
-        for (uint32_t b0 = 0; b0 < cnt; b0 += 32) {
-            const uint32_t t = b0 + lane;
-            const bool valid = t < cnt;
-            uint32_t J;
-            if (a.compress) {
-                const uint32_t w0 = body[pos >> 3];
-                const uint32_t w1 = (pos & 7u) ? body[(pos >> 3) + 1] : 0u;
-                const uint32_t bm = __funnelshift_r(w0, w1, (pos & 7u) * 4u);
-                const bool bit = (bm >> lane) & 1u;
-                const uint32_t nbits = __popc(bm);
-                uint32_t info = bit ? get_nibble(bodyb, pos + 8 + __popc(bm & lt)) : 0u;
-                uint32_t ndat = (bit && info < 8u) ? info + 1u : 0u;
-                uint32_t incl = warp_incl_scan(ndat);
-                uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
-                uint32_t pd = pos + 8 + nbits + incl - ndat;
-                uint32_t v = 0;
-                for (uint32_t q = 0; q < ndat; ++q) v = (v << 4) | get_nibble(bodyb, pd + q);
-                uint32_t d = !bit ? 1u : (info >= 8u ? info - 6u : v);
-                J = prevJ + warp_incl_scan(d);
-                pos += 8 + nbits + tot;
-            } else {
-                J = valid ? body[t] : 0u;
-            }
-            prevJ = __shfl_sync(0xffffffffu, J, 31);
-            const uint32_t mk = valid ? masks[t] : 0u;
-            const uint32_t nb = min(32u, cnt - b0);
-            for (uint32_t e = 0; e < nb; ++e) {
-                const uint32_t Je = __shfl_sync(0xffffffffu, J, e);
-                const uint32_t me = __shfl_sync(0xffffffffu, mk, e);
-#pragma unroll
-                for (int tt = 0; tt < NP; ++tt) {
-                    const uint32_t jj = Je * M + JJ0 + tt * JSTEP;
-                    const float4 pj = a.pos[jj];
-                    float2 aj = make_float2(0.f, 0.f);
-                    if constexpr (KIND == PASS_DENSITY || KIND == PASS_SPH) aj = a.aux[jj];
-#pragma unroll
-                    for (int k = 0; k < kSC; ++k) {
-                        if (!((me >> k) & 1u)) continue;
-                        const uint32_t ii = (s * kSC + k) * M + II;
-                        const float3 dv = pair_dx<PER>(pi[k], pj, a.box);
-                        const float d2 = d2_of(dv);
-                        if constexpr (KIND == PASS_DENSITY) {
-                            if (owner && ii != jj && d2 < ri2[k]) {
-                                float q = sqrtf(d2) * hinv[k];
-                                acc.v[k] += aj.x * spline_w(q);
-                            }
-                        } else if constexpr (KIND == PASS_COUNT) {
-                            if (owner && ii != jj && d2 < ri2[k]) acc.v[k] += 1u;
-                        } else if constexpr (KIND == PASS_SPH) {
-                            const float rj = __fmul_rn(a.support, pj.w);
-                            const float rr = fmaxf(ri[k], rj);
-                            if (owner && ii != jj && d2 < __fmul_rn(rr, rr)) {
-                                // a_i -= m_j (c_i gW_i + c_j gW_j) (x_i - x_j) / r
-                                float r = sqrtf(d2);
-                                float hj = pj.w, hji = 1.f / hj;
-                                float gi = spline_dw(r * hinv[k]) * hinv[k] * hinv[k] * hinv[k] * hinv[k];
-                                float gj = spline_dw(r * hji) * hji * hji * hji * hji;
-                                float sc = aj.x * (ci[k] * gi + aj.y * gj) * 0.318309886183790672f / r;
-                                // x_i - x_j = -dv
-                                acc.x[k] += sc * dv.x;
-                                acc.y[k] += sc * dv.y;
-                                acc.z[k] += sc * dv.z;
-                            }
-                        } else {  // LJ: F_i += 24 eps (2 s^12/r^14 - s^6/r^8)(x_i - x_j)
-                            if (owner && ii != jj && d2 < ri2[k]) {
-                                float ir2 = 1.f / d2;
-                                float s2 = a.p1 * a.p1 * ir2;
-                                float s6 = s2 * s2 * s2;
-                                float c = 24.f * a.p0 * ir2 * s6 * (2.f * s6 - 1.f);
-                                acc.x[k] -= c * dv.x;
-                                acc.y[k] -= c * dv.y;
-                                acc.z[k] -= c * dv.z;
-                            }
-                        }
-                    }
-                }
-            }
-        }
-
-        // combine lanes holding the same i particle, write in caller order
-#pragma unroll
-        for (int k = 0; k < kSC; ++k) {
-#pragma unroll
-            for (int o = M; o < 32; o <<= 1) {
-                if constexpr (KIND == PASS_DENSITY || KIND == PASS_COUNT) {
-                    acc.v[k] += __shfl_xor_sync(0xffffffffu, acc.v[k], o);
-                } else {
-                    acc.x[k] += __shfl_xor_sync(0xffffffffu, acc.x[k], o);
-                    acc.y[k] += __shfl_xor_sync(0xffffffffu, acc.y[k], o);
-                    acc.z[k] += __shfl_xor_sync(0xffffffffu, acc.z[k], o);
-                }
-            }
-        }
-        // lane (II, g) with g = lane / M writes the i-clusters k = g (mod 32/M)
-        constexpr uint32_t G = 32 / M;
-        const uint32_t g = lane / M;
-#pragma unroll
-        for (int k = 0; k < kSC; ++k) {
-            if ((uint32_t)k % G != g) continue;
-            const uint32_t i = (s * kSC + k) * M + II;
-            if (i >= a.n) continue;
-            const uint32_t o = a.sorted_out ? i : a.perm[i];
-            if constexpr (KIND == PASS_DENSITY) {
-                float self = a.aux[i].x;  // m_i w(0) = m_i
-                a.out0[o] = (acc.v[k] + self) * (0.318309886183790672f * hinv[k] * hinv[k] * hinv[k]);
-            } else if constexpr (KIND == PASS_COUNT) {
-                a.outc[o] = acc.v[k];
-            } else if constexpr (KIND == PASS_SPH) {
-                a.out0[o] = acc.x[k];
-                a.out1[o] = acc.y[k];
-                a.out2[o] = acc.z[k];
-            } else {
-                a.out0[o] = acc.x[k];
-                a.out1[o] = acc.y[k];
-                a.out2[o] = acc.z[k];
-            }
-        }
-    }
-}
-
-template <int M, int KIND>
-static void launch_mk(const PassArgs &a, int per, int grid, cudaStream_t s)
-{
-    if (per)
-        k_pass<M, true, KIND><<<grid, PS_THREADS, 0, s>>>(a);
-    else
-        k_pass<M, false, KIND><<<grid, PS_THREADS, 0, s>>>(a);
-}
-
-template <int KIND>
-static cudaError_t launch_k(const PassArgs &a, int M, int per, int grid, cudaStream_t s)
-{
-    switch (M) {
-    case 4: launch_mk<4, KIND>(a, per, grid, s); break;
-    case 8: launch_mk<8, KIND>(a, per, grid, s); break;
-    case 16: launch_mk<16, KIND>(a, per, grid, s); break;
-    default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
+constexpr int kPassBlocksPerSM = 4;
+cudaError_t launch_pass_density(const PassArgs &a, int M, int per, int grid, cudaStream_t s);
+cudaError_t launch_pass_count(const PassArgs &a, int M, int per, int grid, cudaStream_t s);
+cudaError_t launch_pass_sph(const PassArgs &a, int M, int per, int grid, cudaStream_t s);
+cudaError_t launch_pass_lj(const PassArgs &a, int M, int per, int grid, cudaStream_t s);
 
 cudaError_t launch_pass(const PassArgs &a, int kind, int M, int any_periodic, int num_sms,
                         cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(&a.st->pass_ticket, 0, 4, s);
     if (e != cudaSuccess) return e;
-    int grid = num_sms * PS_BLOCKS_PER_SM;
+    int grid = num_sms * kPassBlocksPerSM;
     switch (kind) {
-    case PASS_DENSITY: return launch_k<PASS_DENSITY>(a, M, any_periodic, grid, s);
-    case PASS_COUNT: return launch_k<PASS_COUNT>(a, M, any_periodic, grid, s);
-    case PASS_SPH: return launch_k<PASS_SPH>(a, M, any_periodic, grid, s);
-    case PASS_LJ: return launch_k<PASS_LJ>(a, M, any_periodic, grid, s);
+    case PASS_DENSITY: return launch_pass_density(a, M, any_periodic, grid, s);
+    case PASS_COUNT: return launch_pass_count(a, M, any_periodic, grid, s);
+    case PASS_SPH: return launch_pass_sph(a, M, any_periodic, grid, s);
+    case PASS_LJ: return launch_pass_lj(a, M, any_periodic, grid, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -1,0 +1,9 @@
+// Instantiation of the neighborhood pass kernel for PASS_SPH (see pass_impl.cuh).
+#include "pass_impl.cuh"
+
+namespace nlg {
+cudaError_t launch_pass_sph(const PassArgs &a, int M, int per, int grid, cudaStream_t s)
+{
+    return launch_k<PASS_SPH>(a, M, per, grid, s);
+}
+}  // namespace nlg

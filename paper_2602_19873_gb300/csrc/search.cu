@@ -136,6 +136,8 @@ __global__ void __launch_bounds__(SR_THREADS) k_search(SearchArgs a, SearchCtl c
 {
     constexpr int NP = (M * M) / 32 > 0 ? (M * M) / 32 : 1;  // pairs per lane per tile
     constexpr int JSTEP = 32 / M;
+    constexpr int NPI = (kSC * M) / 32;   // i particles per lane for the pruning tests
+    constexpr int CPB = 32 / M;           // clusters covered by one 32-particle ballot
     __shared__ uint32_t wins[SR_WARPS][WIN_WORDS];
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
     uint32_t *win = wins[warp];
@@ -151,15 +153,25 @@ __global__ void __launch_bounds__(SR_THREADS) k_search(SearchArgs a, SearchCtl c
         tk = __shfl_sync(0xffffffffu, tk, 0);
         if (tk >= ctl.count) break;
         const uint32_t s = ctl.work ? ctl.work[tk] : tk;
+        const uint32_t base = s * kSC * M;
 
         // i-cluster box of this lane's cluster (lane & 7)
         const float4 ilo = a.clo[s * kSC + (lane & 7)];
         const float4 ihi = a.chi[s * kSC + (lane & 7)];
+        // pruning particles: base + lane + 32 t
+        float4 qp[NPI];
+        float qr[NPI];
+#pragma unroll
+        for (int t = 0; t < NPI; ++t) {
+            qp[t] = a.pos[base + lane + 32 * t];
+            qr[t] = __fmul_rn(a.support, qp[t].w);
+        }
+        // tile-test particles: lane's particle II of every i-cluster
         float4 pi[kSC];
         float ri[kSC];
 #pragma unroll
         for (int k = 0; k < kSC; ++k) {
-            pi[k] = a.pos[(s * kSC + k) * M + II];
+            pi[k] = a.pos[base + k * M + II];
             ri[k] = __fmul_rn(a.support, pi[k].w);
         }
 
@@ -170,7 +182,9 @@ __global__ void __launch_bounds__(SR_THREADS) k_search(SearchArgs a, SearchCtl c
             const float4 nlo = a.nlo[v];
             const float4 nhi = a.nhi[v];
             const uint32_t skip = (uint32_t)__float_as_int(nhi.w);
-            const bool near = boxes_near<PER>(ilo, ihi, nlo, nhi, a.box);
+            bool near = false;
+#pragma unroll
+            for (int t = 0; t < NPI; ++t) near |= point_near<PER>(qp[t], qr[t], nlo, nhi, a.box);
             if (!__any_sync(0xffffffffu, near)) {
                 v = skip > v ? skip : v + 1;  // always advances
                 continue;
@@ -183,14 +197,31 @@ __global__ void __launch_bounds__(SR_THREADS) k_search(SearchArgs a, SearchCtl c
             const int Jlo = max(rg.x / M, lastJ + 1);
             const int Jhi = (rg.y - 1) / M;
             for (int Jb = Jlo; Jb <= Jhi; Jb += 4) {
+                // round 1: 4 j-clusters x 8 i-cluster boxes, one per lane
                 const int Jl = Jb + (int)(lane >> 3);
                 bool cand = false;
                 if (Jl <= Jhi) cand = boxes_near<PER>(ilo, ihi, a.clo[Jl], a.chi[Jl], a.box);
                 const uint32_t bal = __ballot_sync(0xffffffffu, cand);
                 for (int q = 0; q < 4; ++q) {
-                    const uint32_t cm = (bal >> (8 * q)) & 0xffu;
+                    uint32_t cm = (bal >> (8 * q)) & 0xffu;
                     if (!cm) continue;
                     const int J = Jb + q;
+                    if (__popc(cm) > 1) {
+                        // round 2: every i particle against the j-cluster box
+                        const float4 jlo = a.clo[J], jhi = a.chi[J];
+                        uint32_t pm = 0;
+#pragma unroll
+                        for (int t = 0; t < NPI; ++t) {
+                            const uint32_t b = __ballot_sync(
+                                0xffffffffu, point_near<PER>(qp[t], qr[t], jlo, jhi, a.box));
+#pragma unroll
+                            for (int c = 0; c < CPB; ++c)
+                                if ((b >> (c * M)) & ((M == 32) ? 0xffffffffu : ((1u << M) - 1u)))
+                                    pm |= 1u << (t * CPB + c);
+                        }
+                        cm &= pm;
+                        if (!cm) continue;
+                    }
                     uint32_t mask = 0;
 #pragma unroll
                     for (int t = 0; t < NP; ++t) {
@@ -200,7 +231,7 @@ __global__ void __launch_bounds__(SR_THREADS) k_search(SearchArgs a, SearchCtl c
 #pragma unroll
                         for (int k = 0; k < kSC; ++k) {
                             if (!((cm >> k) & 1u) || ((mask >> k) & 1u)) continue;
-                            const uint32_t ii = (s * kSC + k) * M + II;
+                            const uint32_t ii = base + k * M + II;
                             const float d2 = pair_d2<PER>(pi[k], pj, a.box);
                             const float r = fmaxf(ri[k], rj);
                             const bool hit = (ii != jj) && d2 < __fmul_rn(r, r);
