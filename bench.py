@@ -99,10 +99,9 @@ def dist_init():
     return ws, rank, local
 
 
-def workload(seed):
+def workload(seed, n=N_FULL):
     from paper_2602_19873_gb300 import workloads as wl
-    return wl.cached(wl.plummer, "plummer64_%d_%d" % (N_FULL, seed), N_FULL, n_spheres=64,
-                     seed=seed)
+    return wl.cached(wl.plummer, "plummer64_%d_%d" % (n, seed), n, n_spheres=64, seed=seed)
 
 
 def converge_h(L, dev, d, params, start, stream):
@@ -127,7 +126,7 @@ def run_native(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    d = workload(4 + rank)
+    d = workload(4 + rank, args.n)
     n = len(d["x"])
     dev = {k: torch.from_numpy(d[k]).cuda() for k in ("x", "y", "z", "h", "m")}
     params = nl.make_params(key=d["kind"], cluster=8, support=d["support"], compress=1,
@@ -137,8 +136,15 @@ def run_native(args):
     # smoothing lengths at 200 +- 2 neighbors from the plain start (untimed
     # input preparation; the iteration is reported separately)
     H = nl.NeighborList()
-    converge_h(H, dev, d, params, nl.NL_HSTART_PLAIN, stream)       # warm-up
-    hconv, hinfo, hms = converge_h(H, dev, d, params, nl.NL_HSTART_PLAIN, stream)
+    hcache = os.path.join(__import__("tempfile").gettempdir(), "nlgb_workloads",
+                          "hconv_%d_%d.npy" % (n, 4 + rank))
+    if args.reuse_h and os.path.exists(hcache):
+        hconv = torch.from_numpy(np.load(hcache)).cuda()
+        hinfo, hms = {"iterations": None, "rebuilds": None, "unconverged": None}, None
+    else:
+        converge_h(H, dev, d, params, nl.NL_HSTART_PLAIN, stream)       # warm-up
+        hconv, hinfo, hms = converge_h(H, dev, d, params, nl.NL_HSTART_PLAIN, stream)
+        np.save(hcache, hconv.cpu().numpy())
     H.free()
     dev["h"] = hconv
     d["h"] = hconv.cpu().numpy()
@@ -181,13 +187,13 @@ def run_native(args):
     pin = {k: torch.from_numpy(d[k]).pin_memory().numpy() for k in ("x", "y", "z", "h", "m")}
     rho_h = torch.empty(n, dtype=torch.float32).pin_memory().numpy()
     E = nl.NeighborList()
-    for _ in range(max(1, args.warmup)):
+    for _ in range(0 if args.no_e2e else max(1, args.warmup)):
         E.density_from_host(pin["x"], pin["y"], pin["z"], pin["h"], pin["m"], d["box"], params,
                             rho_h, stream)
     torch.cuda.synchronize()
     te = time.perf_counter()
     esteps = max(1, min(args.steps, 5))
-    for _ in range(esteps):
+    for _ in range(0 if args.no_e2e else esteps):
         E.density_from_host(pin["x"], pin["y"], pin["z"], pin["h"], pin["m"], d["box"], params,
                             rho_h, stream)
     torch.cuda.synchronize()
@@ -227,9 +233,14 @@ def run_native(args):
                      "frac": step_bytes / (ms * 1e-3) / 1e9 / hbm,
                      "bytes_per_particle": ALGO_BYTES_PER_PARTICLE},
         "list": {"bytes_per_particle": sizes["list_bytes"] / n, "entries": sizes["n_entries"],
-                 "computed_pairs": pairs, "nodes": sizes["n_nodes"], "leaves": sizes["n_leaves"]},
-        "e2e": {"value": ws * n / (e_ms * 1e-3) / 1e6, "unit": UNIT,
-                "h2d_bytes_per_step": 20 * n, "d2h_bytes_per_step": 4 * n},
+                 "computed_pairs": pairs, "nodes": sizes["n_nodes"], "leaves": sizes["n_leaves"],
+                 "search_node_visits": sizes["node_visits"],
+                 "search_leaf_visits": sizes["leaf_visits"],
+                 "search_j_examined": sizes["j_examined"],
+                 "search_tile_tests": sizes["tile_tests"]},
+        "e2e": None if args.no_e2e else {
+            "value": ws * n / (e_ms * 1e-3) / 1e6, "unit": UNIT,
+            "h2d_bytes_per_step": 20 * n, "d2h_bytes_per_step": 4 * n},
         "h_iteration": {"plain": {"ms": hms, "iterations": hinfo["iterations"],
                                   "rebuilds": hinfo["rebuilds"],
                                   "unconverged": hinfo["unconverged"]}},
@@ -314,6 +325,11 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=1 << 18)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=N_FULL,
+                    help="particles (smaller cases are for profiling only)")
+    ap.add_argument("--reuse-h", action="store_true",
+                    help="reuse converged h cached by an earlier run with the same n")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -90,6 +90,11 @@ typedef struct {
     int64_t list_bytes;      /* bytes of all super-cluster records */
     int32_t cluster;         /* M */
     int32_t compress;
+    /* work of the last cluster-pair search (all rounds) */
+    int64_t node_visits;     /* octree nodes tested, summed over super-clusters */
+    int64_t leaf_visits;     /* leaves reached */
+    int64_t j_examined;      /* j-clusters box-tested against a super-cluster */
+    int64_t tile_tests;      /* (i-cluster, j-cluster) tiles decided by the exact predicate */
 } nl_sizes;
 
 /* Builds a new list (Sec. II-A, Listing "build"): keys, sort, clusters,

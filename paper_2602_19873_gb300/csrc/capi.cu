@@ -86,6 +86,7 @@ struct nl_list {
     DevBox dbox{};
     int any_per = 0;
     unsigned long long list_bytes = 0, n_entries = 0, n_tiles = 0;
+    unsigned long long node_visits = 0, leaf_visits = 0, j_examined = 0, tile_tests = 0;
     uint32_t stage_cap = kStageCap0;
     int stage_grown = 0;
     int64_t n_prepared = 0;
@@ -327,7 +328,7 @@ nl_status do_search(nl_list *nl, cudaStream_t s)
     sa.st = dst;
     sa.rec_off = nl->rec_off.as<uint32_t>();
 
-    unsigned long long entries = 0, tiles = 0, used = 0;
+    unsigned long long entries = 0, tiles = 0, used = 0, nv = 0, lv = 0, jx = 0, tt = 0;
     const uint32_t *work = nullptr;
     uint32_t count = nsc;
     for (int round = 0;; ++round) {
@@ -341,6 +342,10 @@ nl_status do_search(nl_list *nl, cudaStream_t s)
         if (st != NL_OK) return st;
         entries += nl->hst->n_entries;
         tiles += nl->hst->n_tiles;
+        nv += nl->hst->node_visits;
+        lv += nl->hst->leaf_visits;
+        jx += nl->hst->j_examined;
+        tt += nl->hst->tile_tests;
         used = nl->hst->list_used;
         const uint32_t nredo = nl->hst->stage_overflow;
         if (nredo == 0) break;
@@ -381,6 +386,10 @@ nl_status do_search(nl_list *nl, cudaStream_t s)
     nl->list_bytes = used;
     nl->n_entries = entries;
     nl->n_tiles = tiles;
+    nl->node_visits = nv;
+    nl->leaf_visits = lv;
+    nl->j_examined = jx;
+    nl->tile_tests = tt;
     return NL_OK;
 }
 
@@ -668,6 +677,10 @@ nl_status nl_get_sizes(const nl_list *nl, nl_sizes *out)
     out->list_bytes = (int64_t)nl->list_bytes;
     out->cluster = nl->p.cluster;
     out->compress = nl->p.compress;
+    out->node_visits = (int64_t)nl->node_visits;
+    out->leaf_visits = (int64_t)nl->leaf_visits;
+    out->j_examined = (int64_t)nl->j_examined;
+    out->tile_tests = (int64_t)nl->tile_tests;
     return NL_OK;
 }
 

@@ -36,6 +36,11 @@ struct Status {
     unsigned int pass_ticket;
     unsigned int pad;
     unsigned long long fail_off;   // lowest failed list reservation (host sets ~0 first)
+    // search work counters
+    unsigned long long node_visits;
+    unsigned long long leaf_visits;
+    unsigned long long j_examined;     // j-clusters box-tested against the 8 i-clusters
+    unsigned long long tile_tests;     // (i-cluster, j-cluster) tiles decided by the exact predicate
 };
 
 // ---------------------------------------------------------------------------

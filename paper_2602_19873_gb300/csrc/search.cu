@@ -175,10 +175,11 @@ __global__ void __launch_bounds__(SR_THREADS) k_search(SearchArgs a, SearchCtl c
             ri[k] = __fmul_rn(a.support, pi[k].w);
         }
 
-        uint32_t cnt = 0, tiles = 0;
+        uint32_t cnt = 0, tiles = 0, nvis = 0, lvis = 0, jex = 0, ttests = 0;
         int lastJ = -1;
         uint32_t v = 0;
         while (v < a.nnodes) {
+            ++nvis;
             const float4 nlo = a.nlo[v];
             const float4 nhi = a.nhi[v];
             const uint32_t skip = (uint32_t)__float_as_int(nhi.w);
@@ -196,6 +197,8 @@ __global__ void __launch_bounds__(SR_THREADS) k_search(SearchArgs a, SearchCtl c
             const int2 rg = a.nrng[v];
             const int Jlo = max(rg.x / M, lastJ + 1);
             const int Jhi = (rg.y - 1) / M;
+            ++lvis;
+            jex += Jhi >= Jlo ? (uint32_t)(Jhi - Jlo + 1) : 0u;
             for (int Jb = Jlo; Jb <= Jhi; Jb += 4) {
                 // round 1: 4 j-clusters x 8 i-cluster boxes, one per lane
                 const int Jl = Jb + (int)(lane >> 3);
@@ -223,6 +226,7 @@ __global__ void __launch_bounds__(SR_THREADS) k_search(SearchArgs a, SearchCtl c
                         if (!cm) continue;
                     }
                     uint32_t mask = 0;
+                    ttests += __popc(cm);
 #pragma unroll
                     for (int t = 0; t < NP; ++t) {
                         const uint32_t jj = (uint32_t)J * M + JJ0 + t * JSTEP;
@@ -268,6 +272,10 @@ __global__ void __launch_bounds__(SR_THREADS) k_search(SearchArgs a, SearchCtl c
                 atomicAdd(&a.st->n_entries, (unsigned long long)cnt);
                 atomicAdd(&a.st->n_tiles, (unsigned long long)tiles);
             }
+            atomicAdd(&a.st->node_visits, (unsigned long long)nvis);
+            atomicAdd(&a.st->leaf_visits, (unsigned long long)lvis);
+            atomicAdd(&a.st->j_examined, (unsigned long long)jex);
+            atomicAdd(&a.st->tile_tests, (unsigned long long)ttests);
         }
     }
 }

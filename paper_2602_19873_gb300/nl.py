@@ -43,7 +43,8 @@ class nl_sizes(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_clusters", C.c_int64), ("n_superclusters", C.c_int64),
                 ("n_leaves", C.c_int64), ("n_nodes", C.c_int64), ("n_entries", C.c_int64),
                 ("n_tiles", C.c_int64), ("list_bytes", C.c_int64), ("cluster", C.c_int32),
-                ("compress", C.c_int32)]
+                ("compress", C.c_int32), ("node_visits", C.c_int64), ("leaf_visits", C.c_int64),
+                ("j_examined", C.c_int64), ("tile_tests", C.c_int64)]
 
 
 P = C.c_void_p
