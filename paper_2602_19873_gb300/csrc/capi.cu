@@ -77,6 +77,15 @@ constexpr int kMaxRedoRounds = 8;
 
 }  // namespace
 
+namespace nlg {
+// Sets the thread-local message returned by nl_last_error (other entry files).
+nl_status report_error(nl_status st, const char *msg)
+{
+    g_err = msg;
+    return st;
+}
+}  // namespace nlg
+
 struct nl_list {
     int dev = -1, num_sms = 0;
     int64_t n = 0;

@@ -64,6 +64,8 @@ _SIGS = {
     "nl_set_profiling": (C.c_int, [P, C.c_int32]),
     "nl_get_stage_times": (C.c_int, [P, P, C.c_int32, P]),
     "nl_density_from_host": (C.c_int, [P, P, P, P, P, P, C.c_int64, P, P, P, P]),
+    "nl_sfc_order_noalloc": (C.c_int, [P, P, P, P, C.c_int64, P, C.c_int32, C.c_float, P, P,
+                                        P]),
     "nl_iterate_h": (C.c_int, [P, P, P, P, P, C.c_int64, P, P, C.c_float, C.c_float, C.c_int32,
                                C.c_float, C.c_int32, P, P, P]),
 }
@@ -140,6 +142,18 @@ def make_params(key=NL_KEY_HILBERT, cluster=8, support=2.0, compress=1, leaf_buc
     p.key, p.cluster, p.support = int(key), int(cluster), float(support)
     p.compress, p.leaf_bucket = int(compress), int(leaf_bucket)
     return p
+
+
+NL_NOALLOC_MAX_N = 1048576
+
+
+def sfc_order_noalloc(x, y, z, h, box, key, support, keys, perm, stream=None):
+    """nl_sfc_order_noalloc: keys (int64 tensor viewed as uint64) and perm
+    (int32 tensor) are caller-owned CUDA outputs of n entries."""
+    b = make_box(box) if isinstance(box, dict) else box
+    _check(load().nl_sfc_order_noalloc(_ptr(x), _ptr(y), _ptr(z), _ptr(h), int(x.numel()),
+                                       C.byref(b), int(key), float(support), _ptr(keys),
+                                       _ptr(perm), _stream(stream)))
 
 
 class NeighborList:
