@@ -116,6 +116,21 @@ nl_status nl_rebuild(nl_list *nl, const float *x, const float *y, const float *z
  * order.  FP32 arithmetic.  Does not synchronise. */
 nl_status nl_density_pass(const nl_list *nl, const float *m, float *rho, void *stream);
 
+/* Force passes over the list (Sec. II-D pair functions; Sec. III-B LJ).
+ *  NL_FORCE_SPH_PRESSURE: over symmetric pairs (i != j, d2 < max(ri,rj)^2),
+ *    a_i = -sum_j m_j [P_i/rho_i^2 grad_i W(r_ij,h_i) + P_j/rho_j^2 grad_i W(r_ij,h_j)],
+ *    grad_i W(r,h) = w'(r/h) / (pi h^4) * (x_i - x_j) / r, W the cubic spline of
+ *    nl_density_pass.  m, rho, pres: n device floats (caller order); params unused.
+ *  NL_FORCE_LJ: over gather pairs (i != j, d2 < ri^2),
+ *    F_i = sum_j 24 eps (2 sigma^12 / r^14 - sigma^6 / r^8) (x_i - x_j);
+ *    params = host {eps, sigma}; m, rho, pres unused (may be NULL).
+ * ax, ay, az: n device floats written in caller order.  FP32 arithmetic with
+ * block-partial sums.  Does not synchronise. */
+enum { NL_FORCE_SPH_PRESSURE = 0, NL_FORCE_LJ = 1 };
+nl_status nl_force_pass(const nl_list *nl, int32_t kind, const float *params, const float *m,
+                        const float *rho, const float *pres, float *ax, float *ay, float *az,
+                        void *stream);
+
 /* Gather-neighbor count of every particle (j != i with d2 < ri^2), caller
  * order, n device uint32.  Does not synchronise. */
 nl_status nl_neighbor_counts(const nl_list *nl, uint32_t *counts, void *stream);

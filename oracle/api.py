@@ -94,7 +94,7 @@ def lib():
                 "orc_dw": (C.c_double, [C.c_double]),
                 "orc_W": (C.c_double, [C.c_double, C.c_double]),
                 "orc_density": (None, [P, P, P, P, P, P, P, P, P]),
-                "orc_sph_force": (None, [P] * 13),
+                "orc_sph_force": (None, [P] * 14),
                 "orc_lj_force": (None, [P, P, P, P, C.c_double, C.c_double, P, P, P, P, P, P]),
                 "orc_lj_energy": (C.c_double, [P, P, P, P, C.c_double, C.c_double, P]),
                 "orc_gather_counts_brute": (None, [I64, P, P, P, P, P, F32, I64, P, P]),
@@ -335,21 +335,22 @@ def density(xs, ys, zs, hs, ms, box, off, idx, rows):
 
 
 def sph_force(xs, ys, zs, hs, ms, rho, pres, box, off, idx, rows):
-    """FP64 pressure acceleration of particles rows over symmetric sets.
-    rho and pres are full per-particle arrays (sorted order)."""
+    """FP64 pressure acceleration of particles rows over symmetric sets, and
+    sum_j |pair term| per row.  rho and pres are full per-particle arrays
+    (sorted order)."""
     xs, ys, zs, hs, ms = (_f32(a) for a in (xs, ys, zs, hs, ms))
     rho = np.ascontiguousarray(rho, dtype=np.float64)
     pres = np.ascontiguousarray(pres, dtype=np.float64)
     h, keep = _csr_make(off, idx)
     rows = _i64(rows)
-    ax, ay, az = (np.zeros(len(rows)) for _ in range(3))
+    ax, ay, az, fa = (np.zeros(len(rows)) for _ in range(4))
     b = _box(box)
     try:
         lib().orc_sph_force(_p(xs), _p(ys), _p(zs), _p(hs), _p(ms), _p(rho), _p(pres),
-                            C.byref(b), h, _p(rows), _p(ax), _p(ay), _p(az))
+                            C.byref(b), h, _p(rows), _p(ax), _p(ay), _p(az), _p(fa))
     finally:
         lib().orc_csr_free(h)
-    return ax, ay, az
+    return ax, ay, az, fa
 
 
 def lj_force(xs, ys, zs, box, eps, sigma, off, idx, rows):

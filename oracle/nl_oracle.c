@@ -966,14 +966,15 @@ void orc_density(const float *xs, const float *ys, const float *zs, const float 
  * gW(r,h) = grad_i W = (x_i - x_j)/r * w'(r/h)/(pi h^4). */
 void orc_sph_force(const float *xs, const float *ys, const float *zs, const float *hs,
                    const float *ms, const double *rho, const double *pres, const orc_box *b,
-                   const orc_csr *P, const int64_t *rows, double *ax, double *ay, double *az)
+                   const orc_csr *P, const int64_t *rows, double *ax, double *ay, double *az,
+                   double *fabs_sum)
 {
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t k = 0; k < P->n; ++k) {
         int64_t i = rows[k];
         double hi = (double)hs[i];
         double ci = pres[i] / (rho[i] * rho[i]);
-        double fx = 0, fy = 0, fz = 0;
+        double fx = 0, fy = 0, fz = 0, fa = 0;
         for (int64_t t = P->off[k]; t < P->off[k + 1]; ++t) {
             int64_t j = P->idx[t];
             double dx = dx64(xs, i, j, b, 0), dy = dx64(ys, i, j, b, 1), dz = dx64(zs, i, j, b, 2);
@@ -988,10 +989,12 @@ void orc_sph_force(const float *xs, const float *ys, const float *zs, const floa
             fx -= s * (-dx);
             fy -= s * (-dy);
             fz -= s * (-dz);
+            fa += fabs(s) * r;
         }
         ax[k] = fx;
         ay[k] = fy;
         az[k] = fz;
+        if (fabs_sum) fabs_sum[k] = fa;
     }
 }
 

@@ -659,6 +659,44 @@ nl_status nl_density_pass(const nl_list *cnl, const float *m, float *rho, void *
     return NL_OK;
 }
 
+nl_status nl_force_pass(const nl_list *cnl, int32_t kind, const float *params, const float *m,
+                        const float *rho, const float *pres, float *ax, float *ay, float *az,
+                        void *stream)
+{
+    nl_status st = check_list(cnl);
+    if (st != NL_OK) return st;
+    if (!ax || !ay || !az) return fail(NL_ERR_ARG, "NULL force output");
+    nl_list *nl = const_cast<nl_list *>(cnl);
+    cudaStream_t s = (cudaStream_t)stream;
+    PassArgs a = pass_args(nl);
+    a.out0 = ax;
+    a.out1 = ay;
+    a.out2 = az;
+    if (kind == NL_FORCE_SPH_PRESSURE) {
+        if (!m || !rho || !pres) return fail(NL_ERR_ARG, "SPH force needs m, rho and pres");
+        CK(nl->aux.ensure((size_t)nl->npad * 8));
+        CK(nl->mark(5, s));
+        CK(launch_gather_aux((uint32_t)nl->n, nl->npad, nl->vals.as<uint32_t>(), m, pres, rho, 1,
+                             nl->aux.as<float2>(), s));
+        CK(nl->mark(6, s));
+        CK(launch_pass(a, PASS_SPH, nl->p.cluster, nl->any_per, nl->num_sms, s));
+        CK(nl->mark(7, s));
+    } else if (kind == NL_FORCE_LJ) {
+        if (!params) return fail(NL_ERR_ARG, "LJ force needs params {eps, sigma}");
+        if (!std::isfinite(params[0]) || !(params[1] > 0.f))
+            return fail(NL_ERR_ARG, "LJ needs finite eps and sigma > 0");
+        a.p0 = params[0];
+        a.p1 = params[1];
+        CK(nl->mark(5, s));
+        CK(nl->mark(6, s));
+        CK(launch_pass(a, PASS_LJ, nl->p.cluster, nl->any_per, nl->num_sms, s));
+        CK(nl->mark(7, s));
+    } else {
+        return fail(NL_ERR_ARG, "unknown force kind %d", kind);
+    }
+    return NL_OK;
+}
+
 nl_status nl_neighbor_counts(const nl_list *cnl, uint32_t *counts, void *stream)
 {
     nl_status st = check_list(cnl);

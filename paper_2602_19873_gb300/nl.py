@@ -55,6 +55,7 @@ _SIGS = {
     "nl_rebuild": (C.c_int, [P, P, P, P, P, C.c_int64, P, P, P]),
     "nl_density_pass": (C.c_int, [P, P, P, P]),
     "nl_neighbor_counts": (C.c_int, [P, P, P]),
+    "nl_force_pass": (C.c_int, [P, C.c_int32, P, P, P, P, P, P, P, P]),
     "nl_free": (C.c_int, [P]),
     "nl_get_sizes": (C.c_int, [P, P]),
     "nl_copy_sorted": (C.c_int, [P, P, P]),
@@ -71,6 +72,7 @@ _SIGS = {
 }
 
 NL_HSTART_GIVEN, NL_HSTART_PLAIN = 0, 1
+NL_FORCE_SPH_PRESSURE, NL_FORCE_LJ = 0, 1
 
 
 class nl_hiter_info(C.Structure):
@@ -223,6 +225,12 @@ class NeighborList:
 
     def density_pass(self, m, rho, stream=None):
         _check(load().nl_density_pass(self.handle, _ptr(m), _ptr(rho), _stream(stream)))
+
+    def force_pass(self, kind, ax, ay, az, m=None, rho=None, pres=None, eps=1.0, sigma=1.0,
+                   stream=None):
+        prm = (C.c_float * 2)(float(eps), float(sigma))
+        _check(load().nl_force_pass(self.handle, int(kind), prm, _ptr(m), _ptr(rho), _ptr(pres),
+                                    _ptr(ax), _ptr(ay), _ptr(az), _stream(stream)))
 
     def neighbor_counts(self, counts, stream=None):
         _check(load().nl_neighbor_counts(self.handle, _ptr(counts), _stream(stream)))

@@ -236,3 +236,57 @@ def test_overflow_rounds_keep_records_exact(cases, monkeypatch):
                        np.arange(n))
     assert (np.abs(rho - want) / want).max() <= DENSITY_RTOL
     L.free()
+
+
+FORCE_RTOL = 1e-5   # |a_gpu - a_64| / sum_j |f_ij|_64, per particle
+
+
+@pytest.mark.parametrize("cluster", [4, 8, 16])
+def test_sph_pressure_force(cases, cluster):
+    """Inputs rho and P are the oracle's FP64 density rounded to FP32 and
+    P = (gamma - 1) rho u, so both sides read identical values."""
+    import torch
+    d, o, (g_off, g_idx, p_off, p_idx) = cases["evrard"]
+    n = len(o["xs"])
+    rho64 = orc.density(o["xs"], o["ys"], o["zs"], o["hs"], o["ms"], d["box"], g_off, g_idx,
+                        np.arange(n))
+    rho32 = rho64.astype(np.float32)
+    pres32 = (np.float32(2.0 / 3.0) * rho32 * np.float32(0.05)).astype(np.float32)
+    ax, ay, az, fa = orc.sph_force(o["xs"], o["ys"], o["zs"], o["hs"], o["ms"],
+                                   rho32.astype(np.float64), pres32.astype(np.float64), d["box"],
+                                   p_off, p_idx, np.arange(n))
+    L, t = gpu_build(d, cluster=cluster)
+    inv = np.empty(n, np.int64)
+    inv[o["perm"]] = np.arange(n)
+    rho_c = torch.from_numpy(rho32[inv]).cuda()       # caller order
+    pres_c = torch.from_numpy(pres32[inv]).cuda()
+    out = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+    L.force_pass(nl.NL_FORCE_SPH_PRESSURE, *out, m=t["m"], rho=rho_c, pres=pres_c)
+    torch.cuda.synchronize()
+    got = np.stack([a.cpu().numpy()[o["perm"]] for a in out], 1)
+    want = np.stack([ax, ay, az], 1)
+    err = np.linalg.norm(got - want, axis=1) / np.maximum(fa, 1e-300)
+    assert err.max() <= FORCE_RTOL, err.max()
+    # momentum: sum m a vanishes up to FP32 roundoff
+    mom = (o["ms"][:, None].astype(np.float64) * got).sum(0)
+    assert np.abs(mom).max() <= 1e-5 * (o["ms"][:, None] * fa[:, None]).sum()
+    L.free()
+
+
+@pytest.mark.parametrize("cluster", [4, 8, 16])
+def test_lj_force(cases, cluster):
+    import torch
+    d, o, (g_off, g_idx, p_off, p_idx) = cases["lj_fluid"]
+    n = len(o["xs"])
+    fx, fy, fz, fa = orc.lj_force(o["xs"], o["ys"], o["zs"], d["box"], 1.0, 0.3, g_off, g_idx,
+                                  np.arange(n))
+    L, t = gpu_build(d, cluster=cluster)
+    out = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+    L.force_pass(nl.NL_FORCE_LJ, *out, eps=1.0, sigma=0.3)
+    torch.cuda.synchronize()
+    got = np.stack([a.cpu().numpy()[o["perm"]] for a in out], 1)
+    want = np.stack([fx, fy, fz], 1)
+    err = np.linalg.norm(got - want, axis=1) / fa
+    assert err.max() <= FORCE_RTOL, err.max()
+    assert np.abs(got.sum(0)).max() <= 1e-5 * fa.sum()
+    L.free()

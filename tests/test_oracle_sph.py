@@ -100,7 +100,7 @@ def test_pressure_force_is_minus_energy_gradient(orc):
     pres = K * rho ** gamma
     g_off, g_idx = orc.gather_all(xs, ys, zs, hs, d["box"], 2.0)
     p_off, p_idx = orc.symmetrize(g_off, g_idx)
-    ax, ay, az = orc.sph_force(xs, ys, zs, hs, ms, rho, pres, d["box"], p_off, p_idx, np.arange(n))
+    ax, ay, az, _ = orc.sph_force(xs, ys, zs, hs, ms, rho, pres, d["box"], p_off, p_idx, np.arange(n))
     acc = np.stack([ax, ay, az], 1)
     # momentum conservation
     assert np.abs((ms[:, None].astype(np.float64) * acc).sum(0)).max() < 1e-12 * np.abs(
