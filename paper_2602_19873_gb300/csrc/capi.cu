@@ -668,13 +668,15 @@ nl_status nl_force_pass(const nl_list *cnl, int32_t kind, const float *params, c
     if (!ax || !ay || !az) return fail(NL_ERR_ARG, "NULL force output");
     nl_list *nl = const_cast<nl_list *>(cnl);
     cudaStream_t s = (cudaStream_t)stream;
-    PassArgs a = pass_args(nl);
+    if (kind == NL_FORCE_SPH_PRESSURE) {
+        if (!m || !rho || !pres) return fail(NL_ERR_ARG, "SPH force needs m, rho and pres");
+        CK(nl->aux.ensure((size_t)nl->npad * 8));
+    }
+    PassArgs a = pass_args(nl);  // after every buffer it points to exists
     a.out0 = ax;
     a.out1 = ay;
     a.out2 = az;
     if (kind == NL_FORCE_SPH_PRESSURE) {
-        if (!m || !rho || !pres) return fail(NL_ERR_ARG, "SPH force needs m, rho and pres");
-        CK(nl->aux.ensure((size_t)nl->npad * 8));
         CK(nl->mark(5, s));
         CK(launch_gather_aux((uint32_t)nl->n, nl->npad, nl->vals.as<uint32_t>(), m, pres, rho, 1,
                              nl->aux.as<float2>(), s));

@@ -85,6 +85,32 @@ __device__ __forceinline__ float3 pair_dx(const float4 &pi, const float4 &pj, co
     return make_float3(dx, dy, dz);
 }
 
+// Accurate pair vector for the sums.  The canonical wrap subtracts L from the
+// rounded difference, which loses up to ulp(L)/2 for pairs across a periodic
+// face; here the coordinate is shifted first (exact: both operands lie in
+// [L/2, 2L]) and one rounding remains.  The decision to wrap is the
+// canonical one, so the pair set is unchanged.
+__device__ __forceinline__ float wrap_axis_acc(float xi, float xj, float len, float half, int per)
+{
+    float d = __fsub_rn(xj, xi);
+    if (per) {
+        if (d > half)
+            d = __fsub_rn(__fsub_rn(xj, len), xi);
+        else if (d < -half)
+            d = __fsub_rn(__fadd_rn(xj, len), xi);
+    }
+    return d;
+}
+
+template <bool PER>
+__device__ __forceinline__ float3 pair_dx_acc(const float4 &pi, const float4 &pj, const DevBox &b)
+{
+    if (!PER) return make_float3(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z));
+    return make_float3(wrap_axis_acc(pi.x, pj.x, b.len[0], b.half[0], b.per[0]),
+                       wrap_axis_acc(pi.y, pj.y, b.len[1], b.half[1], b.per[1]),
+                       wrap_axis_acc(pi.z, pj.z, b.len[2], b.half[2], b.per[2]));
+}
+
 __device__ __forceinline__ float d2_of(const float3 &d)
 {
     return __fadd_rn(__fadd_rn(__fmul_rn(d.x, d.x), __fmul_rn(d.y, d.y)), __fmul_rn(d.z, d.z));

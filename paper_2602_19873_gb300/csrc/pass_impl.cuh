@@ -179,11 +179,13 @@ __global__ void __launch_bounds__(PS_THREADS) k_pass(PassArgs a)
                     for (int k = 0; k < kSC; ++k) {
                         if (!((me >> k) & 1u)) continue;
                         const uint32_t ii = (s * kSC + k) * M + II;
-                        const float3 dv = pair_dx<PER>(pi[k], pj, a.box);
-                        const float d2 = d2_of(dv);
+                        // canonical distance decides the pair; the sums use the
+                        // accurate vector (identical unless wrapped)
+                        const float d2 = pair_d2<PER>(pi[k], pj, a.box);
                         if constexpr (KIND == PASS_DENSITY) {
                             if (owner && ii != jj && d2 < ri2[k]) {
-                                float q = sqrtf(d2) * hinv[k];
+                                const float3 dv = pair_dx_acc<PER>(pi[k], pj, a.box);
+                                float q = sqrtf(d2_of(dv)) * hinv[k];
                                 acc.b[k] += aj.x * spline_w(q);
                             }
                         } else if constexpr (KIND == PASS_COUNT) {
@@ -193,7 +195,8 @@ __global__ void __launch_bounds__(PS_THREADS) k_pass(PassArgs a)
                             const float rr = fmaxf(ri[k], rj);
                             if (owner && ii != jj && d2 < __fmul_rn(rr, rr)) {
                                 // a_i -= m_j (c_i gW_i + c_j gW_j) (x_i - x_j) / r
-                                float r = sqrtf(d2);
+                                const float3 dv = pair_dx_acc<PER>(pi[k], pj, a.box);
+                                float r = sqrtf(d2_of(dv));
                                 float hj = pj.w, hji = 1.f / hj;
                                 float gi = spline_dw(r * hinv[k]) * hinv[k] * hinv[k] * hinv[k] * hinv[k];
                                 float gj = spline_dw(r * hji) * hji * hji * hji * hji;
@@ -205,7 +208,8 @@ __global__ void __launch_bounds__(PS_THREADS) k_pass(PassArgs a)
                             }
                         } else {  // LJ: F_i += 24 eps (2 s^12/r^14 - s^6/r^8)(x_i - x_j)
                             if (owner && ii != jj && d2 < ri2[k]) {
-                                float ir2 = 1.f / d2;
+                                const float3 dv = pair_dx_acc<PER>(pi[k], pj, a.box);
+                                float ir2 = 1.f / d2_of(dv);
                                 float s2 = a.p1 * a.p1 * ir2;
                                 float s6 = s2 * s2 * s2;
                                 float c = 24.f * a.p0 * ir2 * s6 * (2.f * s6 - 1.f);
