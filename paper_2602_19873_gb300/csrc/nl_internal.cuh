@@ -85,11 +85,13 @@ __device__ __forceinline__ float3 pair_dx(const float4 &pi, const float4 &pj, co
     return make_float3(dx, dy, dz);
 }
 
-// Accurate pair vector for the sums.  The canonical wrap subtracts L from the
-// rounded difference, which loses up to ulp(L)/2 for pairs across a periodic
-// face; here the coordinate is shifted first (exact: both operands lie in
-// [L/2, 2L]) and one rounding remains.  The decision to wrap is the
-// canonical one, so the pair set is unchanged.
+// Accurate pair vector for the sums.  The canonical wrap adds or subtracts
+// L from the rounded difference, which loses up to ulp(L)/2 for pairs across
+// a periodic face.  Here the coordinate near L is shifted first: when
+// xj - xi > L/2 it is xj, when xj - xi < -L/2 it is xi, and in both cases
+// the shift is exact (Sterbenz: the operand lies in [L/2, L]), so one
+// rounding remains.  The decision to wrap is the canonical one, so the pair
+// set is unchanged.
 __device__ __forceinline__ float wrap_axis_acc(float xi, float xj, float len, float half, int per)
 {
     float d = __fsub_rn(xj, xi);
@@ -97,7 +99,7 @@ __device__ __forceinline__ float wrap_axis_acc(float xi, float xj, float len, fl
         if (d > half)
             d = __fsub_rn(__fsub_rn(xj, len), xi);
         else if (d < -half)
-            d = __fsub_rn(__fadd_rn(xj, len), xi);
+            d = __fsub_rn(xj, __fsub_rn(xi, len));
     }
     return d;
 }
