@@ -62,8 +62,10 @@ __global__ void __launch_bounds__(256) k_cluster_boxes(uint32_t npad, const floa
     float r = real ? __fmul_rn(support, p.w) : 0.f;
     float lx = real ? p.x : INFINITY, ly = real ? p.y : INFINITY, lz = real ? p.z : INFINITY;
     float hx = real ? p.x : -INFINITY, hy = real ? p.y : -INFINITY, hz = real ? p.z : -INFINITY;
+    float rmin = real ? r : INFINITY;
 #pragma unroll
     for (int o = 1; o < M; o <<= 1) {
+        rmin = fminf(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
         lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
         ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
         lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
@@ -74,7 +76,7 @@ __global__ void __launch_bounds__(256) k_cluster_boxes(uint32_t npad, const floa
     }
     if ((k & (M - 1)) == 0) {
         clo[k / M] = make_float4(lx, ly, lz, r);
-        chi[k / M] = make_float4(hx, hy, hz, 0.f);
+        chi[k / M] = make_float4(hx, hy, hz, rmin);
     }
 }
 

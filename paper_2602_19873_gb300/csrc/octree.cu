@@ -51,8 +51,10 @@ __global__ void __launch_bounds__(256) k_permute(uint32_t n, uint32_t npad,
     pos[k] = p;
     float lx = k < n ? p.x : INFINITY, ly = k < n ? p.y : INFINITY, lz = k < n ? p.z : INFINITY;
     float hx = k < n ? p.x : -INFINITY, hy = k < n ? p.y : -INFINITY, hz = k < n ? p.z : -INFINITY;
+    float rmin = k < n ? r : INFINITY;
 #pragma unroll
     for (int o = 1; o < M; o <<= 1) {
+        rmin = fminf(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
         lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
         ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
         lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
@@ -63,7 +65,7 @@ __global__ void __launch_bounds__(256) k_permute(uint32_t n, uint32_t npad,
     }
     if ((k & (M - 1)) == 0) {
         clo[k / M] = make_float4(lx, ly, lz, r);
-        chi[k / M] = make_float4(hx, hy, hz, 0.f);
+        chi[k / M] = make_float4(hx, hy, hz, rmin);
     }
 }
 

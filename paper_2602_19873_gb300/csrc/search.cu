@@ -132,7 +132,7 @@ __device__ bool encode_record(uint32_t cnt, const uint32_t *stJ, const uint8_t *
 }
 
 template <int M, bool PER>
-__global__ void __launch_bounds__(SR_THREADS) k_search(SearchArgs a, SearchCtl ctl)
+__global__ void __launch_bounds__(SR_THREADS, 3) k_search(SearchArgs a, SearchCtl ctl)
 {
     constexpr int NP = (M * M) / 32 > 0 ? (M * M) / 32 : 1;  // pairs per lane per tile
     constexpr int JSTEP = 32 / M;
@@ -200,15 +200,32 @@ __global__ void __launch_bounds__(SR_THREADS) k_search(SearchArgs a, SearchCtl c
             ++lvis;
             jex += Jhi >= Jlo ? (uint32_t)(Jhi - Jlo + 1) : 0u;
             for (int Jb = Jlo; Jb <= Jhi; Jb += 4) {
-                // round 1: 4 j-clusters x 8 i-cluster boxes, one per lane
+                // round 1: 4 j-clusters x 8 i-cluster boxes, one per lane:
+                // may some pair be neighbors, and are all pairs neighbors?
                 const int Jl = Jb + (int)(lane >> 3);
-                bool cand = false;
-                if (Jl <= Jhi) cand = boxes_near<PER>(ilo, ihi, a.clo[Jl], a.chi[Jl], a.box);
+                bool cand = false, sure = false;
+                if (Jl <= Jhi) {
+                    const float4 jlo = a.clo[Jl], jhi = a.chi[Jl];
+                    cand = boxes_near<PER>(ilo, ihi, jlo, jhi, a.box);
+                    sure = cand && (uint32_t)Jl != s * kSC + (lane & 7) &&
+                           boxes_all_near<PER>(ilo, ihi, jlo, jhi, a.box);
+                }
                 const uint32_t bal = __ballot_sync(0xffffffffu, cand);
+                const uint32_t sbal = __ballot_sync(0xffffffffu, sure);
                 for (int q = 0; q < 4; ++q) {
                     uint32_t cm = (bal >> (8 * q)) & 0xffu;
                     if (!cm) continue;
                     const int J = Jb + q;
+                    const uint32_t sm = (sbal >> (8 * q)) & 0xffu;
+                    if (sm == cm) {  // every candidate tile is a sure hit
+                        if (lane == 0 && cnt < a.stage_cap) {
+                            stJ[cnt] = (uint32_t)J;
+                            stM[cnt] = (uint8_t)sm;
+                        }
+                        ++cnt;
+                        tiles += __popc(sm);
+                        continue;
+                    }
                     if (__popc(cm) > 1) {
                         // round 2: every i particle against the j-cluster box
                         const float4 jlo = a.clo[J], jhi = a.chi[J];
@@ -222,11 +239,11 @@ __global__ void __launch_bounds__(SR_THREADS) k_search(SearchArgs a, SearchCtl c
                                 if ((b >> (c * M)) & ((M == 32) ? 0xffffffffu : ((1u << M) - 1u)))
                                     pm |= 1u << (t * CPB + c);
                         }
-                        cm &= pm;
+                        cm &= pm | sm;
                         if (!cm) continue;
                     }
-                    uint32_t mask = 0;
-                    ttests += __popc(cm);
+                    uint32_t mask = sm;
+                    ttests += __popc(cm & ~sm);
 #pragma unroll
                     for (int t = 0; t < NP; ++t) {
                         const uint32_t jj = (uint32_t)J * M + JJ0 + t * JSTEP;
