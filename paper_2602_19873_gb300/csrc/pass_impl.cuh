@@ -88,11 +88,23 @@ __device__ __forceinline__ void acc_end_block(Acc<KIND> &acc)
     }
 }
 
+// Shared memory per warp: the j particles (and pass inputs) of one block
+// of 32 list entries, loaded in bulk before the block is computed.
+template <int M, int KIND>
+constexpr size_t pass_smem_per_warp()
+{
+    return (size_t)32 * M * (sizeof(float4) + ((KIND == PASS_DENSITY || KIND == PASS_SPH) ? sizeof(float2) : 0));
+}
+
 template <int M, bool PER, int KIND>
 __global__ void __launch_bounds__(PS_THREADS) k_pass(PassArgs a)
 {
     constexpr int NP = (M * M) / 32 > 0 ? (M * M) / 32 : 1;
     constexpr int JSTEP = 32 / M;
+    constexpr bool AUX = (KIND == PASS_DENSITY || KIND == PASS_SPH);
+    extern __shared__ __align__(16) unsigned char pass_smem[];
+    float4 *sp = reinterpret_cast<float4 *>(pass_smem + (threadIdx.x >> 5) * pass_smem_per_warp<M, KIND>());
+    float2 *sa = reinterpret_cast<float2 *>(sp + 32 * M);
     const unsigned lane = lane_id();
     const unsigned lt = lanemask_lt();
     const uint32_t II = lane % M;
@@ -166,15 +178,28 @@ __global__ void __launch_bounds__(PS_THREADS) k_pass(PassArgs a)
             const uint32_t mk = valid ? masks[t] : 0u;
             const uint32_t nb = min(32u, cnt - b0);
             acc_begin_block<KIND>(acc);
+            // stage the block's j clusters: entry e's particles at sp[e*M ..]
+            __syncwarp();
+#pragma unroll 4
+            for (uint32_t q0 = 0; q0 < nb * M; q0 += 32) {  // whole warp in every shuffle
+                const uint32_t q = q0 + lane;
+                const uint32_t e = min(q / M, 31u);
+                const uint32_t src = __shfl_sync(0xffffffffu, J, e) * M + (q % M);
+                if (q < nb * M) {
+                    sp[q] = a.pos[src];
+                    if constexpr (AUX) sa[q] = a.aux[src];
+                }
+            }
+            __syncwarp();
             for (uint32_t e = 0; e < nb; ++e) {
                 const uint32_t Je = __shfl_sync(0xffffffffu, J, e);
                 const uint32_t me = __shfl_sync(0xffffffffu, mk, e);
 #pragma unroll
                 for (int tt = 0; tt < NP; ++tt) {
                     const uint32_t jj = Je * M + JJ0 + tt * JSTEP;
-                    const float4 pj = a.pos[jj];
+                    const float4 pj = sp[e * M + JJ0 + tt * JSTEP];
                     float2 aj = make_float2(0.f, 0.f);
-                    if constexpr (KIND == PASS_DENSITY || KIND == PASS_SPH) aj = a.aux[jj];
+                    if constexpr (AUX) aj = sa[e * M + JJ0 + tt * JSTEP];
 #pragma unroll
                     for (int k = 0; k < kSC; ++k) {
                         if (!((me >> k) & 1u)) continue;
@@ -271,10 +296,19 @@ __global__ void __launch_bounds__(PS_THREADS) k_pass(PassArgs a)
 template <int M, int KIND>
 static void launch_mk(const PassArgs &a, int per, int grid, cudaStream_t s)
 {
+    const size_t smem = (size_t)(PS_THREADS / 32) * pass_smem_per_warp<M, KIND>();
+    static bool attr[2] = {false, false};
+    if (!attr[per ? 1 : 0]) {
+        if (per)
+            cudaFuncSetAttribute(k_pass<M, true, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        else
+            cudaFuncSetAttribute(k_pass<M, false, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr[per ? 1 : 0] = true;
+    }
     if (per)
-        k_pass<M, true, KIND><<<grid, PS_THREADS, 0, s>>>(a);
+        k_pass<M, true, KIND><<<grid, PS_THREADS, smem, s>>>(a);
     else
-        k_pass<M, false, KIND><<<grid, PS_THREADS, 0, s>>>(a);
+        k_pass<M, false, KIND><<<grid, PS_THREADS, smem, s>>>(a);
 }
 
 template <int KIND>
