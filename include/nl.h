@@ -235,6 +235,30 @@ nl_status nl_sfc_order_noalloc(const float *x, const float *y, const float *z, c
                                int64_t n, const nl_box *box, int32_t key, float support,
                                uint64_t *keys, uint32_t *perm, void *stream);
 
+/* Batches of independent systems (the workloads' "many uneven systems").
+ * The caller's arrays hold nsys systems back to back: system s owns
+ * indices [offsets[s], offsets[s+1]) (host int64 array of nsys+1 entries,
+ * offsets[0] = 0, every system non-empty) and has its own box boxes[s]
+ * (host array).  Every stage runs once for the whole batch: one key kernel,
+ * one radix sort ordering (system, key), one permutation that starts every
+ * system on a super-cluster boundary, one octree pass producing each
+ * system's pre-order octree, one persistent search launch and one
+ * persistent pass launch over all super-clusters.  Pairs never cross
+ * systems; results equal those of building every system on its own (the
+ * records hold batch-global cluster indices).  Passes, counts, forces and
+ * inspection calls accept batched lists unchanged (caller order). */
+nl_status nl_build_batch(const float *x, const float *y, const float *z, const float *h,
+                         int32_t nsys, const int64_t *offsets, const nl_box *boxes,
+                         const nl_params *p, void *stream, nl_list **out);
+nl_status nl_rebuild_batch(nl_list *nl, const float *x, const float *y, const float *z,
+                           const float *h, int32_t nsys, const int64_t *offsets,
+                           const nl_box *boxes, const nl_params *p, void *stream);
+nl_status nl_iterate_h_batch(nl_list *nl, const float *x, const float *y, const float *z, float *h,
+                             int32_t nsys, const int64_t *offsets, const nl_box *boxes,
+                             const nl_params *p, float n_target, float tol, int32_t max_iter,
+                             float margin, int32_t start, uint8_t *converged, nl_hiter_info *info,
+                             void *stream);
+
 /* Thread-local description of the last error (never NULL). */
 const char *nl_last_error(void);
 

@@ -103,7 +103,20 @@ struct nl_list {
         nodeoff, bsum;
     DevBuf nlo, nhi, nrng, nlevel, nparent, nchild, narrive;
     DevBuf stageJ, stageM, list, rec_off, redo, work, aux, status;
+    DevBuf perm_pad, sys_off, sys_pad, sys_box, sys_root, sys_hcap;
+    int32_t nsys = 1;
     Status *hst = nullptr;
+
+    SysTables tables() const
+    {
+        return SysTables{sys_off.as<uint32_t>(), sys_pad.as<uint32_t>(), sys_box.as<DevBox>(),
+                         sys_root.as<uint32_t>(), (uint32_t)nsys};
+    }
+    OctreeOut octree_out() const
+    {
+        return OctreeOut{nlo.as<float4>(), nhi.as<float4>(), nrng.as<int2>(), nlevel.as<uint8_t>(),
+                         nparent.as<int32_t>(), nchild.as<uint32_t>(), narrive.as<uint32_t>()};
+    }
     // stage timing (CUDA events on the launching stream)
     static constexpr int kStages = 7;
     int profiling = 0;
@@ -136,7 +149,8 @@ struct nl_list {
         DevBuf *all[] = {&keys, &keys_alt, &vals, &vals_alt, &hist, &pos, &clo, &chi, &lcp, &lev,
                          &leaf_first, &leaf_lev, &nodeoff, &bsum, &nlo, &nhi, &nrng, &nlevel,
                          &nparent, &nchild, &narrive, &stageJ, &stageM, &list, &rec_off, &redo,
-                         &work, &aux, &status, &hx, &hy, &hz, &hh, &hm, &hrho, &it_hq,
+                         &work, &aux, &status, &hx, &hy, &hz, &hh, &hm, &hrho, &perm_pad,
+                         &sys_off, &sys_pad, &sys_box, &sys_root, &sys_hcap, &it_hq,
                          &it_hlo, &it_hhi, &it_hs, &it_counts, &it_conv, &it_aflag, &it_alist,
                          &it_words, &it_tmp};
         for (DevBuf *b : all) b->release();
@@ -194,14 +208,25 @@ nl_status read_status(nl_list *nl, cudaStream_t s)
     return NL_OK;
 }
 
+// Keys, stable sort (by system, then key), padded permutation with cluster
+// boxes, octree.  Systems: nsys >= 1; offs[0..nsys] caller offsets (host),
+// boxes[0..nsys-1] (host).
 nl_status do_prep(nl_list *nl, const float *x, const float *y, const float *z, const float *h,
-                  int64_t n, const nl_box *box, const nl_params *p, cudaStream_t s)
+                  int64_t n, int32_t nsys, const int64_t *offs, const nl_box *boxes,
+                  const nl_params *p, cudaStream_t s)
 {
     if (!x || !y || !z || !h) return fail(NL_ERR_ARG, "NULL particle array");
     if (n < 1) return fail(NL_ERR_ARG, "n must be >= 1 (got %lld)", (long long)n);
     if (n > (int64_t)1 << 30) return fail(NL_ERR_ARG, "n must be <= 2^30");
-    nl_status st = check_params(p, box);
-    if (st != NL_OK) return st;
+    if (nsys < 1 || nsys > (1 << 20)) return fail(NL_ERR_ARG, "need 1 <= nsys <= 2^20");
+    if (!offs || !boxes) return fail(NL_ERR_ARG, "NULL system table");
+    if (offs[0] != 0 || offs[nsys] != n)
+        return fail(NL_ERR_ARG, "system offsets must start at 0 and end at n");
+    for (int32_t k = 0; k < nsys; ++k) {
+        if (offs[k + 1] <= offs[k]) return fail(NL_ERR_ARG, "system %d is empty", k);
+        nl_status st = check_params(p, &boxes[k]);
+        if (st != NL_OK) return st;
+    }
 
     int dev;
     CK(cudaGetDevice(&dev));
@@ -213,12 +238,34 @@ nl_status do_prep(nl_list *nl, const float *x, const float *y, const float *z, c
 
     const uint32_t N = (uint32_t)n;
     const int M = p->cluster;
-    const uint32_t nsc = (N + kSC * M - 1) / (kSC * M);
-    const uint32_t ncl = nsc * kSC, npad = ncl * M;
+    const uint32_t scp = (uint32_t)(kSC * M);
+    // host tables: offsets, padded offsets, boxes, periodic h caps
+    std::vector<uint32_t> off(nsys + 1), pad(nsys + 1);
+    std::vector<DevBox> dbox(nsys);
+    std::vector<float> hcap(nsys);
+    nl->any_per = 0;
+    pad[0] = 0;
+    for (int32_t k = 0; k <= nsys; ++k) off[k] = (uint32_t)offs[k];
+    for (int32_t k = 0; k < nsys; ++k) {
+        uint64_t nk = off[k + 1] - off[k];
+        uint64_t padded = (nk + scp - 1) / scp * scp;
+        if ((uint64_t)pad[k] + padded > 0xffffffffull) return fail(NL_ERR_ARG, "batch too large");
+        pad[k + 1] = pad[k] + (uint32_t)padded;
+        dbox[k] = make_devbox(boxes[k]);
+        float cap = 3.0e38f;
+        for (int a = 0; a < 3; ++a) {
+            if (boxes[k].periodic[a]) {
+                nl->any_per = 1;
+                cap = std::min(cap, dbox[k].half[a] / p->support * 0.999999f);
+            }
+        }
+        hcap[k] = cap;
+    }
+    const uint32_t npad = pad[nsys], ncl = npad / M, nsc = npad / scp;
     nl->p = *p;
-    nl->box = *box;
-    nl->dbox = make_devbox(*box);
-    nl->any_per = box->periodic[0] || box->periodic[1] || box->periodic[2];
+    nl->box = boxes[0];
+    nl->dbox = dbox[0];
+    nl->nsys = nsys;
 
     CK(nl->keys.ensure((size_t)N * 8));
     CK(nl->keys_alt.ensure((size_t)N * 8));
@@ -226,6 +273,7 @@ nl_status do_prep(nl_list *nl, const float *x, const float *y, const float *z, c
     CK(nl->vals_alt.ensure((size_t)N * 4));
     CK(nl->hist.ensure(radix_hist_words(N) * 4));
     CK(nl->pos.ensure((size_t)npad * 16));
+    CK(nl->perm_pad.ensure((size_t)npad * 4));
     CK(nl->clo.ensure((size_t)ncl * 16));
     CK(nl->chi.ensure((size_t)ncl * 16));
     CK(nl->lcp.ensure((size_t)N));
@@ -238,39 +286,51 @@ nl_status do_prep(nl_list *nl, const float *x, const float *y, const float *z, c
     CK(nl->redo.ensure((size_t)nsc * 4));
     CK(nl->work.ensure((size_t)nsc * 4));
     CK(nl->status.ensure(sizeof(Status)));
+    CK(nl->sys_off.ensure((size_t)(nsys + 1) * 4));
+    CK(nl->sys_pad.ensure((size_t)(nsys + 1) * 4));
+    CK(nl->sys_box.ensure((size_t)nsys * sizeof(DevBox)));
+    CK(nl->sys_root.ensure((size_t)nsys * 4));
+    CK(nl->sys_hcap.ensure((size_t)nsys * 4));
+    CK(cudaMemcpyAsync(nl->sys_off.p, off.data(), (size_t)(nsys + 1) * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(nl->sys_pad.p, pad.data(), (size_t)(nsys + 1) * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(nl->sys_box.p, dbox.data(), (size_t)nsys * sizeof(DevBox),
+                       cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(nl->sys_hcap.p, hcap.data(), (size_t)nsys * 4, cudaMemcpyHostToDevice, s));
+    const SysTables T = nl->tables();
     Status *dst = nl->status.as<Status>();
     CK(cudaMemsetAsync(dst, 0, sizeof(Status), s));
 
     // 1. keys (+ validation), 2. stable sort, 3. permute + cluster boxes
     CK(nl->mark(0, s));
-    CK(launch_keys(n, x, y, z, h, nl->dbox, p->support, p->key, nl->keys.as<uint64_t>(),
-                   nl->vals.as<uint32_t>(), dst, s));
+    CK(launch_keys_batch(n, x, y, z, h, T, p->support, p->key, nl->keys.as<uint64_t>(),
+                         nl->vals.as<uint32_t>(), dst, s));
     CK(nl->mark(1, s));
     CK(radix_sort_pairs(nl->keys.as<uint64_t>(), nl->vals.as<uint32_t>(),
                         nl->keys_alt.as<uint64_t>(), nl->vals_alt.as<uint32_t>(), N,
                         3 * kKeyBits, nl->hist.as<uint32_t>(), s));
+    CK(radix_sort_by_system(nl->keys.as<uint64_t>(), nl->vals.as<uint32_t>(),
+                            nl->keys_alt.as<uint64_t>(), nl->vals_alt.as<uint32_t>(), N,
+                            nl->sys_off.as<uint32_t>(), (uint32_t)nsys, nl->hist.as<uint32_t>(), s));
     CK(nl->mark(2, s));
-    CK(launch_permute(N, npad, M, nl->vals.as<uint32_t>(), x, y, z, h, p->support,
-                      nl->pos.as<float4>(), nl->clo.as<float4>(), nl->chi.as<float4>(), s));
-    // 4. octree leaves
+    CK(launch_permute(npad, M, T, nl->vals.as<uint32_t>(), x, y, z, h, p->support,
+                      nl->pos.as<float4>(), nl->perm_pad.as<uint32_t>(), nl->clo.as<float4>(),
+                      nl->chi.as<float4>(), s));
+    // 4. octree
     CK(nl->mark(3, s));
-    CK(octree_leaves(nl->keys.as<uint64_t>(), N, p->leaf_bucket, nl->lcp.as<uint8_t>(),
+    CK(octree_leaves(nl->keys.as<uint64_t>(), N, p->leaf_bucket, T, nl->lcp.as<uint8_t>(),
                      nl->lev.as<uint8_t>(), nl->leaf_first.as<uint32_t>(),
                      nl->leaf_lev.as<uint8_t>(), nl->bsum.as<uint32_t>(), dst, s));
-    st = read_status(nl, s);
+    nl_status st = read_status(nl, s);
     if (st != NL_OK) return st;
-    if (nl->hst->bad_input) {
+    if (nl->hst->bad_input & 7u) {
         unsigned b = nl->hst->bad_input;
         return fail(NL_ERR_ARG, "invalid particle input:%s%s%s", (b & 1) ? " non-finite coordinate" : "",
                     (b & 2) ? " coordinate outside the box" : "", (b & 4) ? " h <= 0 or non-finite" : "");
     }
-    const float rmax = __builtin_bit_cast(float, nl->hst->rmax_bits);
-    for (int a = 0; a < 3; ++a)
-        if (box->periodic[a] && !(rmax < nl->dbox.half[a]))
-            return fail(NL_ERR_RADIUS, "support*max(h) = %g >= L/2 = %g on periodic axis %d",
-                        (double)rmax, (double)nl->dbox.half[a], a);
+    if (nl->hst->bad_input & 8u)
+        return fail(NL_ERR_RADIUS, "support*h >= L/2 on a periodic axis for some particle");
     const uint32_t nleaves = nl->hst->n_leaves;
-    CK(octree_count_nodes(nl->keys.as<uint64_t>(), nleaves, nl->leaf_first.as<uint32_t>(),
+    CK(octree_count_nodes(nl->keys.as<uint64_t>(), nleaves, T, nl->leaf_first.as<uint32_t>(),
                           nl->leaf_lev.as<uint8_t>(), nl->nodeoff.as<uint32_t>(),
                           nl->bsum.as<uint32_t>(), dst, s));
     st = read_status(nl, s);
@@ -283,12 +343,9 @@ nl_status do_prep(nl_list *nl, const float *x, const float *y, const float *z, c
     CK(nl->nparent.ensure((size_t)nnodes * 4));
     CK(nl->nchild.ensure((size_t)nnodes * 4));
     CK(nl->narrive.ensure((size_t)nnodes * 4));
-    OctreeOut oo{nl->nlo.as<float4>(), nl->nhi.as<float4>(), nl->nrng.as<int2>(),
-                 nl->nlevel.as<uint8_t>(), nl->nparent.as<int32_t>(), nl->nchild.as<uint32_t>(),
-                 nl->narrive.as<uint32_t>()};
-    CK(octree_emit(nl->keys.as<uint64_t>(), N, nleaves, nnodes, nl->leaf_first.as<uint32_t>(),
+    CK(octree_emit(nl->keys.as<uint64_t>(), N, nleaves, nnodes, T, nl->leaf_first.as<uint32_t>(),
                    nl->leaf_lev.as<uint8_t>(), nl->nodeoff.as<uint32_t>(), nl->pos.as<float4>(),
-                   p->support, oo, s));
+                   p->support, nl->octree_out(), s));
     nl->npad = npad;
     nl->ncl = ncl;
     nl->nsc = nsc;
@@ -331,7 +388,7 @@ nl_status do_search(nl_list *nl, cudaStream_t s)
     sa.n = N;
     sa.nsc = nsc;
     sa.nnodes = nnodes;
-    sa.box = nl->dbox;
+    sa.sys = nl->tables();
     sa.support = p->support;
     sa.compress = p->compress;
     sa.st = dst;
@@ -403,9 +460,10 @@ nl_status do_search(nl_list *nl, cudaStream_t s)
 }
 
 nl_status do_build(nl_list *nl, const float *x, const float *y, const float *z, const float *h,
-                   int64_t n, const nl_box *box, const nl_params *p, cudaStream_t s)
+                   int64_t n, int32_t nsys, const int64_t *offs, const nl_box *boxes,
+                   const nl_params *p, cudaStream_t s)
 {
-    nl_status st = do_prep(nl, x, y, z, h, n, box, p, s);
+    nl_status st = do_prep(nl, x, y, z, h, n, nsys, offs, boxes, p, s);
     if (st != NL_OK) return st;
     return do_search(nl, s);
 }
@@ -423,11 +481,11 @@ PassArgs pass_args(const nl_list *nl)
     a.pos = nl->pos.as<float4>();
     a.list = nl->list.as<uint8_t>();
     a.rec_off = nl->rec_off.as<uint32_t>();
-    a.perm = nl->vals.as<uint32_t>();
+    a.perm = nl->perm_pad.as<uint32_t>();
     a.aux = nl->aux.as<float2>();
     a.n = (uint32_t)nl->n;
     a.nsc = nl->nsc;
-    a.box = nl->dbox;
+    a.sys = nl->tables();
     a.support = nl->p.support;
     a.compress = nl->p.compress;
     a.st = nl->status.as<Status>();
@@ -454,10 +512,43 @@ nl_status nl_rebuild(nl_list *nl, const float *x, const float *y, const float *z
                      int64_t n, const nl_box *box, const nl_params *p, void *stream)
 {
     if (!nl) return fail(NL_ERR_ARG, "list is NULL");
+    if (!box) return fail(NL_ERR_ARG, "box is NULL");
     nl->n = 0;
-    nl_status st = do_build(nl, x, y, z, h, n, box, p, (cudaStream_t)stream);
+    const int64_t offs[2] = {0, n};
+    nl_status st = do_build(nl, x, y, z, h, n, 1, offs, box, p, (cudaStream_t)stream);
     if (st != NL_OK) nl->n = 0;
     return st;
+}
+
+nl_status nl_rebuild_batch(nl_list *nl, const float *x, const float *y, const float *z,
+                           const float *h, int32_t nsys, const int64_t *offsets,
+                           const nl_box *boxes, const nl_params *p, void *stream)
+{
+    if (!nl) return fail(NL_ERR_ARG, "list is NULL");
+    if (!offsets || nsys < 1) return fail(NL_ERR_ARG, "need nsys >= 1 and offsets");
+    nl->n = 0;
+    nl_status st = do_build(nl, x, y, z, h, offsets[nsys], nsys, offsets, boxes, p,
+                            (cudaStream_t)stream);
+    if (st != NL_OK) nl->n = 0;
+    return st;
+}
+
+nl_status nl_build_batch(const float *x, const float *y, const float *z, const float *h,
+                         int32_t nsys, const int64_t *offsets, const nl_box *boxes,
+                         const nl_params *p, void *stream, nl_list **out)
+{
+    if (!out) return fail(NL_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    nl_list *nl = new (std::nothrow) nl_list();
+    if (!nl) return fail(NL_ERR_OOM, "host allocation failed");
+    nl_status st = nl_rebuild_batch(nl, x, y, z, h, nsys, offsets, boxes, p, stream);
+    if (st != NL_OK) {
+        nl->release_all();
+        delete nl;
+        return st;
+    }
+    *out = nl;
+    return NL_OK;
 }
 
 nl_status nl_build(const float *x, const float *y, const float *z, const float *h, int64_t n,
@@ -532,10 +623,11 @@ nl_status nl_density_from_host(nl_list *nl, const float *x, const float *y, cons
     return NL_OK;
 }
 
-nl_status nl_iterate_h(nl_list *nl, const float *x, const float *y, const float *z, float *h,
-                       int64_t n, const nl_box *box, const nl_params *p, float n_target, float tol,
-                       int32_t max_iter, float margin, int32_t start, uint8_t *converged,
-                       nl_hiter_info *info, void *stream)
+static nl_status do_iterate_h(nl_list *nl, const float *x, const float *y, const float *z,
+                              float *h, int64_t n, int32_t nsys, const int64_t *offs,
+                              const nl_box *boxes, const nl_params *p, float n_target, float tol,
+                              int32_t max_iter, float margin, int32_t start, uint8_t *converged,
+                              nl_hiter_info *info, cudaStream_t s)
 {
     if (!nl) return fail(NL_ERR_ARG, "list is NULL");
     if (!h) return fail(NL_ERR_ARG, "h is NULL");
@@ -544,7 +636,6 @@ nl_status nl_iterate_h(nl_list *nl, const float *x, const float *y, const float 
     if (start != NL_HSTART_GIVEN && start != NL_HSTART_PLAIN)
         return fail(NL_ERR_ARG, "unknown start %d", start);
     if (n < 1 || n > (int64_t)1 << 30) return fail(NL_ERR_ARG, "bad n %lld", (long long)n);
-    cudaStream_t s = (cudaStream_t)stream;
     nl->n = 0;
     const uint32_t N = (uint32_t)n;
     const float *hin = h;
@@ -553,46 +644,43 @@ nl_status nl_iterate_h(nl_list *nl, const float *x, const float *y, const float 
         CK(launch_fill(nl->it_tmp.as<float>(), N, 1e-30f, s));
         hin = nl->it_tmp.as<float>();
     }
-    nl_status st = do_prep(nl, x, y, z, hin, n, box, p, s);
+    nl_status st = do_prep(nl, x, y, z, hin, n, nsys, offs, boxes, p, s);
     if (st != NL_OK) return st;
     const int M = p->cluster;
-    const uint32_t nsc = nl->nsc;
-    CK(nl->it_hq.ensure((size_t)N * 4));
-    CK(nl->it_hlo.ensure((size_t)N * 4));
-    CK(nl->it_hhi.ensure((size_t)N * 4));
-    CK(nl->it_hs.ensure((size_t)N * 4));
-    CK(nl->it_counts.ensure((size_t)N * 4));
-    CK(nl->it_conv.ensure((size_t)N));
+    const uint32_t nsc = nl->nsc, npad = nl->npad;
+    CK(nl->it_hq.ensure((size_t)npad * 4));
+    CK(nl->it_hlo.ensure((size_t)npad * 4));
+    CK(nl->it_hhi.ensure((size_t)npad * 4));
+    CK(nl->it_hs.ensure((size_t)npad * 4));
+    CK(nl->it_counts.ensure((size_t)npad * 4));
+    CK(nl->it_conv.ensure((size_t)npad));
     CK(nl->it_aflag.ensure((size_t)nsc * 4));
     CK(nl->it_alist.ensure((size_t)nsc * 4));
     CK(nl->it_words.ensure(16));
+    const SysTables T = nl->tables();
     HIterState hs{nl->it_hq.as<float>(), nl->it_hlo.as<float>(), nl->it_hhi.as<float>(),
                   nl->it_hs.as<float>(), nl->it_counts.as<uint32_t>(), nl->it_conv.as<uint8_t>(),
                   nl->it_aflag.as<uint32_t>(), nl->it_alist.as<uint32_t>(),
-                  nl->it_words.as<unsigned int>()};
+                  nl->it_words.as<unsigned int>(), nl->perm_pad.as<uint32_t>(),
+                  nl->sys_hcap.as<float>()};
     if (start == NL_HSTART_GIVEN)
-        CK(launch_pos_h_to(N, nl->pos.as<float4>(), hs.hq, s));
+        CK(launch_pos_h_to(npad, nl->pos.as<float4>(), hs.hq, s));
     else
-        CK(launch_plain_h0(N, nsc, M, nl->clo.as<float4>(), nl->chi.as<float4>(), n_target, hs.hq, s));
-    CK(cudaMemsetAsync(hs.hlo, 0, (size_t)N * 4, s));
-    CK(launch_fill(hs.hhi, N, INFINITY, s));
-    CK(cudaMemsetAsync(hs.conv, 0, (size_t)N, s));
+        CK(launch_plain_h0(nsc, M, hs.perm_pad, nl->clo.as<float4>(), nl->chi.as<float4>(),
+                           n_target, hs.hq, s));
+    CK(cudaMemsetAsync(hs.hlo, 0, (size_t)npad * 4, s));
+    CK(launch_fill(hs.hhi, npad, INFINITY, s));
+    CK(cudaMemsetAsync(hs.conv, 0, (size_t)npad, s));
     CK(cudaMemsetAsync(hs.active_flag, 0, (size_t)nsc * 4, s));
-    // largest h whose search radius stays below half a periodic box length
-    float hcap = 3.0e38f;
-    for (int a = 0; a < 3; ++a)
-        if (box->periodic[a]) hcap = std::min(hcap, nl->dbox.half[a] / (p->support * (1.f + margin)) * 0.999999f);
-    OctreeOut oo{nl->nlo.as<float4>(), nl->nhi.as<float4>(), nl->nrng.as<int2>(),
-                 nl->nlevel.as<uint8_t>(), nl->nparent.as<int32_t>(), nl->nchild.as<uint32_t>(),
-                 nl->narrive.as<uint32_t>()};
+    const OctreeOut oo = nl->octree_out();
     bool rebuild = true, first = true;
     int iters = 0, rebuilds = 0;
     unsigned int words[4] = {0, 0, 0, 0};
     for (; iters < max_iter;) {
         if (rebuild) {
-            CK(launch_hsearch(N, hs.hq, margin, hcap, hs.hs, s));
-            CK(launch_pos_h(N, hs.hs, nl->pos.as<float4>(), s));
-            CK(launch_cluster_boxes(nl->npad, M, nl->pos.as<float4>(), p->support,
+            CK(launch_hsearch(npad, hs.hq, margin, hs.hcap_sys, T, hs.hs, s));
+            CK(launch_pos_h(npad, hs.hs, nl->pos.as<float4>(), s));
+            CK(launch_cluster_boxes(npad, M, nl->pos.as<float4>(), p->support,
                                     nl->clo.as<float4>(), nl->chi.as<float4>(), s));
             CK(octree_boxes(nl->n_nodes, nl->pos.as<float4>(), p->support, oo, s));
             st = do_search(nl, s);
@@ -611,14 +699,14 @@ nl_status nl_iterate_h(nl_list *nl, const float *x, const float *y, const float 
         ++iters;
         first = false;
         CK(cudaMemsetAsync(hs.words, 0, 16, s));
-        CK(launch_hupdate(N, M, n_target, tol, hcap, hs, s));
+        CK(launch_hupdate(npad, M, n_target, tol, T, hs, s));
         CK(launch_active_list(nsc, hs, s));
         CK(cudaMemcpyAsync(words, hs.words, 16, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (words[0] == 0) break;
         rebuild = words[1] != 0;
     }
-    CK(launch_scatter_h(N, nl->vals.as<uint32_t>(), hs.hq, hs.conv, h, converged, s));
+    CK(launch_scatter_h(npad, hs.perm_pad, hs.hq, hs.conv, h, converged, s));
     CK(cudaStreamSynchronize(s));
     if (info) {
         info->iterations = iters;
@@ -629,6 +717,28 @@ nl_status nl_iterate_h(nl_list *nl, const float *x, const float *y, const float 
         return fail(NL_ERR_NOT_CONVERGED, "%u particles outside the neighbor window after %d passes",
                     words[0], iters);
     return NL_OK;
+}
+
+nl_status nl_iterate_h(nl_list *nl, const float *x, const float *y, const float *z, float *h,
+                       int64_t n, const nl_box *box, const nl_params *p, float n_target, float tol,
+                       int32_t max_iter, float margin, int32_t start, uint8_t *converged,
+                       nl_hiter_info *info, void *stream)
+{
+    if (!box) return fail(NL_ERR_ARG, "box is NULL");
+    const int64_t offs[2] = {0, n};
+    return do_iterate_h(nl, x, y, z, h, n, 1, offs, box, p, n_target, tol, max_iter, margin, start,
+                        converged, info, (cudaStream_t)stream);
+}
+
+nl_status nl_iterate_h_batch(nl_list *nl, const float *x, const float *y, const float *z, float *h,
+                             int32_t nsys, const int64_t *offsets, const nl_box *boxes,
+                             const nl_params *p, float n_target, float tol, int32_t max_iter,
+                             float margin, int32_t start, uint8_t *converged, nl_hiter_info *info,
+                             void *stream)
+{
+    if (!offsets || nsys < 1) return fail(NL_ERR_ARG, "need nsys >= 1 and offsets");
+    return do_iterate_h(nl, x, y, z, h, offsets[nsys], nsys, offsets, boxes, p, n_target, tol,
+                        max_iter, margin, start, converged, info, (cudaStream_t)stream);
 }
 
 nl_status nl_free(nl_list *nl)
@@ -649,8 +759,8 @@ nl_status nl_density_pass(const nl_list *cnl, const float *m, float *rho, void *
     cudaStream_t s = (cudaStream_t)stream;
     CK(nl->aux.ensure((size_t)nl->npad * 8));
     CK(nl->mark(5, s));
-    CK(launch_gather_aux((uint32_t)nl->n, nl->npad, nl->vals.as<uint32_t>(), m, nullptr, nullptr,
-                         0, nl->aux.as<float2>(), s));
+    CK(launch_gather_aux(nl->npad, nl->perm_pad.as<uint32_t>(), m, nullptr, nullptr, 0,
+                         nl->aux.as<float2>(), s));
     CK(nl->mark(6, s));
     PassArgs a = pass_args(nl);
     a.out0 = rho;
@@ -678,7 +788,7 @@ nl_status nl_force_pass(const nl_list *cnl, int32_t kind, const float *params, c
     a.out2 = az;
     if (kind == NL_FORCE_SPH_PRESSURE) {
         CK(nl->mark(5, s));
-        CK(launch_gather_aux((uint32_t)nl->n, nl->npad, nl->vals.as<uint32_t>(), m, pres, rho, 1,
+        CK(launch_gather_aux(nl->npad, nl->perm_pad.as<uint32_t>(), m, pres, rho, 1,
                              nl->aux.as<float2>(), s));
         CK(nl->mark(6, s));
         CK(launch_pass(a, PASS_SPH, nl->p.cluster, nl->any_per, nl->num_sms, s));

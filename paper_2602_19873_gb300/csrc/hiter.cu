@@ -25,27 +25,28 @@ cudaError_t launch_fill(float *a, uint32_t n, float v, cudaStream_t s)
     return cudaGetLastError();
 }
 
-__global__ void k_pos_h(uint32_t n, const float *__restrict__ hs, float4 *__restrict__ pos)
+// (dummy slots carry h = 0 in both directions)
+__global__ void k_pos_h(uint32_t npad, const float *__restrict__ hs, float4 *__restrict__ pos)
 {
     uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) pos[k].w = hs[k];
+    if (k < npad) pos[k].w = hs[k];
 }
 
-cudaError_t launch_pos_h(uint32_t n, const float *hs, float4 *pos, cudaStream_t s)
+cudaError_t launch_pos_h(uint32_t npad, const float *hs, float4 *pos, cudaStream_t s)
 {
-    k_pos_h<<<(n + 255) / 256, 256, 0, s>>>(n, hs, pos);
+    k_pos_h<<<(npad + 255) / 256, 256, 0, s>>>(npad, hs, pos);
     return cudaGetLastError();
 }
 
-__global__ void k_pos_h_to(uint32_t n, const float4 *__restrict__ pos, float *__restrict__ hq)
+__global__ void k_pos_h_to(uint32_t npad, const float4 *__restrict__ pos, float *__restrict__ hq)
 {
     uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) hq[k] = pos[k].w;
+    if (k < npad) hq[k] = pos[k].w;
 }
 
-cudaError_t launch_pos_h_to(uint32_t n, const float4 *pos, float *hq, cudaStream_t s)
+cudaError_t launch_pos_h_to(uint32_t npad, const float4 *pos, float *hq, cudaStream_t s)
 {
-    k_pos_h_to<<<(n + 255) / 256, 256, 0, s>>>(n, pos, hq);
+    k_pos_h_to<<<(npad + 255) / 256, 256, 0, s>>>(npad, pos, hq);
     return cudaGetLastError();
 }
 
@@ -96,8 +97,9 @@ cudaError_t launch_cluster_boxes(uint32_t npad, int M, const float4 *pos, float 
 // Plain start: the 8*M particles of a super-cluster fill (about) its box,
 // so the number density there is count / volume and the sphere of radius
 // 2h holds n_t particles for h = 0.5 * (3 n_t V / (4 pi count))^(1/3).
-__global__ void k_plain_h0(uint32_t n, uint32_t nsc, int M, const float4 *__restrict__ clo,
-                           const float4 *__restrict__ chi, float n_target, float *__restrict__ hq)
+__global__ void k_plain_h0(uint32_t nsc, int M, const uint32_t *__restrict__ perm_pad,
+                           const float4 *__restrict__ clo, const float4 *__restrict__ chi,
+                           float n_target, float *__restrict__ hq)
 {
     uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nsc) return;
@@ -107,43 +109,49 @@ __global__ void k_plain_h0(uint32_t n, uint32_t nsc, int M, const float4 *__rest
         lx = fminf(lx, a.x); ly = fminf(ly, a.y); lz = fminf(lz, a.z);
         hx = fmaxf(hx, b.x); hy = fmaxf(hy, b.y); hz = fmaxf(hz, b.z);
     }
-    uint32_t first = s * kSC * M, last = min(n, first + kSC * M);
-    float cnt = (float)(last - first);
+    const uint32_t first = s * kSC * M, last = first + kSC * M;
+    uint32_t real = 0;
+    for (uint32_t k = first; k < last; ++k) real += perm_pad[k] != 0xffffffffu;
+    float cnt = (float)real;
     float ex = fmaxf(hx - lx, 0.f), ey = fmaxf(hy - ly, 0.f), ez = fmaxf(hz - lz, 0.f);
     float emax = fmaxf(ex, fmaxf(ey, ez));
     float floor_e = fmaxf(emax * 1e-2f, 1e-30f);  // flat or collinear groups
     float vol = fmaxf(ex, floor_e) * fmaxf(ey, floor_e) * fmaxf(ez, floor_e);
     float h = 0.5f * cbrtf(3.f * n_target * vol / (4.f * 3.14159265f * fmaxf(cnt, 1.f)));
     if (!(h > 0.f) || !isfinite(h)) h = 1e-6f;
-    for (uint32_t k = first; k < last; ++k) hq[k] = h;
+    for (uint32_t k = first; k < last; ++k) hq[k] = perm_pad[k] != 0xffffffffu ? h : 0.f;
 }
 
-cudaError_t launch_plain_h0(uint32_t n, uint32_t nsc, int M, const float4 *clo, const float4 *chi,
-                            float n_target, float *hq, cudaStream_t s)
+cudaError_t launch_plain_h0(uint32_t nsc, int M, const uint32_t *perm_pad, const float4 *clo,
+                            const float4 *chi, float n_target, float *hq, cudaStream_t s)
 {
-    k_plain_h0<<<(nsc + 127) / 128, 128, 0, s>>>(n, nsc, M, clo, chi, n_target, hq);
+    k_plain_h0<<<(nsc + 127) / 128, 128, 0, s>>>(nsc, M, perm_pad, clo, chi, n_target, hq);
     return cudaGetLastError();
 }
 
-__global__ void k_hsearch(uint32_t n, const float *__restrict__ hq, float margin, float hcap,
-                          float *__restrict__ hs)
+__global__ void k_hsearch(uint32_t npad, const float *__restrict__ hq, float margin,
+                          const float *__restrict__ hcap_sys, SysTables t, float *__restrict__ hs)
 {
     uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) hs[k] = fminf(hq[k] * (1.f + margin), hcap);
+    if (k < npad) hs[k] = fminf(hq[k] * (1.f + margin), hcap_sys[sys_of(t.pad_off, t.nsys, k)]);
 }
 
-cudaError_t launch_hsearch(uint32_t n, const float *hq, float margin, float hcap, float *hs,
-                           cudaStream_t s)
+cudaError_t launch_hsearch(uint32_t npad, const float *hq, float margin, const float *hcap_sys,
+                           const SysTables &t, float *hs, cudaStream_t s)
 {
-    k_hsearch<<<(n + 255) / 256, 256, 0, s>>>(n, hq, margin, hcap, hs);
+    k_hsearch<<<(npad + 255) / 256, 256, 0, s>>>(npad, hq, margin, hcap_sys, t, hs);
     return cudaGetLastError();
 }
 
-__global__ void k_hupdate(uint32_t n, int M, float n_target, float tol, float hcap, HIterState h)
+// hcap_sys[s] is the largest h whose radius stays below half a periodic box
+// length of system s; it bounds both the iterated h and the search h.
+__global__ void k_hupdate(uint32_t npad, int M, float n_target, float tol, SysTables t,
+                          HIterState h)
 {
     uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     bool act = false, reb = false;
-    if (k < n && !h.conv[k]) {
+    if (k < npad && h.perm_pad[k] != 0xffffffffu && !h.conv[k]) {
+        const float hcap = h.hcap_sys[sys_of(t.pad_off, t.nsys, k)];
         float c = (float)h.counts[k];
         float hv = h.hq[k];
         if (fabsf(c - n_target) <= tol) {
@@ -175,10 +183,10 @@ __global__ void k_hupdate(uint32_t n, int M, float n_target, float tol, float hc
     }
 }
 
-cudaError_t launch_hupdate(uint32_t n, int M, float n_target, float tol, float hcap,
+cudaError_t launch_hupdate(uint32_t npad, int M, float n_target, float tol, const SysTables &t,
                            const HIterState &h, cudaStream_t s)
 {
-    k_hupdate<<<(n + 255) / 256, 256, 0, s>>>(n, M, n_target, tol, hcap, h);
+    k_hupdate<<<(npad + 255) / 256, 256, 0, s>>>(npad, M, n_target, tol, t, h);
     return cudaGetLastError();
 }
 
@@ -202,21 +210,22 @@ cudaError_t launch_active_list(uint32_t nsc, const HIterState &h, cudaStream_t s
     return cudaGetLastError();
 }
 
-__global__ void k_scatter_h(uint32_t n, const uint32_t *__restrict__ perm, const float *__restrict__ hq,
-                            const uint8_t *__restrict__ conv, float *__restrict__ h_out,
-                            uint8_t *__restrict__ conv_out)
+__global__ void k_scatter_h(uint32_t npad, const uint32_t *__restrict__ perm_pad,
+                            const float *__restrict__ hq, const uint8_t *__restrict__ conv,
+                            float *__restrict__ h_out, uint8_t *__restrict__ conv_out)
 {
     uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    uint32_t o = perm[k];
+    if (k >= npad) return;
+    const uint32_t o = perm_pad[k];
+    if (o == 0xffffffffu) return;
     h_out[o] = hq[k];
     if (conv_out) conv_out[o] = conv[k];
 }
 
-cudaError_t launch_scatter_h(uint32_t n, const uint32_t *perm, const float *hq, const uint8_t *conv,
-                             float *h_out, uint8_t *conv_out, cudaStream_t s)
+cudaError_t launch_scatter_h(uint32_t npad, const uint32_t *perm_pad, const float *hq,
+                             const uint8_t *conv, float *h_out, uint8_t *conv_out, cudaStream_t s)
 {
-    k_scatter_h<<<(n + 255) / 256, 256, 0, s>>>(n, perm, hq, conv, h_out, conv_out);
+    k_scatter_h<<<(npad + 255) / 256, 256, 0, s>>>(npad, perm_pad, hq, conv, h_out, conv_out);
     return cudaGetLastError();
 }
 

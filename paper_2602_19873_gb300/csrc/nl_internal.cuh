@@ -20,6 +20,31 @@ struct DevBox {
     int per[3];
 };
 
+// Tables of a batch of independent systems (a single system is a batch of
+// one).  Caller arrays hold the systems back to back: system s owns caller
+// (and, after the sort, sorted) indices [off[s], off[s+1]).  In SFC-sorted
+// padded order every system starts on a super-cluster boundary: system s
+// owns padded indices [pad_off[s], pad_off[s+1]), the tail filled with NaN
+// dummies.  root[s] is the index of the system's octree root.
+struct SysTables {
+    const uint32_t *off;
+    const uint32_t *pad_off;
+    const DevBox *box;
+    uint32_t *root;
+    uint32_t nsys;
+};
+
+// system owning index k of an offset table t (t[0] = 0, t[nsys] = total)
+__device__ __forceinline__ uint32_t sys_of(const uint32_t *t, uint32_t nsys, uint32_t k)
+{
+    uint32_t lo = 0, hi = nsys;  // invariant: t[lo] <= k < t[hi]
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (t[mid] <= k) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
 // Device status words written by the build kernels and read back once.
 struct Status {
     unsigned int bad_input;   // bit0 non-finite coordinate, bit1 outside box, bit2 bad h
@@ -318,41 +343,52 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *sh, ui
 cudaError_t launch_keys(int64_t n, const float *x, const float *y, const float *z, const float *h,
                         const DevBox &box, float support, int kind, uint64_t *keys, uint32_t *vals,
                         Status *st, cudaStream_t s);
+// batch form: each particle uses its own system's box
+cudaError_t launch_keys_batch(int64_t n, const float *x, const float *y, const float *z,
+                              const float *h, const SysTables &t, float support, int kind,
+                              uint64_t *keys, uint32_t *vals, Status *st, cudaStream_t s);
 
 // Stable LSD radix sort of (key, value) pairs on the low `bits` key bits.
 // Scratch: keys_alt/vals_alt (n each), hist (radix_hist_words(n) words).
 size_t radix_hist_words(uint32_t n);
 cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
                              uint32_t n, int bits, uint32_t *hist, cudaStream_t s);
+// Final stable passes by system (digit = system of the value, a caller index):
+// sorts (system, key) when run after radix_sort_pairs.
+cudaError_t radix_sort_by_system(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
+                                 uint32_t *vals_alt, uint32_t n, const uint32_t *sys_off,
+                                 uint32_t nsys, uint32_t *hist, cudaStream_t s);
 
-// Permute into SFC order as float4 (x, y, z, h), NaN dummies up to npad,
-// and per-cluster boxes: clo = (lo, max r), chi = (hi, 0).
-cudaError_t launch_permute(uint32_t n, uint32_t npad, int M, const uint32_t *perm, const float *x,
-                           const float *y, const float *z, const float *h, float support,
-                           float4 *pos, float4 *clo, float4 *chi, cudaStream_t s);
+// Permute into padded SFC order as float4 (x, y, z, h) with NaN dummies,
+// record the caller index of every padded slot (perm_pad, ~0 for dummies),
+// and per-cluster boxes: clo = (lo, max r), chi = (hi, min r).
+cudaError_t launch_permute(uint32_t npad, int M, const SysTables &t, const uint32_t *perm,
+                           const float *x, const float *y, const float *z, const float *h,
+                           float support, float4 *pos, uint32_t *perm_pad, float4 *clo,
+                           float4 *chi, cudaStream_t s);
 
 // Octree, steps 1-2: leaf level per particle, leaf starts; n_leaves lands
 // in st->n_leaves.  Scratch: lev (n bytes), bsum (scan_bsum_words(n)).
 size_t scan_bsum_words(uint32_t n);
-cudaError_t octree_leaves(const uint64_t *keys, uint32_t n, int bucket, uint8_t *lcp,
-                          uint8_t *lev, uint32_t *leaf_first, uint8_t *leaf_lev, uint32_t *bsum,
-                          Status *st, cudaStream_t s);
+cudaError_t octree_leaves(const uint64_t *keys, uint32_t n, int bucket, const SysTables &t,
+                          uint8_t *lcp, uint8_t *lev, uint32_t *leaf_first, uint8_t *leaf_lev,
+                          uint32_t *bsum, Status *st, cudaStream_t s);
 // step 3: node offsets per leaf; n_nodes lands in st->n_nodes.
-cudaError_t octree_count_nodes(const uint64_t *keys, uint32_t n_leaves, const uint32_t *leaf_first,
-                               const uint8_t *leaf_lev, uint32_t *nodeoff, uint32_t *bsum,
-                               Status *st, cudaStream_t s);
+cudaError_t octree_count_nodes(const uint64_t *keys, uint32_t n_leaves, const SysTables &t,
+                               const uint32_t *leaf_first, const uint8_t *leaf_lev,
+                               uint32_t *nodeoff, uint32_t *bsum, Status *st, cudaStream_t s);
 // step 4: emit pre-order nodes and their boxes.
 struct OctreeOut {
     float4 *nlo;      // (lo.xyz, max r)
     float4 *nhi;      // (hi.xyz, skip as int bits)
-    int2 *nrng;       // (first, end) particle range
+    int2 *nrng;       // (first, end) particle range in padded indices
     uint8_t *nlevel;
     int32_t *nparent;
     uint32_t *nchild;
     uint32_t *narrive;
 };
 cudaError_t octree_emit(const uint64_t *keys, uint32_t n, uint32_t n_leaves, uint32_t n_nodes,
-                        const uint32_t *leaf_first, const uint8_t *leaf_lev,
+                        const SysTables &t, const uint32_t *leaf_first, const uint8_t *leaf_lev,
                         const uint32_t *nodeoff, const float4 *pos, float support,
                         const OctreeOut &o, cudaStream_t s);
 
@@ -362,7 +398,7 @@ struct SearchArgs {
     const float4 *nlo, *nhi;
     const int2 *nrng;
     uint32_t n, nsc, nnodes;
-    DevBox box;
+    SysTables sys;
     float support;
     uint32_t *stageJ;
     uint8_t *stageM;
@@ -382,10 +418,10 @@ struct PassArgs {
     const float4 *pos;
     const uint8_t *list;
     const uint32_t *rec_off;
-    const uint32_t *perm;
-    const float2 *aux;     // per sorted particle: density m; SPH (m, P/rho^2)
+    const uint32_t *perm;  // caller index of every padded slot, ~0 for dummies
+    const float2 *aux;     // per padded particle: density m; SPH (m, P/rho^2)
     uint32_t n, nsc;
-    DevBox box;
+    SysTables sys;
     float support;
     int compress;
     float p0, p1;          // LJ: eps, sigma
@@ -399,8 +435,8 @@ struct PassArgs {
 };
 cudaError_t launch_pass(const PassArgs &a, int kind, int M, int any_periodic, int num_sms,
                         cudaStream_t s);
-// aux[k] = (a[perm[k]], b ? b[perm[k]] : 0) for k < n; zero for padding.
-cudaError_t launch_gather_aux(uint32_t n, uint32_t npad, const uint32_t *perm, const float *a,
+// aux[k] = (a[perm[k]], ...) for real padded slots, zero for dummies.
+cudaError_t launch_gather_aux(uint32_t npad, const uint32_t *perm_pad, const float *a,
                               const float *b, const float *c, int mode, float2 *aux,
                               cudaStream_t s);
 
@@ -408,16 +444,16 @@ cudaError_t launch_gather_aux(uint32_t n, uint32_t npad, const uint32_t *perm, c
 cudaError_t octree_boxes(uint32_t n_nodes, const float4 *pos, float support, const OctreeOut &o,
                          cudaStream_t s);
 
-// h iteration helpers (hiter.cu); all arrays in SFC-sorted order.
+// h iteration helpers (hiter.cu); all arrays in padded SFC order (npad).
 cudaError_t launch_fill(float *a, uint32_t n, float v, cudaStream_t s);
-cudaError_t launch_pos_h(uint32_t n, const float *hs, float4 *pos, cudaStream_t s);
-cudaError_t launch_pos_h_to(uint32_t n, const float4 *pos, float *hq, cudaStream_t s);
+cudaError_t launch_pos_h(uint32_t npad, const float *hs, float4 *pos, cudaStream_t s);
+cudaError_t launch_pos_h_to(uint32_t npad, const float4 *pos, float *hq, cudaStream_t s);
 cudaError_t launch_cluster_boxes(uint32_t npad, int M, const float4 *pos, float support,
                                  float4 *clo, float4 *chi, cudaStream_t s);
-cudaError_t launch_plain_h0(uint32_t n, uint32_t nsc, int M, const float4 *clo, const float4 *chi,
-                            float n_target, float *hq, cudaStream_t s);
-cudaError_t launch_hsearch(uint32_t n, const float *hq, float margin, float hcap, float *hs,
-                           cudaStream_t s);
+cudaError_t launch_plain_h0(uint32_t nsc, int M, const uint32_t *perm_pad, const float4 *clo,
+                            const float4 *chi, float n_target, float *hq, cudaStream_t s);
+cudaError_t launch_hsearch(uint32_t npad, const float *hq, float margin, const float *hcap_sys,
+                           const SysTables &t, float *hs, cudaStream_t s);
 struct HIterState {
     float *hq, *hlo, *hhi, *hs;
     uint32_t *counts;
@@ -425,11 +461,13 @@ struct HIterState {
     uint32_t *active_flag;   // per super-cluster
     uint32_t *active_list;
     unsigned int *words;     // [0] unconverged, [1] rebuild needed, [2] active count
+    const uint32_t *perm_pad;
+    const float *hcap_sys;   // per system: largest h keeping the search radius < L/2
 };
-cudaError_t launch_hupdate(uint32_t n, int M, float n_target, float tol, float hcap,
+cudaError_t launch_hupdate(uint32_t npad, int M, float n_target, float tol, const SysTables &t,
                            const HIterState &h, cudaStream_t s);
 cudaError_t launch_active_list(uint32_t nsc, const HIterState &h, cudaStream_t s);
-cudaError_t launch_scatter_h(uint32_t n, const uint32_t *perm, const float *hq, const uint8_t *conv,
-                             float *h_out, uint8_t *conv_out, cudaStream_t s);
+cudaError_t launch_scatter_h(uint32_t npad, const uint32_t *perm_pad, const float *hq,
+                             const uint8_t *conv, float *h_out, uint8_t *conv_out, cudaStream_t s);
 
 }  // namespace nlg

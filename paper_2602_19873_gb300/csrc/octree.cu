@@ -25,33 +25,39 @@ namespace nlg {
 // Permute + cluster boxes
 // ---------------------------------------------------------------------------
 template <int M>
-__global__ void __launch_bounds__(256) k_permute(uint32_t n, uint32_t npad,
+__global__ void __launch_bounds__(256) k_permute(uint32_t npad, SysTables t,
                                                  const uint32_t *__restrict__ perm,
                                                  const float *__restrict__ x,
                                                  const float *__restrict__ y,
                                                  const float *__restrict__ z,
                                                  const float *__restrict__ h, float support,
                                                  float4 *__restrict__ pos,
+                                                 uint32_t *__restrict__ perm_pad,
                                                  float4 *__restrict__ clo,
                                                  float4 *__restrict__ chi)
 {
-    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;  // npad is a multiple of 256
+    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;  // npad is a multiple of 32
     if (k >= npad) return;
+    const uint32_t sy = sys_of(t.pad_off, t.nsys, k);
+    const uint32_t local = k - t.pad_off[sy];
+    const bool real = local < t.off[sy + 1] - t.off[sy];
     float4 p;
     float r;
     const float nan = __int_as_float(0x7fc00000);
-    if (k < n) {
-        uint32_t o = perm[k];
+    if (real) {
+        uint32_t o = perm[t.off[sy] + local];
         p = make_float4(x[o], y[o], z[o], h[o]);
         r = __fmul_rn(support, p.w);
+        perm_pad[k] = o;
     } else {
         p = make_float4(nan, nan, nan, 0.f);
         r = 0.f;
+        perm_pad[k] = 0xffffffffu;
     }
     pos[k] = p;
-    float lx = k < n ? p.x : INFINITY, ly = k < n ? p.y : INFINITY, lz = k < n ? p.z : INFINITY;
-    float hx = k < n ? p.x : -INFINITY, hy = k < n ? p.y : -INFINITY, hz = k < n ? p.z : -INFINITY;
-    float rmin = k < n ? r : INFINITY;
+    float lx = real ? p.x : INFINITY, ly = real ? p.y : INFINITY, lz = real ? p.z : INFINITY;
+    float hx = real ? p.x : -INFINITY, hy = real ? p.y : -INFINITY, hz = real ? p.z : -INFINITY;
+    float rmin = real ? r : INFINITY;
 #pragma unroll
     for (int o = 1; o < M; o <<= 1) {
         rmin = fminf(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
@@ -69,15 +75,16 @@ __global__ void __launch_bounds__(256) k_permute(uint32_t n, uint32_t npad,
     }
 }
 
-cudaError_t launch_permute(uint32_t n, uint32_t npad, int M, const uint32_t *perm, const float *x,
-                           const float *y, const float *z, const float *h, float support,
-                           float4 *pos, float4 *clo, float4 *chi, cudaStream_t s)
+cudaError_t launch_permute(uint32_t npad, int M, const SysTables &t, const uint32_t *perm,
+                           const float *x, const float *y, const float *z, const float *h,
+                           float support, float4 *pos, uint32_t *perm_pad, float4 *clo,
+                           float4 *chi, cudaStream_t s)
 {
     unsigned grid = (npad + 255) / 256;
     switch (M) {
-    case 4: k_permute<4><<<grid, 256, 0, s>>>(n, npad, perm, x, y, z, h, support, pos, clo, chi); break;
-    case 8: k_permute<8><<<grid, 256, 0, s>>>(n, npad, perm, x, y, z, h, support, pos, clo, chi); break;
-    case 16: k_permute<16><<<grid, 256, 0, s>>>(n, npad, perm, x, y, z, h, support, pos, clo, chi); break;
+    case 4: k_permute<4><<<grid, 256, 0, s>>>(npad, t, perm, x, y, z, h, support, pos, perm_pad, clo, chi); break;
+    case 8: k_permute<8><<<grid, 256, 0, s>>>(npad, t, perm, x, y, z, h, support, pos, perm_pad, clo, chi); break;
+    case 16: k_permute<16><<<grid, 256, 0, s>>>(npad, t, perm, x, y, z, h, support, pos, perm_pad, clo, chi); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -164,11 +171,15 @@ static cudaError_t scan_exclusive(F f, S sink, uint32_t n, uint32_t *bsum, uint3
 // ---------------------------------------------------------------------------
 // Step 1: leaf level of every particle
 // ---------------------------------------------------------------------------
-__global__ void k_lcp_window(const uint64_t *__restrict__ keys, uint32_t n, int B,
+// lcp level of the window [s, s+B], 0xff when it spans two systems
+__global__ void k_lcp_window(const uint64_t *__restrict__ keys, uint32_t n, int B, SysTables t,
                              uint8_t *__restrict__ lcp)
 {
     uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s + (uint32_t)B < n) lcp[s] = (uint8_t)lcp_level(keys[s], keys[s + B]);
+    if (s + (uint32_t)B < n) {
+        bool same = t.nsys == 1 || sys_of(t.off, t.nsys, s) == sys_of(t.off, t.nsys, s + B);
+        lcp[s] = same ? (uint8_t)lcp_level(keys[s], keys[s + B]) : (uint8_t)0xffu;
+    }
 }
 
 constexpr int LL_THREADS = 512;
@@ -188,16 +199,12 @@ __global__ void __launch_bounds__(LL_THREADS) k_leaf_level(const uint8_t *__rest
     __syncthreads();
     int64_t k = k0 + threadIdx.x;
     if (k >= n) return;
-    if ((int64_t)n <= B) {
-        lev[k] = 0;
-        return;
-    }
     int m = -1;
     for (int t = 0; t <= B; ++t) {
         uint8_t v = win[threadIdx.x + t];
         if (v != 0xffu && (int)v > m) m = v;
     }
-    int l = m + 1;
+    int l = m + 1;  // no window of B+1 in its system: the system root is a leaf
     lev[k] = (uint8_t)(l > kMaxLevel ? kMaxLevel : l);
 }
 
@@ -207,9 +214,11 @@ __global__ void __launch_bounds__(LL_THREADS) k_leaf_level(const uint8_t *__rest
 struct LeafFlag {
     const uint64_t *keys;
     const uint8_t *lev;
+    SysTables t;
     __device__ uint32_t operator()(uint32_t k) const
     {
         if (k == 0) return 1u;
+        if (t.nsys > 1 && sys_of(t.off, t.nsys, k) != sys_of(t.off, t.nsys, k - 1)) return 1u;
         int l = lev[k];
         if (l != lev[k - 1]) return 1u;
         if (l == 0) return 0u;
@@ -233,35 +242,42 @@ struct LeafSink {
     }
 };
 
-cudaError_t octree_leaves(const uint64_t *keys, uint32_t n, int bucket, uint8_t *lcp,
-                          uint8_t *lev, uint32_t *leaf_first, uint8_t *leaf_lev, uint32_t *bsum,
-                          Status *st, cudaStream_t s)
+cudaError_t octree_leaves(const uint64_t *keys, uint32_t n, int bucket, const SysTables &t,
+                          uint8_t *lcp, uint8_t *lev, uint32_t *leaf_first, uint8_t *leaf_lev,
+                          uint32_t *bsum, Status *st, cudaStream_t s)
 {
     if (n > (uint32_t)bucket)
-        k_lcp_window<<<(n - bucket + 255) / 256, 256, 0, s>>>(keys, n, bucket, lcp);
+        k_lcp_window<<<(n - bucket + 255) / 256, 256, 0, s>>>(keys, n, bucket, t, lcp);
     k_leaf_level<<<(n + LL_THREADS - 1) / LL_THREADS, LL_THREADS, LL_THREADS + bucket, s>>>(
         lcp, n, bucket, lev);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return scan_exclusive(LeafFlag{keys, lev}, LeafSink{lev, n, leaf_first, leaf_lev}, n, bsum,
+    return scan_exclusive(LeafFlag{keys, lev, t}, LeafSink{lev, n, leaf_first, leaf_lev}, n, bsum,
                           &st->n_leaves, s);
 }
 
 // ---------------------------------------------------------------------------
 // Step 3: nodes opened by each leaf
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int leaf_lcp(const uint64_t *keys, const uint32_t *leaf_first, uint32_t i)
+// lcp level of leaf i with the previous leaf; -1 for the first leaf of a
+// system (it opens that system's root)
+__device__ __forceinline__ int leaf_lcp(const uint64_t *keys, const uint32_t *leaf_first,
+                                        const SysTables &t, uint32_t i)
 {
-    return i == 0 ? -1 : lcp_level(keys[leaf_first[i - 1]], keys[leaf_first[i]]);
+    if (i == 0) return -1;
+    const uint32_t a = leaf_first[i - 1], b = leaf_first[i];
+    if (t.nsys > 1 && sys_of(t.off, t.nsys, a) != sys_of(t.off, t.nsys, b)) return -1;
+    return lcp_level(keys[a], keys[b]);
 }
 
 struct NodeCount {
     const uint64_t *keys;
     const uint32_t *leaf_first;
     const uint8_t *leaf_lev;
+    SysTables t;
     __device__ uint32_t operator()(uint32_t i) const
     {
-        return (uint32_t)((int)leaf_lev[i] - leaf_lcp(keys, leaf_first, i));
+        return (uint32_t)((int)leaf_lev[i] - leaf_lcp(keys, leaf_first, t, i));
     }
 };
 
@@ -275,11 +291,11 @@ struct NodeSink {
     }
 };
 
-cudaError_t octree_count_nodes(const uint64_t *keys, uint32_t n_leaves, const uint32_t *leaf_first,
-                               const uint8_t *leaf_lev, uint32_t *nodeoff, uint32_t *bsum,
-                               Status *st, cudaStream_t s)
+cudaError_t octree_count_nodes(const uint64_t *keys, uint32_t n_leaves, const SysTables &t,
+                               const uint32_t *leaf_first, const uint8_t *leaf_lev,
+                               uint32_t *nodeoff, uint32_t *bsum, Status *st, cudaStream_t s)
 {
-    return scan_exclusive(NodeCount{keys, leaf_first, leaf_lev}, NodeSink{n_leaves, nodeoff},
+    return scan_exclusive(NodeCount{keys, leaf_first, leaf_lev, t}, NodeSink{n_leaves, nodeoff},
                           n_leaves, bsum, &st->n_nodes, s);
 }
 
@@ -309,53 +325,57 @@ __device__ __forceinline__ uint32_t leaf_of(const uint32_t *leaf_first, uint32_t
 }
 
 __global__ void k_emit_nodes(const uint64_t *__restrict__ keys, uint32_t n, uint32_t nl,
-                             uint32_t nn, const uint32_t *__restrict__ leaf_first,
+                             uint32_t nn, SysTables t, const uint32_t *__restrict__ leaf_first,
                              const uint8_t *__restrict__ leaf_lev,
                              const uint32_t *__restrict__ nodeoff, OctreeOut o)
 {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nl) return;
-    const int c = leaf_lcp(keys, leaf_first, i);
+    const int c = leaf_lcp(keys, leaf_first, t, i);
     const uint32_t v0 = nodeoff[i], e = nodeoff[i + 1] - v0;
     const uint32_t first = leaf_first[i];
+    const uint32_t sy = sys_of(t.off, t.nsys, first);
+    const uint32_t sbeg = t.off[sy], send = t.off[sy + 1];
+    const int shift_pad = (int)(t.pad_off[sy] - sbeg);  // sorted -> padded index
     const uint64_t kf = keys[first];
-    for (uint32_t t = 0; t < e; ++t) {
-        const uint32_t v = v0 + t;
-        const int l = c + 1 + (int)t;
+    for (uint32_t tt = 0; tt < e; ++tt) {
+        const uint32_t v = v0 + tt;
+        const int l = c + 1 + (int)tt;
         uint32_t end, skip;
-        if (t == e - 1) {
+        if (tt == e - 1) {
             end = leaf_first[i + 1];
             skip = v + 1;
         } else {
             if (l == 0) {
-                end = n;
+                end = send;
             } else {
                 int sh = 63 - 3 * l;
                 uint64_t bound = ((kf >> sh) + 1ull) << sh;
-                end = lower_bound_u64(keys, first, n, bound);
+                end = lower_bound_u64(keys, first, send, bound);
             }
             skip = end >= n ? nn : nodeoff[leaf_of(leaf_first, nl, end)];
         }
         int32_t parent;
-        if (t > 0) {
+        if (tt > 0) {
             parent = (int32_t)(v - 1);
-        } else if (i == 0) {
-            parent = -1;
+        } else if (c < 0) {
+            parent = -1;  // the root of system sy
+            t.root[sy] = v;
         } else {
             // ancestor of leaf i at level c, opened by the leaf holding its
             // first particle
             uint32_t pf;
             if (c == 0) {
-                pf = 0;
+                pf = sbeg;
             } else {
                 int sh = 63 - 3 * c;
-                pf = lower_bound_u64(keys, 0, first, (kf >> sh) << sh);
+                pf = lower_bound_u64(keys, sbeg, first, (kf >> sh) << sh);
             }
             uint32_t j = leaf_of(leaf_first, nl, pf);
-            int cj = leaf_lcp(keys, leaf_first, j);
+            int cj = leaf_lcp(keys, leaf_first, t, j);
             parent = (int32_t)(nodeoff[j] + (uint32_t)(c - cj - 1));
         }
-        o.nrng[v] = make_int2((int)first, (int)end);
+        o.nrng[v] = make_int2((int)first + shift_pad, (int)end + shift_pad);
         o.nlevel[v] = (uint8_t)l;
         o.nparent[v] = parent;
         o.nhi[v] = make_float4(0.f, 0.f, 0.f, __int_as_float((int)skip));
@@ -406,14 +426,14 @@ __global__ void k_node_boxes(uint32_t nn, const float4 *__restrict__ pos, float 
 }
 
 cudaError_t octree_emit(const uint64_t *keys, uint32_t n, uint32_t n_leaves, uint32_t n_nodes,
-                        const uint32_t *leaf_first, const uint8_t *leaf_lev,
+                        const SysTables &t, const uint32_t *leaf_first, const uint8_t *leaf_lev,
                         const uint32_t *nodeoff, const float4 *pos, float support,
                         const OctreeOut &o, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(o.nchild, 0, (size_t)n_nodes * 4, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(o.narrive, 0, (size_t)n_nodes * 4, s);
     if (e != cudaSuccess) return e;
-    k_emit_nodes<<<(n_leaves + 127) / 128, 128, 0, s>>>(keys, n, n_leaves, n_nodes, leaf_first,
+    k_emit_nodes<<<(n_leaves + 127) / 128, 128, 0, s>>>(keys, n, n_leaves, n_nodes, t, leaf_first,
                                                         leaf_lev, nodeoff, o);
     k_node_boxes<<<(n_nodes + 127) / 128, 128, 0, s>>>(n_nodes, pos, support, o);
     return cudaGetLastError();

@@ -27,15 +27,15 @@ cudaError_t launch_pass(const PassArgs &a, int kind, int M, int any_periodic, in
 
 // Gather per-particle pass inputs into SFC order.
 // mode 0: aux = (a, 0); mode 1: aux = (a, b / (c*c)) (SPH: m, P / rho^2).
-__global__ void k_gather_aux(uint32_t n, uint32_t npad, const uint32_t *__restrict__ perm,
+__global__ void k_gather_aux(uint32_t npad, const uint32_t *__restrict__ perm_pad,
                              const float *__restrict__ a, const float *__restrict__ b,
                              const float *__restrict__ c, int mode, float2 *__restrict__ aux)
 {
     uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= npad) return;
     float2 v = make_float2(0.f, 0.f);
-    if (k < n) {
-        uint32_t o = perm[k];
+    const uint32_t o = perm_pad[k];
+    if (o != 0xffffffffu) {
         v.x = a[o];
         if (mode == 1) {
             float rho = c[o];
@@ -45,11 +45,11 @@ __global__ void k_gather_aux(uint32_t n, uint32_t npad, const uint32_t *__restri
     aux[k] = v;
 }
 
-cudaError_t launch_gather_aux(uint32_t n, uint32_t npad, const uint32_t *perm, const float *a,
+cudaError_t launch_gather_aux(uint32_t npad, const uint32_t *perm_pad, const float *a,
                               const float *b, const float *c, int mode, float2 *aux,
                               cudaStream_t s)
 {
-    k_gather_aux<<<(npad + 255) / 256, 256, 0, s>>>(n, npad, perm, a, b, c, mode, aux);
+    k_gather_aux<<<(npad + 255) / 256, 256, 0, s>>>(npad, perm_pad, a, b, c, mode, aux);
     return cudaGetLastError();
 }
 

@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(PS_THREADS) k_pass(PassArgs a)
         s = __shfl_sync(0xffffffffu, s, 0);
         if (s >= (a.work ? a.nwork : a.nsc)) break;
         if (a.work) s = a.work[s];
+        const DevBox &box = a.sys.box[sys_of(a.sys.pad_off, a.sys.nsys, s * kSC * M)];
 
         float4 pi[kSC];
         float ri2[kSC], hinv[kSC], ci[kSC], ri[kSC];
@@ -206,10 +207,10 @@ __global__ void __launch_bounds__(PS_THREADS) k_pass(PassArgs a)
                         const uint32_t ii = (s * kSC + k) * M + II;
                         // canonical distance decides the pair; the sums use the
                         // accurate vector (identical unless wrapped)
-                        const float d2 = pair_d2<PER>(pi[k], pj, a.box);
+                        const float d2 = pair_d2<PER>(pi[k], pj, box);
                         if constexpr (KIND == PASS_DENSITY) {
                             if (owner && ii != jj && d2 < ri2[k]) {
-                                const float3 dv = pair_dx_acc<PER>(pi[k], pj, a.box);
+                                const float3 dv = pair_dx_acc<PER>(pi[k], pj, box);
                                 float q = sqrtf(d2_of(dv)) * hinv[k];
                                 acc.b[k] += aj.x * spline_w(q);
                             }
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(PS_THREADS) k_pass(PassArgs a)
                             const float rr = fmaxf(ri[k], rj);
                             if (owner && ii != jj && d2 < __fmul_rn(rr, rr)) {
                                 // a_i -= m_j (c_i gW_i + c_j gW_j) (x_i - x_j) / r
-                                const float3 dv = pair_dx_acc<PER>(pi[k], pj, a.box);
+                                const float3 dv = pair_dx_acc<PER>(pi[k], pj, box);
                                 float r = sqrtf(d2_of(dv));
                                 float hj = pj.w, hji = 1.f / hj;
                                 float gi = spline_dw(r * hinv[k]) * hinv[k] * hinv[k] * hinv[k] * hinv[k];
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(PS_THREADS) k_pass(PassArgs a)
                             }
                         } else {  // LJ: F_i += 24 eps (2 s^12/r^14 - s^6/r^8)(x_i - x_j)
                             if (owner && ii != jj && d2 < ri2[k]) {
-                                const float3 dv = pair_dx_acc<PER>(pi[k], pj, a.box);
+                                const float3 dv = pair_dx_acc<PER>(pi[k], pj, box);
                                 float ir2 = 1.f / d2_of(dv);
                                 float s2 = a.p1 * a.p1 * ir2;
                                 float s6 = s2 * s2 * s2;
@@ -273,8 +274,9 @@ __global__ void __launch_bounds__(PS_THREADS) k_pass(PassArgs a)
         for (int k = 0; k < kSC; ++k) {
             if ((uint32_t)k % G != g) continue;
             const uint32_t i = (s * kSC + k) * M + II;
-            if (i >= a.n) continue;
-            const uint32_t o = a.sorted_out ? i : a.perm[i];
+            const uint32_t pc = a.perm[i];
+            if (pc == 0xffffffffu) continue;  // dummy slot
+            const uint32_t o = a.sorted_out ? i : pc;
             if constexpr (KIND == PASS_DENSITY) {
                 float self = a.aux[i].x;  // m_i w(0) = m_i
                 a.out0[o] = (acc.v[k] + self) * (0.318309886183790672f * hinv[k] * hinv[k] * hinv[k]);

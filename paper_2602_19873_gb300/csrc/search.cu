@@ -154,6 +154,11 @@ __global__ void __launch_bounds__(SR_THREADS, 3) k_search(SearchArgs a, SearchCt
         if (tk >= ctl.count) break;
         const uint32_t s = ctl.work ? ctl.work[tk] : tk;
         const uint32_t base = s * kSC * M;
+        // the super-cluster's system: its box and its own octree subtree
+        const uint32_t sy = sys_of(a.sys.pad_off, a.sys.nsys, base);
+        const DevBox &box = a.sys.box[sy];
+        const uint32_t vroot = a.sys.root[sy];
+        const uint32_t vend = (uint32_t)__float_as_int(a.nhi[vroot].w);
 
         // i-cluster box of this lane's cluster (lane & 7)
         const float4 ilo = a.clo[s * kSC + (lane & 7)];
@@ -177,15 +182,15 @@ __global__ void __launch_bounds__(SR_THREADS, 3) k_search(SearchArgs a, SearchCt
 
         uint32_t cnt = 0, tiles = 0, nvis = 0, lvis = 0, jex = 0, ttests = 0;
         int lastJ = -1;
-        uint32_t v = 0;
-        while (v < a.nnodes) {
+        uint32_t v = vroot;
+        while (v < vend) {
             ++nvis;
             const float4 nlo = a.nlo[v];
             const float4 nhi = a.nhi[v];
             const uint32_t skip = (uint32_t)__float_as_int(nhi.w);
             bool near = false;
 #pragma unroll
-            for (int t = 0; t < NPI; ++t) near |= point_near<PER>(qp[t], qr[t], nlo, nhi, a.box);
+            for (int t = 0; t < NPI; ++t) near |= point_near<PER>(qp[t], qr[t], nlo, nhi, box);
             if (!__any_sync(0xffffffffu, near)) {
                 v = skip > v ? skip : v + 1;  // always advances
                 continue;
@@ -206,9 +211,9 @@ __global__ void __launch_bounds__(SR_THREADS, 3) k_search(SearchArgs a, SearchCt
                 bool cand = false, sure = false;
                 if (Jl <= Jhi) {
                     const float4 jlo = a.clo[Jl], jhi = a.chi[Jl];
-                    cand = boxes_near<PER>(ilo, ihi, jlo, jhi, a.box);
+                    cand = boxes_near<PER>(ilo, ihi, jlo, jhi, box);
                     sure = cand && (uint32_t)Jl != s * kSC + (lane & 7) &&
-                           boxes_all_near<PER>(ilo, ihi, jlo, jhi, a.box);
+                           boxes_all_near<PER>(ilo, ihi, jlo, jhi, box);
                 }
                 const uint32_t bal = __ballot_sync(0xffffffffu, cand);
                 const uint32_t sbal = __ballot_sync(0xffffffffu, sure);
@@ -233,7 +238,7 @@ __global__ void __launch_bounds__(SR_THREADS, 3) k_search(SearchArgs a, SearchCt
 #pragma unroll
                         for (int t = 0; t < NPI; ++t) {
                             const uint32_t b = __ballot_sync(
-                                0xffffffffu, point_near<PER>(qp[t], qr[t], jlo, jhi, a.box));
+                                0xffffffffu, point_near<PER>(qp[t], qr[t], jlo, jhi, box));
 #pragma unroll
                             for (int c = 0; c < CPB; ++c)
                                 if ((b >> (c * M)) & ((M == 32) ? 0xffffffffu : ((1u << M) - 1u)))
@@ -253,7 +258,7 @@ __global__ void __launch_bounds__(SR_THREADS, 3) k_search(SearchArgs a, SearchCt
                         for (int k = 0; k < kSC; ++k) {
                             if (!((cm >> k) & 1u) || ((mask >> k) & 1u)) continue;
                             const uint32_t ii = base + k * M + II;
-                            const float d2 = pair_d2<PER>(pi[k], pj, a.box);
+                            const float d2 = pair_d2<PER>(pi[k], pj, box);
                             const float r = fmaxf(ri[k], rj);
                             const bool hit = (ii != jj) && d2 < __fmul_rn(r, r);
                             if (__any_sync(0xffffffffu, hit)) mask |= 1u << k;

@@ -76,6 +76,52 @@ cudaError_t launch_keys(int64_t n, const float *x, const float *y, const float *
     return cudaGetLastError();
 }
 
+template <int KIND>
+__global__ void __launch_bounds__(256) k_keys_batch(int64_t n, const float *__restrict__ x,
+                                                    const float *__restrict__ y,
+                                                    const float *__restrict__ z,
+                                                    const float *__restrict__ h, SysTables t,
+                                                    float support, uint64_t *__restrict__ keys,
+                                                    uint32_t *__restrict__ vals, Status *st)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned bad = 0;
+    if (i < n) {
+        const DevBox &b = t.box[sys_of(t.off, t.nsys, (uint32_t)i)];
+        float px = x[i], py = y[i], pz = z[i], ph = h[i];
+        if (!isfinite(px) || !isfinite(py) || !isfinite(pz)) bad |= 1u;
+        if (!(px >= b.lo[0] && px <= b.hi[0] && py >= b.lo[1] && py <= b.hi[1] &&
+              pz >= b.lo[2] && pz <= b.hi[2]))
+            bad |= 2u;
+        if (!(ph > 0.f) || !isfinite(ph)) bad |= 4u;
+        // a search radius reaching half a periodic box length is reported
+        float r = __fmul_rn(support, ph);
+        for (int a = 0; a < 3; ++a)
+            if (b.per[a] && !(r < b.half[a])) bad |= 8u;
+        uint32_t qx = quantize21(px, b.lo[0], b.qs[0]);
+        uint32_t qy = quantize21(py, b.lo[1], b.qs[1]);
+        uint32_t qz = quantize21(pz, b.lo[2], b.qs[2]);
+        keys[i] = KIND == NL_KEY_MORTON ? morton_key(qx, qy, qz) : hilbert_key(qx, qy, qz);
+        vals[i] = (uint32_t)i;
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    if (lane_id() == 0 && bad) atomicOr(&st->bad_input, bad);
+}
+
+cudaError_t launch_keys_batch(int64_t n, const float *x, const float *y, const float *z,
+                              const float *h, const SysTables &t, float support, int kind,
+                              uint64_t *keys, uint32_t *vals, Status *st, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    unsigned grid = (unsigned)((n + 255) / 256);
+    if (kind == NL_KEY_MORTON)
+        k_keys_batch<NL_KEY_MORTON><<<grid, 256, 0, s>>>(n, x, y, z, h, t, support, keys, vals, st);
+    else
+        k_keys_batch<NL_KEY_HILBERT><<<grid, 256, 0, s>>>(n, x, y, z, h, t, support, keys, vals, st);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Radix sort
 // ---------------------------------------------------------------------------
@@ -89,7 +135,41 @@ static uint32_t rs_tiles(uint32_t n) { return (n + RS_TILE - 1) / RS_TILE; }
 
 size_t radix_hist_words(uint32_t n) { return (size_t)256 * rs_tiles(n) + 256; }
 
+// Digit of an element: 8 key bits, or 8 bits of the system owning the value
+// (a caller index) for the final by-system passes.
+struct DigitSrc {
+    const uint32_t *sys_off;  // NULL: key digits
+    uint32_t nsys;
+    __device__ __forceinline__ uint32_t operator()(uint64_t key, uint32_t val, int shift) const
+    {
+        if (!sys_off) return (unsigned)(key >> shift) & 0xffu;
+        return (sys_of(sys_off, nsys, val) >> shift) & 0xffu;
+    }
+};
+
 // Per-tile digit counts, digit-major: hist[d * ntiles + tile].
+__global__ void __launch_bounds__(RS_THREADS) k_rs_upsweep_sys(const uint32_t *__restrict__ vals,
+                                                               uint32_t n, int shift, DigitSrc dg,
+                                                               uint32_t *__restrict__ hist,
+                                                               uint32_t ntiles)
+{
+    __shared__ uint32_t cnt[RS_WARPS][256];
+    for (int t = threadIdx.x; t < RS_WARPS * 256; t += RS_THREADS) (&cnt[0][0])[t] = 0;
+    __syncthreads();
+    const uint32_t base = blockIdx.x * RS_TILE;
+    const int warp = threadIdx.x >> 5;
+    for (int it = 0; it < RS_ITEMS; ++it) {
+        uint32_t k = base + it * RS_THREADS + threadIdx.x;
+        if (k < n) atomicAdd(&cnt[warp][dg(0ull, vals[k], shift)], 1u);
+    }
+    __syncthreads();
+    const int d = threadIdx.x;
+    uint32_t sum = 0;
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w) sum += cnt[w][d];
+    hist[(size_t)d * ntiles + blockIdx.x] = sum;
+}
+
 __global__ void __launch_bounds__(RS_THREADS) k_rs_upsweep(const uint64_t *__restrict__ keys,
                                                            uint32_t n, int shift,
                                                            uint32_t *__restrict__ hist,
@@ -135,7 +215,7 @@ __global__ void __launch_bounds__(1024) k_rs_scan(uint32_t *__restrict__ hist, u
 __global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     uint32_t *__restrict__ vout, uint32_t n, int shift, const uint32_t *__restrict__ hist,
-    const uint32_t *__restrict__ tot, uint32_t ntiles)
+    const uint32_t *__restrict__ tot, uint32_t ntiles, DigitSrc dg)
 {
     extern __shared__ __align__(16) unsigned char rs_smem[];
     uint64_t *skeys = reinterpret_cast<uint64_t *>(rs_smem);
@@ -160,7 +240,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(
         bool valid = k < n;
         key[it] = valid ? kin[k] : 0ull;
         val[it] = valid ? vin[k] : 0u;
-        uint32_t d = valid ? ((unsigned)(key[it] >> shift) & 0xffu) : 256u;
+        uint32_t d = valid ? dg(key[it], val[it], shift) : 256u;
         uint32_t peers = __match_any_sync(0xffffffffu, d);
         uint32_t before = d < 256u ? wcnt[warp][d] : 0u;
         rank[it] = before + __popc(peers & lt);
@@ -191,7 +271,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(
     for (int it = 0; it < RS_ITEMS; ++it) {
         uint32_t k = base + warp * RS_WARP_SPAN + it * 32 + lane;
         if (k < n) {
-            uint32_t d = (unsigned)(key[it] >> shift) & 0xffu;
+            uint32_t d = dg(key[it], val[it], shift);
             uint32_t lp = tstart[d] + wcnt[warp][d] + rank[it];
             skeys[lp] = key[it];
             svals[lp] = val[it];
@@ -200,10 +280,11 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(
     __syncthreads();
     for (uint32_t t = threadIdx.x; t < tile_n; t += RS_THREADS) {
         uint64_t kk = skeys[t];
-        uint32_t d = (unsigned)(kk >> shift) & 0xffu;
+        uint32_t vv = svals[t];
+        uint32_t d = dg(kk, vv, shift);
         uint32_t g = gbase[d] + t;
         kout[g] = kk;
-        vout[g] = svals[t];
+        vout[g] = vv;
     }
 }
 
@@ -234,7 +315,7 @@ cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
         k_rs_upsweep<<<ntiles, RS_THREADS, 0, s>>>(ka, n, shift, hist, ntiles);
         k_rs_scan<<<256, 1024, 0, s>>>(hist, ntiles, tot);
         k_rs_downsweep<<<ntiles, RS_THREADS, rs_down_smem(), s>>>(ka, va, kb, vb, n, shift, hist,
-                                                                 tot, ntiles);
+                                                                 tot, ntiles, DigitSrc{nullptr, 0});
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
     }
@@ -245,6 +326,34 @@ cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
         e = cudaMemcpyAsync(keys, ka, (size_t)n * 8, cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(vals, va, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
+    }
+    return e;
+}
+
+cudaError_t radix_sort_by_system(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
+                                 uint32_t *vals_alt, uint32_t n, const uint32_t *sys_off,
+                                 uint32_t nsys, uint32_t *hist, cudaStream_t s)
+{
+    if (n <= 1 || nsys <= 1) return cudaSuccess;
+    const uint32_t ntiles = rs_tiles(n);
+    uint32_t *tot = hist + (size_t)256 * ntiles;
+    const DigitSrc dg{sys_off, nsys};
+    const int passes = nsys <= 256 ? 1 : (nsys <= 65536 ? 2 : 3);
+    uint64_t *ka = keys, *kb = keys_alt;
+    uint32_t *va = vals, *vb = vals_alt;
+    for (int p = 0; p < passes; ++p) {
+        int shift = 8 * p;
+        k_rs_upsweep_sys<<<ntiles, RS_THREADS, 0, s>>>(va, n, shift, dg, hist, ntiles);
+        k_rs_scan<<<256, 1024, 0, s>>>(hist, ntiles, tot);
+        k_rs_downsweep<<<ntiles, RS_THREADS, rs_down_smem(), s>>>(ka, va, kb, vb, n, shift, hist,
+                                                                 tot, ntiles, dg);
+        uint64_t *tk = ka; ka = kb; kb = tk;
+        uint32_t *tv = va; va = vb; vb = tv;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && ka != keys) {
+        e = cudaMemcpyAsync(keys, ka, (size_t)n * 8, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(vals, va, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
     }
     return e;
 }

@@ -67,6 +67,10 @@ _SIGS = {
     "nl_density_from_host": (C.c_int, [P, P, P, P, P, P, C.c_int64, P, P, P, P]),
     "nl_sfc_order_noalloc": (C.c_int, [P, P, P, P, C.c_int64, P, C.c_int32, C.c_float, P, P,
                                         P]),
+    "nl_build_batch": (C.c_int, [P, P, P, P, C.c_int32, P, P, P, P, P]),
+    "nl_rebuild_batch": (C.c_int, [P, P, P, P, P, C.c_int32, P, P, P, P]),
+    "nl_iterate_h_batch": (C.c_int, [P, P, P, P, P, C.c_int32, P, P, P, C.c_float, C.c_float,
+                                     C.c_int32, C.c_float, C.c_int32, P, P, P]),
     "nl_iterate_h": (C.c_int, [P, P, P, P, P, C.c_int64, P, P, C.c_float, C.c_float, C.c_int32,
                                C.c_float, C.c_int32, P, P, P]),
 }
@@ -178,6 +182,41 @@ class NeighborList:
             _check(L.nl_rebuild(self.handle, _ptr(x), _ptr(y), _ptr(z), _ptr(h), n, C.byref(b),
                                 C.byref(params), _stream(stream)))
         return self
+
+    def build_batch(self, x, y, z, h, offsets, boxes, params, stream=None):
+        """Batch of systems back to back in x..h; offsets: nsys+1 ints;
+        boxes: list of box dicts."""
+        L = load()
+        nsys = len(boxes)
+        offs = np.ascontiguousarray(offsets, dtype=np.int64)
+        assert len(offs) == nsys + 1
+        barr = (nl_box * nsys)(*[make_box(b) for b in boxes])
+        if self.handle is None:
+            out = C.c_void_p()
+            _check(L.nl_build_batch(_ptr(x), _ptr(y), _ptr(z), _ptr(h), nsys, offs.ctypes.data,
+                                    barr, C.byref(params), _stream(stream), C.byref(out)))
+            self.handle = out
+        else:
+            _check(L.nl_rebuild_batch(self.handle, _ptr(x), _ptr(y), _ptr(z), _ptr(h), nsys,
+                                      offs.ctypes.data, barr, C.byref(params), _stream(stream)))
+        return self
+
+    def iterate_h_batch(self, x, y, z, h, offsets, boxes, params, n_target, tol=2.0, max_iter=40,
+                        margin=0.15, start=1, converged=None, stream=None, check=True):
+        self.ensure_handle()
+        nsys = len(boxes)
+        offs = np.ascontiguousarray(offsets, dtype=np.int64)
+        barr = (nl_box * nsys)(*[make_box(b) for b in boxes])
+        info = nl_hiter_info()
+        st = load().nl_iterate_h_batch(self.handle, _ptr(x), _ptr(y), _ptr(z), _ptr(h), nsys,
+                                       offs.ctypes.data, barr, C.byref(params), float(n_target),
+                                       float(tol), int(max_iter), float(margin), int(start),
+                                       _ptr(converged), C.byref(info), _stream(stream))
+        out = {"iterations": info.iterations, "rebuilds": info.rebuilds,
+               "unconverged": info.unconverged, "status": st}
+        if st != NL_OK and (check or st != 6):
+            _check(st)
+        return out
 
     def ensure_handle(self):
         if self.handle is None:
