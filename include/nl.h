@@ -71,9 +71,11 @@ typedef struct {
     float support;        /* interaction radius r_i = support * h_i (2 for the cubic spline) */
     int32_t compress;     /* 1: nibble codec (Sec. II-B); 0: raw u32 cluster indices */
     int32_t leaf_bucket;  /* octree leaf capacity B in particles, 8..1024 (default 64) */
+    int32_t threads_per_block; /* search / pass block shape: 128 or 256 threads (0 = 256) */
+    int32_t blocks_per_sm;     /* persistent grids: blocks per SM, 1..8 (0 = 3 search, 4 pass) */
 } nl_params;
 
-/* Fills p with {NL_KEY_HILBERT, 8, 2.0f, 1, 64}. */
+/* Fills p with {NL_KEY_HILBERT, 8, 2.0f, 1, 64, 0, 0}. */
 void nl_default_params(nl_params *p);
 
 typedef struct nl_list nl_list; /* opaque; owns all of its device memory */
@@ -258,6 +260,39 @@ nl_status nl_iterate_h_batch(nl_list *nl, const float *x, const float *y, const 
                              const nl_params *p, float n_target, float tol, int32_t max_iter,
                              float margin, int32_t start, uint8_t *converged, nl_hiter_info *info,
                              void *stream);
+
+/* One step of a batch (build + density pass) as a CUDA graph.  The list is
+ * first built normally (buffers sized with slack, inputs validated), then
+ * the sync-free form of the same step -- keys, radix sort, permutation,
+ * octree with device-side counts, one persistent search launch, input
+ * gather and one persistent density launch -- is captured on `stream` and
+ * instantiated.  nl_graph_launch replays it; the device arrays x, y, z, h,
+ * m, rho must stay allocated at the same addresses (their contents may
+ * change between launches).  A replay never allocates or synchronises, so
+ * capacity overflows (more octree nodes or longer lists than the slack
+ * allows) and invalid inputs are only recorded on the device:
+ * nl_graph_check synchronises `stream` and returns NL_ERR_CAPACITY,
+ * NL_ERR_ARG or NL_ERR_RADIUS for the last replay (then rebuild without the
+ * graph and create a new one), else NL_OK and refreshes nl_get_sizes. */
+typedef struct nl_graph nl_graph;
+nl_status nl_graph_create(nl_list *nl, const float *x, const float *y, const float *z,
+                          const float *h, const float *m, float *rho, int32_t nsys,
+                          const int64_t *offsets, const nl_box *boxes, const nl_params *p,
+                          void *stream, nl_graph **out);
+nl_status nl_graph_launch(nl_graph *g, void *stream);
+nl_status nl_graph_check(nl_graph *g, void *stream);
+nl_status nl_graph_free(nl_graph *g);
+
+/* Autotuner: times build + density of the given batch for every candidate
+ * cluster size M in {4, 8, 16}, block shape in {128, 256} threads and
+ * persistent-grid occupancy in {2, 3, 4} blocks per SM (reps timed runs
+ * each after one warm-up, CUDA events on `stream`) and writes the fastest
+ * parameters (other fields copied from *base) to *best and its mean time
+ * to *best_ms.  Synchronises `stream`. */
+nl_status nl_autotune_batch(const float *x, const float *y, const float *z, const float *h,
+                            const float *m, int32_t nsys, const int64_t *offsets,
+                            const nl_box *boxes, const nl_params *base, int32_t reps,
+                            nl_params *best, float *best_ms, void *stream);
 
 /* Thread-local description of the last error (never NULL). */
 const char *nl_last_error(void);

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstddef>
 #include <cstdlib>
 #include <cstring>
 #include <string>
@@ -105,6 +106,8 @@ struct nl_list {
     DevBuf stageJ, stageM, list, rec_off, redo, work, aux, status;
     DevBuf perm_pad, sys_off, sys_pad, sys_box, sys_root, sys_hcap;
     int32_t nsys = 1;
+    uint32_t node_cap = 0;
+    int graph_mode = 0;   // build without host reads or allocations (stream capture)
     Status *hst = nullptr;
 
     SysTables tables() const
@@ -175,6 +178,10 @@ nl_status check_params(const nl_params *p, const nl_box *box)
     if (p->compress != 0 && p->compress != 1) return fail(NL_ERR_ARG, "compress must be 0 or 1");
     if (p->leaf_bucket < 8 || p->leaf_bucket > 1024)
         return fail(NL_ERR_ARG, "leaf_bucket must be in [8, 1024] (got %d)", p->leaf_bucket);
+    if (p->threads_per_block != 0 && p->threads_per_block != 128 && p->threads_per_block != 256)
+        return fail(NL_ERR_ARG, "threads_per_block must be 0, 128 or 256");
+    if (p->blocks_per_sm < 0 || p->blocks_per_sm > 8)
+        return fail(NL_ERR_ARG, "blocks_per_sm must be in [0, 8]");
     for (int a = 0; a < 3; ++a) {
         if (!std::isfinite(box->lo[a]) || !std::isfinite(box->hi[a]) || !(box->lo[a] < box->hi[a]))
             return fail(NL_ERR_ARG, "box axis %d: need finite lo < hi", a);
@@ -267,6 +274,7 @@ nl_status do_prep(nl_list *nl, const float *x, const float *y, const float *z, c
     nl->dbox = dbox[0];
     nl->nsys = nsys;
 
+    if (!nl->graph_mode) {
     CK(nl->keys.ensure((size_t)N * 8));
     CK(nl->keys_alt.ensure((size_t)N * 8));
     CK(nl->vals.ensure((size_t)N * 4));
@@ -296,6 +304,7 @@ nl_status do_prep(nl_list *nl, const float *x, const float *y, const float *z, c
     CK(cudaMemcpyAsync(nl->sys_box.p, dbox.data(), (size_t)nsys * sizeof(DevBox),
                        cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(nl->sys_hcap.p, hcap.data(), (size_t)nsys * 4, cudaMemcpyHostToDevice, s));
+    }
     const SysTables T = nl->tables();
     Status *dst = nl->status.as<Status>();
     CK(cudaMemsetAsync(dst, 0, sizeof(Status), s));
@@ -320,32 +329,39 @@ nl_status do_prep(nl_list *nl, const float *x, const float *y, const float *z, c
     CK(octree_leaves(nl->keys.as<uint64_t>(), N, p->leaf_bucket, T, nl->lcp.as<uint8_t>(),
                      nl->lev.as<uint8_t>(), nl->leaf_first.as<uint32_t>(),
                      nl->leaf_lev.as<uint8_t>(), nl->bsum.as<uint32_t>(), dst, s));
-    nl_status st = read_status(nl, s);
-    if (st != NL_OK) return st;
-    if (nl->hst->bad_input & 7u) {
-        unsigned b = nl->hst->bad_input;
-        return fail(NL_ERR_ARG, "invalid particle input:%s%s%s", (b & 1) ? " non-finite coordinate" : "",
-                    (b & 2) ? " coordinate outside the box" : "", (b & 4) ? " h <= 0 or non-finite" : "");
-    }
-    if (nl->hst->bad_input & 8u)
-        return fail(NL_ERR_RADIUS, "support*h >= L/2 on a periodic axis for some particle");
-    const uint32_t nleaves = nl->hst->n_leaves;
-    CK(octree_count_nodes(nl->keys.as<uint64_t>(), nleaves, T, nl->leaf_first.as<uint32_t>(),
+    CK(octree_count_nodes(nl->keys.as<uint64_t>(), N, T, nl->leaf_first.as<uint32_t>(),
                           nl->leaf_lev.as<uint8_t>(), nl->nodeoff.as<uint32_t>(),
                           nl->bsum.as<uint32_t>(), dst, s));
-    st = read_status(nl, s);
-    if (st != NL_OK) return st;
-    const uint32_t nnodes = nl->hst->n_nodes;
-    CK(nl->nlo.ensure((size_t)nnodes * 16));
-    CK(nl->nhi.ensure((size_t)nnodes * 16));
-    CK(nl->nrng.ensure((size_t)nnodes * 8));
-    CK(nl->nlevel.ensure((size_t)nnodes));
-    CK(nl->nparent.ensure((size_t)nnodes * 4));
-    CK(nl->nchild.ensure((size_t)nnodes * 4));
-    CK(nl->narrive.ensure((size_t)nnodes * 4));
-    CK(octree_emit(nl->keys.as<uint64_t>(), N, nleaves, nnodes, T, nl->leaf_first.as<uint32_t>(),
+    uint32_t nleaves = 0, nnodes = 0;
+    if (!nl->graph_mode) {
+        nl_status st = read_status(nl, s);  // validation and sizes, one read
+        if (st != NL_OK) return st;
+        if (nl->hst->bad_input & 7u) {
+            unsigned b = nl->hst->bad_input;
+            return fail(NL_ERR_ARG, "invalid particle input:%s%s%s",
+                        (b & 1) ? " non-finite coordinate" : "",
+                        (b & 2) ? " coordinate outside the box" : "",
+                        (b & 4) ? " h <= 0 or non-finite" : "");
+        }
+        if (nl->hst->bad_input & 8u)
+            return fail(NL_ERR_RADIUS, "support*h >= L/2 on a periodic axis for some particle");
+        nleaves = nl->hst->n_leaves;
+        nnodes = nl->hst->n_nodes;
+        const size_t cap = (size_t)nnodes + nnodes / 8 + 64;  // slack for graph replays
+        if (nl->node_cap < nnodes) {
+            CK(nl->nlo.ensure(cap * 16));
+            CK(nl->nhi.ensure(cap * 16));
+            CK(nl->nrng.ensure(cap * 8));
+            CK(nl->nlevel.ensure(cap));
+            CK(nl->nparent.ensure(cap * 4));
+            CK(nl->nchild.ensure(cap * 4));
+            CK(nl->narrive.ensure(cap * 4));
+            nl->node_cap = (uint32_t)cap;
+        }
+    }
+    CK(octree_emit(nl->keys.as<uint64_t>(), N, nl->node_cap, T, nl->leaf_first.as<uint32_t>(),
                    nl->leaf_lev.as<uint8_t>(), nl->nodeoff.as<uint32_t>(), nl->pos.as<float4>(),
-                   p->support, nl->octree_out(), s));
+                   p->support, nl->octree_out(), dst, s));
     nl->npad = npad;
     nl->ncl = ncl;
     nl->nsc = nsc;
@@ -361,20 +377,25 @@ nl_status do_search(nl_list *nl, cudaStream_t s)
 {
     nl_status st;
     const nl_params *p = &nl->p;
-    const uint32_t N = (uint32_t)nl->n_prepared, nsc = nl->nsc, nnodes = nl->n_nodes;
+    const uint32_t N = (uint32_t)nl->n_prepared, nsc = nl->nsc;
     const int M = p->cluster;
     Status *dst = nl->status.as<Status>();
-    CK(cudaMemsetAsync(dst, 0, sizeof(Status), s));
+    const size_t search_words = sizeof(Status) - offsetof(Status, ticket);
+    CK(cudaMemsetAsync(&dst->ticket, 0, search_words, s));
     size_t est = (size_t)N * (p->compress ? 12 : 48) + 65536;
     // test knobs: start from tiny buffers to exercise the overflow rounds
     if (const char *e = std::getenv("NLGB_LIST_CAP0")) est = std::strtoull(e, nullptr, 10) + 8;
     if (const char *e = std::getenv("NLGB_STAGE_CAP0"))
         if (!nl->stage_grown) nl->stage_cap = (uint32_t)std::strtoul(e, nullptr, 10);
-    if (nl->list.cap < est) CK(nl->list.ensure(est));
-    int grid = nl->num_sms * kSearchBlocksPerSM;
-    size_t slots = (size_t)grid * 8;
-    CK(nl->stageJ.ensure(slots * nl->stage_cap * 4));
-    CK(nl->stageM.ensure(slots * nl->stage_cap));
+    const int tpb = p->threads_per_block ? p->threads_per_block : 256;
+    const int wpb = tpb / 32;
+    int grid = nl->num_sms * (p->blocks_per_sm ? p->blocks_per_sm : kSearchBlocksPerSM);
+    size_t slots = (size_t)grid * wpb;
+    if (!nl->graph_mode) {
+        if (nl->list.cap < est) CK(nl->list.ensure(est));
+        CK(nl->stageJ.ensure(slots * nl->stage_cap * 4));
+        CK(nl->stageM.ensure(slots * nl->stage_cap));
+    }
     CK(cudaMemsetAsync(&dst->fail_off, 0xff, sizeof(dst->fail_off), s));
     CK(nl->mark(4, s));
 
@@ -387,7 +408,7 @@ nl_status do_search(nl_list *nl, cudaStream_t s)
     sa.nrng = nl->nrng.as<int2>();
     sa.n = N;
     sa.nsc = nsc;
-    sa.nnodes = nnodes;
+    sa.nnodes = nl->node_cap;  // node array capacity (bounds every node index)
     sa.sys = nl->tables();
     sa.support = p->support;
     sa.compress = p->compress;
@@ -403,7 +424,8 @@ nl_status do_search(nl_list *nl, cudaStream_t s)
         sa.stage_cap = nl->stage_cap;
         sa.list = nl->list.as<uint8_t>();
         sa.list_cap = nl->list.cap - 8;  // 8 bytes of slack behind the last record
-        CK(launch_search_ctl(sa, work, count, nl->redo.as<uint32_t>(), M, nl->any_per, grid, s));
+        CK(launch_search_ctl(sa, work, count, nl->redo.as<uint32_t>(), M, nl->any_per, grid, tpb, s));
+        if (nl->graph_mode) return NL_OK;  // overflow is reported by nl_graph_check
         st = read_status(nl, s);
         if (st != NL_OK) return st;
         entries += nl->hst->n_entries;
@@ -421,8 +443,8 @@ nl_status do_search(nl_list *nl, cudaStream_t s)
         CK(cudaMemcpyAsync(nl->work.p, nl->redo.p, (size_t)nredo * 4, cudaMemcpyDeviceToDevice, s));
         work = nl->work.as<uint32_t>();
         count = nredo;
-        grid = (int)std::min<uint32_t>((uint32_t)(nl->num_sms * kSearchBlocksPerSM), (nredo + 7) / 8);
-        slots = (size_t)grid * 8;
+        grid = (int)std::min<uint32_t>((uint32_t)grid, (nredo + wpb - 1) / wpb);
+        slots = (size_t)grid * wpb;
         if (nl->hst->max_count > nl->stage_cap) {
             nl->stage_cap = nl->hst->max_count + nl->hst->max_count / 4 + 64;
             nl->stage_grown = 1;
@@ -441,10 +463,10 @@ nl_status do_search(nl_list *nl, cudaStream_t s)
             nl->list = bigger;
             bigger.p = nullptr;
         }
-        std::memset(nl->hst, 0, sizeof(Status));
+        std::memset(&nl->hst->ticket, 0, search_words);
         nl->hst->list_used = keep;
         nl->hst->fail_off = ~0ull;
-        CK(cudaMemcpyAsync(dst, nl->hst, sizeof(Status), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(&dst->ticket, &nl->hst->ticket, search_words, cudaMemcpyHostToDevice, s));
     }
     CK(nl->mark(5, s));
     nl->collect(0, 5);
@@ -504,6 +526,8 @@ void nl_default_params(nl_params *p)
     p->support = 2.0f;
     p->compress = 1;
     p->leaf_bucket = 64;
+    p->threads_per_block = 0;
+    p->blocks_per_sm = 0;
 }
 
 const char *nl_last_error(void) { return g_err.c_str(); }
@@ -682,7 +706,8 @@ static nl_status do_iterate_h(nl_list *nl, const float *x, const float *y, const
             CK(launch_pos_h(npad, hs.hs, nl->pos.as<float4>(), s));
             CK(launch_cluster_boxes(npad, M, nl->pos.as<float4>(), p->support,
                                     nl->clo.as<float4>(), nl->chi.as<float4>(), s));
-            CK(octree_boxes(nl->n_nodes, nl->pos.as<float4>(), p->support, oo, s));
+            CK(octree_boxes(nl->node_cap, nl->pos.as<float4>(), p->support, oo,
+                            nl->status.as<Status>(), s));
             st = do_search(nl, s);
             if (st != NL_OK) return st;
             ++rebuilds;
@@ -695,7 +720,8 @@ static nl_status do_iterate_h(nl_list *nl, const float *x, const float *y, const
             a.work = hs.active_list;
             a.nwork = words[2];
         }
-        CK(launch_pass(a, PASS_COUNT, M, nl->any_per, nl->num_sms, s));
+        CK(launch_pass(a, PASS_COUNT, M, nl->any_per, nl->num_sms, s, p->threads_per_block,
+                       p->blocks_per_sm));
         ++iters;
         first = false;
         CK(cudaMemsetAsync(hs.words, 0, 16, s));
@@ -741,6 +767,174 @@ nl_status nl_iterate_h_batch(nl_list *nl, const float *x, const float *y, const 
                         max_iter, margin, start, converged, info, (cudaStream_t)stream);
 }
 
+}  // extern "C"
+
+struct nl_graph {
+    nl_list *nl = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+nl_status nl_graph_create(nl_list *nl, const float *x, const float *y, const float *z,
+                          const float *h, const float *m, float *rho, int32_t nsys,
+                          const int64_t *offsets, const nl_box *boxes, const nl_params *p,
+                          void *stream, nl_graph **out)
+{
+    if (!out) return fail(NL_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!nl || !m || !rho) return fail(NL_ERR_ARG, "NULL list, m or rho");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!s) return fail(NL_ERR_ARG, "graph capture needs a non-default stream");
+    // 1. a normal build and pass size every buffer and validate the inputs
+    nl_status st = nl_rebuild_batch(nl, x, y, z, h, nsys, offsets, boxes, p, stream);
+    if (st != NL_OK) return st;
+    st = nl_density_pass(nl, m, rho, stream);
+    if (st != NL_OK) return st;
+    // slack for the replays: list bytes; the node arrays already carry 1/8
+    const size_t want = (size_t)nl->list_bytes + nl->list_bytes / 4 + 65536;
+    if (nl->list.cap < want) {
+        DevBuf bigger;
+        CK(bigger.ensure(want));
+        nl->list.release();
+        nl->list = bigger;
+    }
+    CK(cudaStreamSynchronize(s));
+    const int64_t n = offsets[nsys];
+    const int prof = nl->profiling;
+    nl->profiling = 0;
+    // 2. capture the sync-free step
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    nl->graph_mode = 1;
+    st = do_prep(nl, x, y, z, h, n, nsys, offsets, boxes, p, s);
+    if (st == NL_OK) st = do_search(nl, s);
+    if (st == NL_OK) st = nl_density_pass(nl, m, rho, stream);
+    nl->graph_mode = 0;
+    nl->profiling = prof;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (st != NL_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __LINE__);
+    cudaGraphExec_t ge = nullptr;
+    e = cudaGraphInstantiate(&ge, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(e, "cudaGraphInstantiate", __LINE__);
+    }
+    nl_graph *G = new (std::nothrow) nl_graph();
+    if (!G) {
+        cudaGraphExecDestroy(ge);
+        cudaGraphDestroy(g);
+        return fail(NL_ERR_OOM, "host allocation failed");
+    }
+    G->nl = nl;
+    G->graph = g;
+    G->exec = ge;
+    *out = G;
+    return NL_OK;
+}
+
+nl_status nl_graph_launch(nl_graph *g, void *stream)
+{
+    if (!g) return fail(NL_ERR_ARG, "graph is NULL");
+    CK(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+    return NL_OK;
+}
+
+nl_status nl_graph_check(nl_graph *g, void *stream)
+{
+    if (!g) return fail(NL_ERR_ARG, "graph is NULL");
+    nl_list *nl = g->nl;
+    nl_status st = read_status(nl, (cudaStream_t)stream);
+    if (st != NL_OK) return st;
+    const Status &h = *nl->hst;
+    if (h.bad_input & 7u) return fail(NL_ERR_ARG, "invalid particle input in the last replay");
+    if (h.bad_input & 8u) return fail(NL_ERR_RADIUS, "support*h >= L/2 on a periodic axis");
+    if (h.node_overflow)
+        return fail(NL_ERR_CAPACITY, "octree needs %u more nodes than the graph reserved",
+                    h.node_overflow);
+    if (h.stage_overflow)
+        return fail(NL_ERR_CAPACITY, "%u super-cluster lists did not fit the graph's buffers",
+                    h.stage_overflow);
+    nl->n_leaves = h.n_leaves;
+    nl->n_nodes = h.n_nodes;
+    nl->list_bytes = h.list_used;
+    nl->n_entries = h.n_entries;
+    nl->n_tiles = h.n_tiles;
+    nl->node_visits = h.node_visits;
+    nl->leaf_visits = h.leaf_visits;
+    nl->j_examined = h.j_examined;
+    nl->tile_tests = h.tile_tests;
+    return NL_OK;
+}
+
+nl_status nl_graph_free(nl_graph *g)
+{
+    if (!g) return NL_OK;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return NL_OK;
+}
+
+nl_status nl_autotune_batch(const float *x, const float *y, const float *z, const float *h,
+                            const float *m, int32_t nsys, const int64_t *offsets,
+                            const nl_box *boxes, const nl_params *base, int32_t reps,
+                            nl_params *best, float *best_ms, void *stream)
+{
+    if (!base || !best || !m || !offsets || nsys < 1) return fail(NL_ERR_ARG, "NULL argument");
+    if (reps < 1) return fail(NL_ERR_ARG, "reps must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = offsets[nsys];
+    DevBuf rho;
+    CK(rho.ensure((size_t)n * 4));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    nl_list *nl = new (std::nothrow) nl_list();
+    if (!nl) return fail(NL_ERR_OOM, "host allocation failed");
+    const int Ms[3] = {4, 8, 16}, T[2] = {128, 256}, B[3] = {2, 3, 4};
+    float bms = INFINITY;
+    nl_params bp = *base;
+    nl_status st = NL_OK;
+    for (int mi = 0; mi < 3 && st == NL_OK; ++mi)
+        for (int ti = 0; ti < 2 && st == NL_OK; ++ti)
+            for (int bi = 0; bi < 3 && st == NL_OK; ++bi) {
+                nl_params c = *base;
+                c.cluster = Ms[mi];
+                c.threads_per_block = T[ti];
+                c.blocks_per_sm = B[bi];
+                float tot = 0.f;
+                for (int r = 0; r <= reps && st == NL_OK; ++r) {
+                    cudaEventRecord(e0, s);
+                    st = nl_rebuild_batch(nl, x, y, z, h, nsys, offsets, boxes, &c, stream);
+                    if (st == NL_OK) st = nl_density_pass(nl, m, rho.as<float>(), stream);
+                    cudaEventRecord(e1, s);
+                    cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (r > 0) tot += ms;  // r = 0 warms up
+                }
+                if (st == NL_OK && tot / reps < bms) {
+                    bms = tot / reps;
+                    bp = c;
+                }
+            }
+    nl->release_all();
+    delete nl;
+    rho.release();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != NL_OK) return st;
+    *best = bp;
+    if (best_ms) *best_ms = bms;
+    return NL_OK;
+}
+
 nl_status nl_free(nl_list *nl)
 {
     if (!nl) return NL_OK;
@@ -764,7 +958,8 @@ nl_status nl_density_pass(const nl_list *cnl, const float *m, float *rho, void *
     CK(nl->mark(6, s));
     PassArgs a = pass_args(nl);
     a.out0 = rho;
-    CK(launch_pass(a, PASS_DENSITY, nl->p.cluster, nl->any_per, nl->num_sms, s));
+    CK(launch_pass(a, PASS_DENSITY, nl->p.cluster, nl->any_per, nl->num_sms, s,
+                       nl->p.threads_per_block, nl->p.blocks_per_sm));
     CK(nl->mark(7, s));
     return NL_OK;
 }
@@ -791,7 +986,8 @@ nl_status nl_force_pass(const nl_list *cnl, int32_t kind, const float *params, c
         CK(launch_gather_aux(nl->npad, nl->perm_pad.as<uint32_t>(), m, pres, rho, 1,
                              nl->aux.as<float2>(), s));
         CK(nl->mark(6, s));
-        CK(launch_pass(a, PASS_SPH, nl->p.cluster, nl->any_per, nl->num_sms, s));
+        CK(launch_pass(a, PASS_SPH, nl->p.cluster, nl->any_per, nl->num_sms, s,
+                       nl->p.threads_per_block, nl->p.blocks_per_sm));
         CK(nl->mark(7, s));
     } else if (kind == NL_FORCE_LJ) {
         if (!params) return fail(NL_ERR_ARG, "LJ force needs params {eps, sigma}");
@@ -801,7 +997,8 @@ nl_status nl_force_pass(const nl_list *cnl, int32_t kind, const float *params, c
         a.p1 = params[1];
         CK(nl->mark(5, s));
         CK(nl->mark(6, s));
-        CK(launch_pass(a, PASS_LJ, nl->p.cluster, nl->any_per, nl->num_sms, s));
+        CK(launch_pass(a, PASS_LJ, nl->p.cluster, nl->any_per, nl->num_sms, s,
+                       nl->p.threads_per_block, nl->p.blocks_per_sm));
         CK(nl->mark(7, s));
     } else {
         return fail(NL_ERR_ARG, "unknown force kind %d", kind);
@@ -817,7 +1014,8 @@ nl_status nl_neighbor_counts(const nl_list *cnl, uint32_t *counts, void *stream)
     nl_list *nl = const_cast<nl_list *>(cnl);
     PassArgs a = pass_args(nl);
     a.outc = counts;
-    CK(launch_pass(a, PASS_COUNT, nl->p.cluster, nl->any_per, nl->num_sms, (cudaStream_t)stream));
+    CK(launch_pass(a, PASS_COUNT, nl->p.cluster, nl->any_per, nl->num_sms, (cudaStream_t)stream,
+                   nl->p.threads_per_block, nl->p.blocks_per_sm));
     return NL_OK;
 }
 

@@ -47,10 +47,15 @@ __device__ __forceinline__ uint32_t sys_of(const uint32_t *t, uint32_t nsys, uin
 
 // Device status words written by the build kernels and read back once.
 struct Status {
-    unsigned int bad_input;   // bit0 non-finite coordinate, bit1 outside box, bit2 bad h
+    // build words (keys, octree)
+    unsigned int bad_input;   // bit0 non-finite coordinate, bit1 outside box, bit2 bad h,
+                              // bit3 radius >= L/2 on a periodic axis
     unsigned int rmax_bits;   // max over particles of support*h (FP32 bits, >= 0)
     unsigned int n_leaves;
     unsigned int n_nodes;
+    unsigned int node_overflow;  // nodes beyond the preallocated capacity (graph replays)
+    unsigned int pad0[3];
+    // search words (reset before every search); ticket is the first of them
     unsigned int ticket;      // work counter of persistent kernels
     unsigned int stage_overflow;
     unsigned int max_count;   // longest super-cluster list seen when staging overflowed
@@ -374,7 +379,8 @@ cudaError_t octree_leaves(const uint64_t *keys, uint32_t n, int bucket, const Sy
                           uint8_t *lcp, uint8_t *lev, uint32_t *leaf_first, uint8_t *leaf_lev,
                           uint32_t *bsum, Status *st, cudaStream_t s);
 // step 3: node offsets per leaf; n_nodes lands in st->n_nodes.
-cudaError_t octree_count_nodes(const uint64_t *keys, uint32_t n_leaves, const SysTables &t,
+// The leaf count is read on the device (st->n_leaves <= n).
+cudaError_t octree_count_nodes(const uint64_t *keys, uint32_t n, const SysTables &t,
                                const uint32_t *leaf_first, const uint8_t *leaf_lev,
                                uint32_t *nodeoff, uint32_t *bsum, Status *st, cudaStream_t s);
 // step 4: emit pre-order nodes and their boxes.
@@ -387,10 +393,12 @@ struct OctreeOut {
     uint32_t *nchild;
     uint32_t *narrive;
 };
-cudaError_t octree_emit(const uint64_t *keys, uint32_t n, uint32_t n_leaves, uint32_t n_nodes,
-                        const SysTables &t, const uint32_t *leaf_first, const uint8_t *leaf_lev,
+// Leaf and node counts are read on the device; node_cap is the capacity of
+// the node arrays (nodes beyond it are counted in st->node_overflow).
+cudaError_t octree_emit(const uint64_t *keys, uint32_t n, uint32_t node_cap, const SysTables &t,
+                        const uint32_t *leaf_first, const uint8_t *leaf_lev,
                         const uint32_t *nodeoff, const float4 *pos, float support,
-                        const OctreeOut &o, cudaStream_t s);
+                        const OctreeOut &o, Status *st, cudaStream_t s);
 
 struct SearchArgs {
     const float4 *pos;
@@ -411,7 +419,7 @@ struct SearchArgs {
 };
 cudaError_t launch_search_ctl(const SearchArgs &a, const uint32_t *work, uint32_t count,
                               uint32_t *redo, int M, int any_periodic, int grid_blocks,
-                              cudaStream_t s);
+                              int threads, cudaStream_t s);
 
 enum PassKind { PASS_DENSITY = 0, PASS_COUNT = 1, PASS_SPH = 2, PASS_LJ = 3 };
 struct PassArgs {
@@ -433,16 +441,17 @@ struct PassArgs {
     const uint32_t *work;    // optional list of super-clusters to process
     uint32_t nwork;
 };
+// threads 0 = 256; blocks_per_sm 0 = default
 cudaError_t launch_pass(const PassArgs &a, int kind, int M, int any_periodic, int num_sms,
-                        cudaStream_t s);
+                        cudaStream_t s, int threads = 0, int blocks_per_sm = 0);
 // aux[k] = (a[perm[k]], ...) for real padded slots, zero for dummies.
 cudaError_t launch_gather_aux(uint32_t npad, const uint32_t *perm_pad, const float *a,
                               const float *b, const float *c, int mode, float2 *aux,
                               cudaStream_t s);
 
 // Octree node boxes only (topology unchanged), e.g. after new radii.
-cudaError_t octree_boxes(uint32_t n_nodes, const float4 *pos, float support, const OctreeOut &o,
-                         cudaStream_t s);
+cudaError_t octree_boxes(uint32_t node_cap, const float4 *pos, float support, const OctreeOut &o,
+                         const Status *st, cudaStream_t s);
 
 // h iteration helpers (hiter.cu); all arrays in padded SFC order (npad).
 cudaError_t launch_fill(float *a, uint32_t n, float v, cudaStream_t s);

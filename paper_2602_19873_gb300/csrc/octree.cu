@@ -100,9 +100,11 @@ constexpr int SC_TILE = SC_THREADS * SC_ITEMS;
 size_t scan_bsum_words(uint32_t n) { return (size_t)(n + SC_TILE - 1) / SC_TILE + 2; }
 
 template <class F>
-__global__ void __launch_bounds__(SC_THREADS) k_scan_reduce(F f, uint32_t n, uint32_t *bsum)
+__global__ void __launch_bounds__(SC_THREADS) k_scan_reduce(F f, uint32_t n, const uint32_t *n_dev,
+                                                           uint32_t *bsum)
 {
     __shared__ uint32_t sh[33];
+    if (n_dev) n = min(n, *n_dev);
     uint32_t base = blockIdx.x * SC_TILE, v = 0;
 #pragma unroll
     for (int it = 0; it < SC_ITEMS; ++it) {
@@ -133,9 +135,11 @@ __global__ void __launch_bounds__(1024) k_scan_bsums(uint32_t *bsum, uint32_t nb
 // processed in blocked order (thread t owns SC_ITEMS consecutive elements).
 template <class F, class S>
 __global__ void __launch_bounds__(SC_THREADS) k_scan_apply(F f, S sink, uint32_t n,
+                                                          const uint32_t *n_dev,
                                                           const uint32_t *bsum)
 {
     __shared__ uint32_t sh[33];
+    if (n_dev) n = min(n, *n_dev);
     uint32_t base = blockIdx.x * SC_TILE + threadIdx.x * SC_ITEMS;
     uint32_t v[SC_ITEMS], s = 0;
 #pragma unroll
@@ -154,17 +158,19 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_apply(F f, S sink, uint32_t
     }
 }
 
+// n: element count, or an upper bound when n_dev points at the count on the
+// device (launches cover the bound; elements past *n_dev contribute zero).
 template <class F, class S>
-static cudaError_t scan_exclusive(F f, S sink, uint32_t n, uint32_t *bsum, uint32_t *total,
-                                  cudaStream_t s)
+static cudaError_t scan_exclusive(F f, S sink, uint32_t n, const uint32_t *n_dev, uint32_t *bsum,
+                                  uint32_t *total, cudaStream_t s)
 {
     uint32_t nb = (n + SC_TILE - 1) / SC_TILE;
     if (nb == 0) {
         return cudaMemsetAsync(total, 0, 4, s);
     }
-    k_scan_reduce<<<nb, SC_THREADS, 0, s>>>(f, n, bsum);
+    k_scan_reduce<<<nb, SC_THREADS, 0, s>>>(f, n, n_dev, bsum);
     k_scan_bsums<<<1, 1024, 0, s>>>(bsum, nb, total);
-    k_scan_apply<<<nb, SC_THREADS, 0, s>>>(f, sink, n, bsum);
+    k_scan_apply<<<nb, SC_THREADS, 0, s>>>(f, sink, n, n_dev, bsum);
     return cudaGetLastError();
 }
 
@@ -252,8 +258,8 @@ cudaError_t octree_leaves(const uint64_t *keys, uint32_t n, int bucket, const Sy
         lcp, n, bucket, lev);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return scan_exclusive(LeafFlag{keys, lev, t}, LeafSink{lev, n, leaf_first, leaf_lev}, n, bsum,
-                          &st->n_leaves, s);
+    return scan_exclusive(LeafFlag{keys, lev, t}, LeafSink{lev, n, leaf_first, leaf_lev}, n,
+                          nullptr, bsum, &st->n_leaves, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -282,21 +288,21 @@ struct NodeCount {
 };
 
 struct NodeSink {
-    uint32_t nl;
+    const uint32_t *nl;   // leaf count on the device
     uint32_t *nodeoff;
     __device__ void operator()(uint32_t i, uint32_t excl, uint32_t v) const
     {
         nodeoff[i] = excl;
-        if (i == nl - 1) nodeoff[nl] = excl + v;
+        if (i == *nl - 1) nodeoff[i + 1] = excl + v;
     }
 };
 
-cudaError_t octree_count_nodes(const uint64_t *keys, uint32_t n_leaves, const SysTables &t,
+cudaError_t octree_count_nodes(const uint64_t *keys, uint32_t n, const SysTables &t,
                                const uint32_t *leaf_first, const uint8_t *leaf_lev,
                                uint32_t *nodeoff, uint32_t *bsum, Status *st, cudaStream_t s)
 {
-    return scan_exclusive(NodeCount{keys, leaf_first, leaf_lev, t}, NodeSink{n_leaves, nodeoff},
-                          n_leaves, bsum, &st->n_nodes, s);
+    return scan_exclusive(NodeCount{keys, leaf_first, leaf_lev, t},
+                          NodeSink{&st->n_leaves, nodeoff}, n, &st->n_leaves, bsum, &st->n_nodes, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -324,13 +330,18 @@ __device__ __forceinline__ uint32_t leaf_of(const uint32_t *leaf_first, uint32_t
     return lo;
 }
 
-__global__ void k_emit_nodes(const uint64_t *__restrict__ keys, uint32_t n, uint32_t nl,
-                             uint32_t nn, SysTables t, const uint32_t *__restrict__ leaf_first,
+__global__ void k_emit_nodes(const uint64_t *__restrict__ keys, uint32_t n, uint32_t node_cap,
+                             SysTables t, const uint32_t *__restrict__ leaf_first,
                              const uint8_t *__restrict__ leaf_lev,
-                             const uint32_t *__restrict__ nodeoff, OctreeOut o)
+                             const uint32_t *__restrict__ nodeoff, OctreeOut o, Status *st)
 {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t nl = st->n_leaves, nn = st->n_nodes;
     if (i >= nl) return;
+    if (nodeoff[i + 1] > node_cap) {  // no room: counted, nothing written
+        atomicAdd(&st->node_overflow, nodeoff[i + 1] - max(nodeoff[i], node_cap));
+        return;
+    }
     const int c = leaf_lcp(keys, leaf_first, t, i);
     const uint32_t v0 = nodeoff[i], e = nodeoff[i + 1] - v0;
     const uint32_t first = leaf_first[i];
@@ -383,10 +394,11 @@ __global__ void k_emit_nodes(const uint64_t *__restrict__ keys, uint32_t n, uint
     }
 }
 
-__global__ void k_node_boxes(uint32_t nn, const float4 *__restrict__ pos, float support, OctreeOut o)
+__global__ void k_node_boxes(uint32_t node_cap, const float4 *__restrict__ pos, float support,
+                             OctreeOut o, const Status *st)
 {
     uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= nn) return;
+    if (v >= min(node_cap, st->n_nodes) || st->node_overflow) return;
     int skip = __float_as_int(o.nhi[v].w);
     if ((uint32_t)skip != v + 1) return;  // internal nodes are reduced by their last child
     int2 rg = o.nrng[v];
@@ -425,26 +437,27 @@ __global__ void k_node_boxes(uint32_t nn, const float4 *__restrict__ pos, float 
     }
 }
 
-cudaError_t octree_emit(const uint64_t *keys, uint32_t n, uint32_t n_leaves, uint32_t n_nodes,
-                        const SysTables &t, const uint32_t *leaf_first, const uint8_t *leaf_lev,
+cudaError_t octree_emit(const uint64_t *keys, uint32_t n, uint32_t node_cap, const SysTables &t,
+                        const uint32_t *leaf_first, const uint8_t *leaf_lev,
                         const uint32_t *nodeoff, const float4 *pos, float support,
-                        const OctreeOut &o, cudaStream_t s)
+                        const OctreeOut &o, Status *st, cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(o.nchild, 0, (size_t)n_nodes * 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(o.narrive, 0, (size_t)n_nodes * 4, s);
+    cudaError_t e = cudaMemsetAsync(o.nchild, 0, (size_t)node_cap * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(o.narrive, 0, (size_t)node_cap * 4, s);
     if (e != cudaSuccess) return e;
-    k_emit_nodes<<<(n_leaves + 127) / 128, 128, 0, s>>>(keys, n, n_leaves, n_nodes, t, leaf_first,
-                                                        leaf_lev, nodeoff, o);
-    k_node_boxes<<<(n_nodes + 127) / 128, 128, 0, s>>>(n_nodes, pos, support, o);
+    // one thread per leaf (n bounds the leaf count), one per node slot
+    k_emit_nodes<<<(n + 127) / 128, 128, 0, s>>>(keys, n, node_cap, t, leaf_first, leaf_lev,
+                                                 nodeoff, o, st);
+    k_node_boxes<<<(node_cap + 127) / 128, 128, 0, s>>>(node_cap, pos, support, o, st);
     return cudaGetLastError();
 }
 
-cudaError_t octree_boxes(uint32_t n_nodes, const float4 *pos, float support, const OctreeOut &o,
-                         cudaStream_t s)
+cudaError_t octree_boxes(uint32_t node_cap, const float4 *pos, float support, const OctreeOut &o,
+                         const Status *st, cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(o.narrive, 0, (size_t)n_nodes * 4, s);
+    cudaError_t e = cudaMemsetAsync(o.narrive, 0, (size_t)node_cap * 4, s);
     if (e != cudaSuccess) return e;
-    k_node_boxes<<<(n_nodes + 127) / 128, 128, 0, s>>>(n_nodes, pos, support, o);
+    k_node_boxes<<<(node_cap + 127) / 128, 128, 0, s>>>(node_cap, pos, support, o, st);
     return cudaGetLastError();
 }
 

@@ -5,22 +5,27 @@
 namespace nlg {
 
 constexpr int kPassBlocksPerSM = 4;
-cudaError_t launch_pass_density(const PassArgs &a, int M, int per, int grid, cudaStream_t s);
-cudaError_t launch_pass_count(const PassArgs &a, int M, int per, int grid, cudaStream_t s);
-cudaError_t launch_pass_sph(const PassArgs &a, int M, int per, int grid, cudaStream_t s);
-cudaError_t launch_pass_lj(const PassArgs &a, int M, int per, int grid, cudaStream_t s);
+cudaError_t launch_pass_density(const PassArgs &a, int M, int per, int grid, int threads,
+                          cudaStream_t s);
+cudaError_t launch_pass_count(const PassArgs &a, int M, int per, int grid, int threads,
+                          cudaStream_t s);
+cudaError_t launch_pass_sph(const PassArgs &a, int M, int per, int grid, int threads,
+                          cudaStream_t s);
+cudaError_t launch_pass_lj(const PassArgs &a, int M, int per, int grid, int threads,
+                          cudaStream_t s);
 
 cudaError_t launch_pass(const PassArgs &a, int kind, int M, int any_periodic, int num_sms,
-                        cudaStream_t s)
+                        cudaStream_t s, int threads, int blocks_per_sm)
 {
     cudaError_t e = cudaMemsetAsync(&a.st->pass_ticket, 0, 4, s);
     if (e != cudaSuccess) return e;
-    int grid = num_sms * kPassBlocksPerSM;
+    const int tpb = threads ? threads : 256;
+    const int grid = num_sms * (blocks_per_sm ? blocks_per_sm : kPassBlocksPerSM);
     switch (kind) {
-    case PASS_DENSITY: return launch_pass_density(a, M, any_periodic, grid, s);
-    case PASS_COUNT: return launch_pass_count(a, M, any_periodic, grid, s);
-    case PASS_SPH: return launch_pass_sph(a, M, any_periodic, grid, s);
-    case PASS_LJ: return launch_pass_lj(a, M, any_periodic, grid, s);
+    case PASS_DENSITY: return launch_pass_density(a, M, any_periodic, grid, tpb, s);
+    case PASS_COUNT: return launch_pass_count(a, M, any_periodic, grid, tpb, s);
+    case PASS_SPH: return launch_pass_sph(a, M, any_periodic, grid, tpb, s);
+    case PASS_LJ: return launch_pass_lj(a, M, any_periodic, grid, tpb, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -144,8 +144,11 @@ __global__ void __launch_bounds__(PS_THREADS) k_pass(PassArgs a)
             }
         }
 
-        const uint32_t *rec = reinterpret_cast<const uint32_t *>(a.list) + a.rec_off[s];
-        const uint32_t cnt = rec[0];
+        // a super-cluster whose list was not stored (an overflow inside a graph
+        // replay, reported by nl_graph_check) is read as an empty list
+        const uint32_t roff = a.rec_off[s];
+        const uint32_t *rec = reinterpret_cast<const uint32_t *>(a.list) + (roff == kBadRecord ? 0u : roff);
+        const uint32_t cnt = roff == kBadRecord ? 0u : rec[0];
         const uint8_t *masks = reinterpret_cast<const uint8_t *>(rec + 1);
         const uint32_t *body = rec + 1 + ((cnt + 3u) >> 2);
         const uint8_t *bodyb = reinterpret_cast<const uint8_t *>(body);
@@ -296,30 +299,33 @@ __global__ void __launch_bounds__(PS_THREADS) k_pass(PassArgs a)
 }
 
 template <int M, int KIND>
-static void launch_mk(const PassArgs &a, int per, int grid, cudaStream_t s)
+static void launch_mk(const PassArgs &a, int per, int grid, int threads, cudaStream_t s)
 {
-    const size_t smem = (size_t)(PS_THREADS / 32) * pass_smem_per_warp<M, KIND>();
+    // the attribute is set for the largest block so that any shape fits
+    const size_t smax = (size_t)(PS_THREADS / 32) * pass_smem_per_warp<M, KIND>();
+    const size_t smem = (size_t)(threads / 32) * pass_smem_per_warp<M, KIND>();
     static bool attr[2] = {false, false};
     if (!attr[per ? 1 : 0]) {
         if (per)
-            cudaFuncSetAttribute(k_pass<M, true, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_pass<M, true, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
         else
-            cudaFuncSetAttribute(k_pass<M, false, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_pass<M, false, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
         attr[per ? 1 : 0] = true;
     }
     if (per)
-        k_pass<M, true, KIND><<<grid, PS_THREADS, smem, s>>>(a);
+        k_pass<M, true, KIND><<<grid, threads, smem, s>>>(a);
     else
-        k_pass<M, false, KIND><<<grid, PS_THREADS, smem, s>>>(a);
+        k_pass<M, false, KIND><<<grid, threads, smem, s>>>(a);
 }
 
 template <int KIND>
-static cudaError_t launch_k(const PassArgs &a, int M, int per, int grid, cudaStream_t s)
+static cudaError_t launch_k(const PassArgs &a, int M, int per, int grid, int threads, cudaStream_t s)
 {
+    if (threads != 128 && threads != PS_THREADS) return cudaErrorInvalidValue;
     switch (M) {
-    case 4: launch_mk<4, KIND>(a, per, grid, s); break;
-    case 8: launch_mk<8, KIND>(a, per, grid, s); break;
-    case 16: launch_mk<16, KIND>(a, per, grid, s); break;
+    case 4: launch_mk<4, KIND>(a, per, grid, threads, s); break;
+    case 8: launch_mk<8, KIND>(a, per, grid, threads, s); break;
+    case 16: launch_mk<16, KIND>(a, per, grid, threads, s); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -2,8 +2,9 @@
 #include "pass_impl.cuh"
 
 namespace nlg {
-cudaError_t launch_pass_lj(const PassArgs &a, int M, int per, int grid, cudaStream_t s)
+cudaError_t launch_pass_lj(const PassArgs &a, int M, int per, int grid, int threads,
+                          cudaStream_t s)
 {
-    return launch_k<PASS_LJ>(a, M, per, grid, s);
+    return launch_k<PASS_LJ>(a, M, per, grid, threads, s);
 }
 }  // namespace nlg

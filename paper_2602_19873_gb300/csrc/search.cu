@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(SR_THREADS, 3) k_search(SearchArgs a, SearchCt
     __shared__ uint32_t wins[SR_WARPS][WIN_WORDS];
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
     uint32_t *win = wins[warp];
-    const uint32_t slot = blockIdx.x * SR_WARPS + warp;
+    const uint32_t slot = blockIdx.x * (blockDim.x >> 5) + warp;
     uint32_t *stJ = a.stageJ + (size_t)slot * a.stage_cap;
     uint8_t *stM = a.stageM + (size_t)slot * a.stage_cap;
     const uint32_t II = lane % M;
@@ -157,8 +157,10 @@ __global__ void __launch_bounds__(SR_THREADS, 3) k_search(SearchArgs a, SearchCt
         // the super-cluster's system: its box and its own octree subtree
         const uint32_t sy = sys_of(a.sys.pad_off, a.sys.nsys, base);
         const DevBox &box = a.sys.box[sy];
-        const uint32_t vroot = a.sys.root[sy];
-        const uint32_t vend = (uint32_t)__float_as_int(a.nhi[vroot].w);
+        // (clamped to the node arrays: after a node overflow in a graph replay
+        // the tables may be stale, and the replay is reported as failed)
+        const uint32_t vroot = min(a.sys.root[sy], a.nnodes - 1);
+        const uint32_t vend = min((uint32_t)__float_as_int(a.nhi[vroot].w), a.nnodes);
 
         // i-cluster box of this lane's cluster (lane & 7)
         const float4 ilo = a.clo[s * kSC + (lane & 7)];
@@ -303,23 +305,25 @@ __global__ void __launch_bounds__(SR_THREADS, 3) k_search(SearchArgs a, SearchCt
 }
 
 template <int M>
-static void launch_m(const SearchArgs &a, const SearchCtl &c, int per, int grid, cudaStream_t s)
+static void launch_m(const SearchArgs &a, const SearchCtl &c, int per, int grid, int threads,
+                     cudaStream_t s)
 {
     if (per)
-        k_search<M, true><<<grid, SR_THREADS, 0, s>>>(a, c);
+        k_search<M, true><<<grid, threads, 0, s>>>(a, c);
     else
-        k_search<M, false><<<grid, SR_THREADS, 0, s>>>(a, c);
+        k_search<M, false><<<grid, threads, 0, s>>>(a, c);
 }
 
 cudaError_t launch_search_ctl(const SearchArgs &a, const uint32_t *work, uint32_t count,
-                              uint32_t *redo, int M, int any_periodic, int grid,
+                              uint32_t *redo, int M, int any_periodic, int grid, int threads,
                               cudaStream_t s)
 {
     SearchCtl c{work, count, redo};
+    if (threads != 128 && threads != SR_THREADS) return cudaErrorInvalidValue;
     switch (M) {
-    case 4: launch_m<4>(a, c, any_periodic, grid, s); break;
-    case 8: launch_m<8>(a, c, any_periodic, grid, s); break;
-    case 16: launch_m<16>(a, c, any_periodic, grid, s); break;
+    case 4: launch_m<4>(a, c, any_periodic, grid, threads, s); break;
+    case 8: launch_m<8>(a, c, any_periodic, grid, threads, s); break;
+    case 16: launch_m<16>(a, c, any_periodic, grid, threads, s); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

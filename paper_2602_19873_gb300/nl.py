@@ -36,7 +36,8 @@ class nl_box(C.Structure):
 
 class nl_params(C.Structure):
     _fields_ = [("key", C.c_int32), ("cluster", C.c_int32), ("support", C.c_float),
-                ("compress", C.c_int32), ("leaf_bucket", C.c_int32)]
+                ("compress", C.c_int32), ("leaf_bucket", C.c_int32),
+                ("threads_per_block", C.c_int32), ("blocks_per_sm", C.c_int32)]
 
 
 class nl_sizes(C.Structure):
@@ -71,6 +72,11 @@ _SIGS = {
     "nl_rebuild_batch": (C.c_int, [P, P, P, P, P, C.c_int32, P, P, P, P]),
     "nl_iterate_h_batch": (C.c_int, [P, P, P, P, P, C.c_int32, P, P, P, C.c_float, C.c_float,
                                      C.c_int32, C.c_float, C.c_int32, P, P, P]),
+    "nl_graph_create": (C.c_int, [P, P, P, P, P, P, P, C.c_int32, P, P, P, P, P]),
+    "nl_graph_launch": (C.c_int, [P, P]),
+    "nl_graph_check": (C.c_int, [P, P]),
+    "nl_graph_free": (C.c_int, [P]),
+    "nl_autotune_batch": (C.c_int, [P, P, P, P, P, C.c_int32, P, P, P, C.c_int32, P, P, P]),
     "nl_iterate_h": (C.c_int, [P, P, P, P, P, C.c_int64, P, P, C.c_float, C.c_float, C.c_int32,
                                C.c_float, C.c_int32, P, P, P]),
 }
@@ -142,12 +148,18 @@ def make_box(box):
     return b
 
 
-def make_params(key=NL_KEY_HILBERT, cluster=8, support=2.0, compress=1, leaf_bucket=64):
+def make_params(key=NL_KEY_HILBERT, cluster=8, support=2.0, compress=1, leaf_bucket=64,
+                threads_per_block=0, blocks_per_sm=0):
     p = nl_params()
     load().nl_default_params(C.byref(p))
     p.key, p.cluster, p.support = int(key), int(cluster), float(support)
     p.compress, p.leaf_bucket = int(compress), int(leaf_bucket)
+    p.threads_per_block, p.blocks_per_sm = int(threads_per_block), int(blocks_per_sm)
     return p
+
+
+def params_dict(p):
+    return {f: getattr(p, f) for f, _ in nl_params._fields_}
 
 
 NL_NOALLOC_MAX_N = 1048576
@@ -160,6 +172,45 @@ def sfc_order_noalloc(x, y, z, h, box, key, support, keys, perm, stream=None):
     _check(load().nl_sfc_order_noalloc(_ptr(x), _ptr(y), _ptr(z), _ptr(h), int(x.numel()),
                                        C.byref(b), int(key), float(support), _ptr(keys),
                                        _ptr(perm), _stream(stream)))
+
+
+def autotune_batch(x, y, z, h, m, offsets, boxes, base, reps=2, stream=None):
+    """nl_autotune_batch: returns (best nl_params, mean ms)."""
+    nsys = len(boxes)
+    offs = np.ascontiguousarray(offsets, dtype=np.int64)
+    barr = (nl_box * nsys)(*[make_box(b) for b in boxes])
+    best = nl_params()
+    ms = C.c_float()
+    _check(load().nl_autotune_batch(_ptr(x), _ptr(y), _ptr(z), _ptr(h), _ptr(m), nsys,
+                                    offs.ctypes.data, barr, C.byref(base), int(reps),
+                                    C.byref(best), C.byref(ms), _stream(stream)))
+    return best, ms.value
+
+
+class Graph:
+    """nl_graph: one captured build + density step of a batch."""
+
+    def __init__(self, nlist, x, y, z, h, m, rho, offsets, boxes, params, stream):
+        nlist.ensure_handle()
+        nsys = len(boxes)
+        offs = np.ascontiguousarray(offsets, dtype=np.int64)
+        barr = (nl_box * nsys)(*[make_box(b) for b in boxes])
+        self.handle = C.c_void_p()
+        self.nlist = nlist
+        _check(load().nl_graph_create(nlist.handle, _ptr(x), _ptr(y), _ptr(z), _ptr(h), _ptr(m),
+                                      _ptr(rho), nsys, offs.ctypes.data, barr, C.byref(params),
+                                      _stream(stream), C.byref(self.handle)))
+
+    def launch(self, stream=None):
+        _check(load().nl_graph_launch(self.handle, _stream(stream)))
+
+    def check(self, stream=None):
+        _check(load().nl_graph_check(self.handle, _stream(stream)))
+
+    def free(self):
+        if self.handle:
+            load().nl_graph_free(self.handle)
+            self.handle = None
 
 
 class NeighborList:

@@ -41,7 +41,7 @@ def _pad_offsets(systems, M):
 @pytest.mark.parametrize("cluster", [4, 8, 16])
 def test_batch_matches_systems_alone(cluster):
     import torch
-    systems = _batch(seed=401 + cluster)
+    systems = _batch(seed=401 + cluster, log_n=(2.7, 3.6))
     offs, cat, dev = _concat(systems)
     p = nl.make_params(key=1, cluster=cluster, support=2.0)
     L = nl.NeighborList().build_batch(dev["x"], dev["y"], dev["z"], dev["h"], offs,
@@ -123,7 +123,7 @@ def test_batch_h_iteration_window():
 
 def test_batch_rejects_bad_tables():
     import torch
-    systems = _batch(seed=431, n_systems=3)
+    systems = _batch(seed=431, n_systems=3, log_n=(2.7, 3.0))
     offs, cat, dev = _concat(systems)
     p = nl.make_params(key=1, cluster=8, support=2.0)
     bad = offs.copy()
