@@ -22,7 +22,8 @@ __all__ = [
     "sort", "octree", "brute_neighbors", "gather_all", "symmetrize", "cluster_lists",
     "encode_block", "encode_record", "decode_record", "record_bytes", "stream_nibbles",
     "w", "dw", "W", "density", "sph_force", "lj_force", "lj_energy", "gather_counts_brute",
-    "pred", "dist2", "dist2_row", "num_threads", "pipeline_lists",
+    "pred", "dist2", "dist2_row", "num_threads", "pipeline_lists", "mlp_nparams",
+    "mlp_forward", "mlp_loss_grad",
 ]
 
 
@@ -100,6 +101,9 @@ def lib():
                 "orc_gather_counts_brute": (None, [I64, P, P, P, P, P, F32, I64, P, P]),
                 "orc_dist2_row": (None, [I64, P, P, P, P, I64, P]),
                 "orc_num_threads": (C.c_int, []),
+                "orc_mlp_nparams": (I64, []),
+                "orc_mlp_forward": (None, [I64, P, P, P]),
+                "orc_mlp_loss_grad": (C.c_double, [I64, P, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -407,3 +411,25 @@ def dist2_row(xs, ys, zs, box, i):
     b = _box(box)
     lib().orc_dist2_row(len(xs), _p(xs), _p(ys), _p(zs), C.byref(b), int(i), _p(out))
     return out
+
+
+# ------------------------------------------------------------------------------ MLP
+def mlp_nparams():
+    return lib().orc_mlp_nparams()
+
+
+def mlp_forward(X, P):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    out = np.zeros(len(X))
+    lib().orc_mlp_forward(len(X), _p(X), _p(P), _p(out))
+    return out
+
+
+def mlp_loss_grad(X, t, P):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    G = np.zeros(mlp_nparams())
+    loss = lib().orc_mlp_loss_grad(len(X), _p(X), _p(t), _p(P), _p(G))
+    return loss, G

@@ -1086,3 +1086,111 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Smoothing-length MLP (not in the paper): F=8 inputs, three hidden layers */
+/* of 64 with SiLU, one output; loss = mean squared error.  Plain FP64.     */
+/* Weight layout (row-major, out x in): W1 64x8, W2 64x64, W3 64x64, W4 1x64 */
+/* packed as W1 b1 W2 b2 W3 b3 W4 b4 (orc_mlp_nparams values).              */
+/* ------------------------------------------------------------------------ */
+#define MLP_F 8
+#define MLP_H 64
+
+int64_t orc_mlp_nparams(void)
+{
+    return (int64_t)MLP_H * MLP_F + MLP_H + 2 * ((int64_t)MLP_H * MLP_H + MLP_H) + MLP_H + 1;
+}
+
+static double silu(double z) { return z / (1.0 + exp(-z)); }
+
+static double dsilu(double z)
+{
+    double s = 1.0 / (1.0 + exp(-z));
+    return s * (1.0 + z * (1.0 - s));
+}
+
+/* One dense layer: out[o] = b[o] + sum_i W[o][i] in[i]. */
+static void dense(int nout, int nin, const double *W, const double *b, const double *in,
+                  double *out)
+{
+    for (int o = 0; o < nout; ++o) {
+        double s = b[o];
+        for (int i = 0; i < nin; ++i) s += W[(int64_t)o * nin + i] * in[i];
+        out[o] = s;
+    }
+}
+
+/* Forward for n samples; X n x 8; pred n. */
+void orc_mlp_forward(int64_t n, const double *X, const double *P, double *pred)
+{
+    const double *W1 = P, *b1 = W1 + MLP_H * MLP_F, *W2 = b1 + MLP_H, *b2 = W2 + MLP_H * MLP_H;
+    const double *W3 = b2 + MLP_H, *b3 = W3 + MLP_H * MLP_H, *W4 = b3 + MLP_H, *b4 = W4 + MLP_H;
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < n; ++r) {
+        double z1[MLP_H], h1[MLP_H], z2[MLP_H], h2[MLP_H], z3[MLP_H], h3[MLP_H], y;
+        dense(MLP_H, MLP_F, W1, b1, X + r * MLP_F, z1);
+        for (int k = 0; k < MLP_H; ++k) h1[k] = silu(z1[k]);
+        dense(MLP_H, MLP_H, W2, b2, h1, z2);
+        for (int k = 0; k < MLP_H; ++k) h2[k] = silu(z2[k]);
+        dense(MLP_H, MLP_H, W3, b3, h2, z3);
+        for (int k = 0; k < MLP_H; ++k) h3[k] = silu(z3[k]);
+        dense(1, MLP_H, W4, b4, h3, &y);
+        pred[r] = y;
+    }
+}
+
+/* Loss = (1/n) sum_r (pred_r - t_r)^2 and its gradient G (same packing as
+ * P) by reverse-mode differentiation of the forward above.  Returns loss. */
+double orc_mlp_loss_grad(int64_t n, const double *X, const double *t, const double *P, double *G)
+{
+    const int64_t np = orc_mlp_nparams();
+    const double *W1 = P, *b1 = W1 + MLP_H * MLP_F, *W2 = b1 + MLP_H, *b2 = W2 + MLP_H * MLP_H;
+    const double *W3 = b2 + MLP_H, *b3 = W3 + MLP_H * MLP_H, *W4 = b3 + MLP_H, *b4 = W4 + MLP_H;
+    for (int64_t k = 0; k < np; ++k) G[k] = 0.0;
+    double *gW1 = G, *gb1 = gW1 + MLP_H * MLP_F, *gW2 = gb1 + MLP_H, *gb2 = gW2 + MLP_H * MLP_H;
+    double *gW3 = gb2 + MLP_H, *gb3 = gW3 + MLP_H * MLP_H, *gW4 = gb3 + MLP_H, *gb4 = gW4 + MLP_H;
+    double loss = 0.0;
+    for (int64_t r = 0; r < n; ++r) {
+        const double *x = X + r * MLP_F;
+        double z1[MLP_H], h1[MLP_H], z2[MLP_H], h2[MLP_H], z3[MLP_H], h3[MLP_H], y;
+        dense(MLP_H, MLP_F, W1, b1, x, z1);
+        for (int k = 0; k < MLP_H; ++k) h1[k] = silu(z1[k]);
+        dense(MLP_H, MLP_H, W2, b2, h1, z2);
+        for (int k = 0; k < MLP_H; ++k) h2[k] = silu(z2[k]);
+        dense(MLP_H, MLP_H, W3, b3, h2, z3);
+        for (int k = 0; k < MLP_H; ++k) h3[k] = silu(z3[k]);
+        dense(1, MLP_H, W4, b4, h3, &y);
+        double e = y - t[r];
+        loss += e * e;
+        double dy = 2.0 * e / (double)n;
+        double d3[MLP_H], d2[MLP_H], d1[MLP_H];
+        gb4[0] += dy;
+        for (int k = 0; k < MLP_H; ++k) {
+            gW4[k] += dy * h3[k];
+            d3[k] = dy * W4[k] * dsilu(z3[k]);
+        }
+        for (int o = 0; o < MLP_H; ++o) {
+            gb3[o] += d3[o];
+            for (int i = 0; i < MLP_H; ++i) gW3[o * MLP_H + i] += d3[o] * h2[i];
+        }
+        for (int i = 0; i < MLP_H; ++i) {
+            double s = 0.0;
+            for (int o = 0; o < MLP_H; ++o) s += d3[o] * W3[o * MLP_H + i];
+            d2[i] = s * dsilu(z2[i]);
+        }
+        for (int o = 0; o < MLP_H; ++o) {
+            gb2[o] += d2[o];
+            for (int i = 0; i < MLP_H; ++i) gW2[o * MLP_H + i] += d2[o] * h1[i];
+        }
+        for (int i = 0; i < MLP_H; ++i) {
+            double s = 0.0;
+            for (int o = 0; o < MLP_H; ++o) s += d2[o] * W2[o * MLP_H + i];
+            d1[i] = s * dsilu(z1[i]);
+        }
+        for (int o = 0; o < MLP_H; ++o) {
+            gb1[o] += d1[o];
+            for (int i = 0; i < MLP_F; ++i) gW1[o * MLP_F + i] += d1[o] * x[i];
+        }
+    }
+    return loss / (double)n;
+}
