@@ -294,6 +294,49 @@ nl_status nl_autotune_batch(const float *x, const float *y, const float *z, cons
                             const nl_box *boxes, const nl_params *base, int32_t reps,
                             nl_params *best, float *best_ms, void *stream);
 
+/* Learned start for the h iteration (not in the paper).  A small MLP maps
+ * per-cluster SFC density features to log(h / e64) (e64 = largest side of
+ * the cluster's super-cluster box): 8 features -> 64 -> 64 -> 64 (SiLU) -> 1,
+ * BF16 tensor-core matrix products with FP32 accumulation, FP32 master
+ * weights, Adam.  Features of cluster c, with e(B) the largest side of box B,
+ * e8 the cluster box, e512 / e4096 the boxes of the 8 / 64 super-clusters
+ * around it in its system, L the largest side of the system box and N_s its
+ * particle count: log(e8/e64), log(e512/e64), log(e4096/e64), log(ex/e8),
+ * log(ey/e8), log(ez/e8), log(count/M), log(e64/L) + log(N_s)/3.
+ * Parameters are packed W1 (64x8, row-major out x in) b1 W2 (64x64) b2
+ * W3 (64x64) b3 W4 (64) b4: nl_mlp_nparams() floats. */
+typedef struct nl_mlp nl_mlp;
+int64_t nl_mlp_nparams(void);
+/* Random initialisation (normal, std 1/sqrt(fan-in); zero biases). */
+nl_status nl_mlp_create(uint64_t seed, nl_mlp **out);
+nl_status nl_mlp_free(nl_mlp *mlp);
+/* Host copies of the FP32 parameters (checkpoints). */
+nl_status nl_mlp_get_params(const nl_mlp *mlp, float *params);
+nl_status nl_mlp_set_params(nl_mlp *mlp, const float *params);
+/* Features X (n_clusters x 8, device) and e64 (n_superclusters, device) of a
+ * built list (any smoothing lengths: features depend on positions only). */
+nl_status nl_mlp_features(const nl_list *nl, float *X, float *e64, void *stream);
+/* Training targets of a built list from converged h (device, caller order):
+ * y[c] = log(mean h over the real particles of cluster c / e64), w[c] = 1,
+ * and y = w = 0 for clusters without real particles. */
+nl_status nl_mlp_targets(const nl_list *nl, const float *h, const float *e64, float *y, float *w,
+                         void *stream);
+/* Gradient (device, nl_mlp_nparams floats) and value (*loss, host) of
+ * (1/n) sum_r w_r (pred_r - y_r)^2 over n samples; synchronises. */
+nl_status nl_mlp_grad(nl_mlp *mlp, const float *X, const float *y, const float *w, int64_t n,
+                      float *grad, float *loss, void *stream);
+/* Minibatch Adam training for `epochs` passes over n samples (shuffled with
+ * `seed`); *loss receives the mean loss of the last epoch.  Synchronises. */
+nl_status nl_mlp_train(nl_mlp *mlp, const float *X, const float *y, const float *w, int64_t n,
+                       int32_t epochs, int32_t batch, float lr, uint64_t seed, float *loss,
+                       void *stream);
+nl_status nl_mlp_predict(const nl_mlp *mlp, const float *X, int64_t n, float *pred, void *stream);
+/* Attaches a model to a list; nl_iterate_h(_batch) with start =
+ * NL_HSTART_LEARNED then starts every particle at e64 * exp(prediction of
+ * its cluster).  The exact iteration still decides the result. */
+enum { NL_HSTART_LEARNED = 2 };
+nl_status nl_set_mlp(nl_list *nl, const nl_mlp *mlp);
+
 /* Thread-local description of the last error (never NULL). */
 const char *nl_last_error(void);
 

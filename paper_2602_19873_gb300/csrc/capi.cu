@@ -1,5 +1,6 @@
 // C ABI of the neighbor-list library: argument checks, device workspace,
 // the build pipeline on one stream, passes, inspection copies.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -9,6 +10,9 @@
 #include <string>
 #include <vector>
 
+#include <random>
+
+#include "mlp.cuh"
 #include "nl_internal.cuh"
 
 using namespace nlg;
@@ -107,6 +111,8 @@ struct nl_list {
     DevBuf perm_pad, sys_off, sys_pad, sys_box, sys_root, sys_hcap;
     int32_t nsys = 1;
     uint32_t node_cap = 0;
+    const struct nl_mlp *mlp = nullptr;
+    DevBuf ml_X, ml_e64, ml_pred, ml_slo, ml_shi;
     int graph_mode = 0;   // build without host reads or allocations (stream capture)
     Status *hst = nullptr;
 
@@ -155,7 +161,7 @@ struct nl_list {
                          &work, &aux, &status, &hx, &hy, &hz, &hh, &hm, &hrho, &perm_pad,
                          &sys_off, &sys_pad, &sys_box, &sys_root, &sys_hcap, &it_hq,
                          &it_hlo, &it_hhi, &it_hs, &it_counts, &it_conv, &it_aflag, &it_alist,
-                         &it_words, &it_tmp};
+                         &it_words, &it_tmp, &ml_X, &ml_e64, &ml_pred, &ml_slo, &ml_shi};
         for (DevBuf *b : all) b->release();
         for (int i = 0; i <= kStages; ++i)
             if (ev[i]) cudaEventDestroy(ev[i]);
@@ -647,6 +653,226 @@ nl_status nl_density_from_host(nl_list *nl, const float *x, const float *y, cons
     return NL_OK;
 }
 
+}  // extern "C"
+
+struct nl_mlp {
+    DevBuf P, m, v, grad, partial, loss, idx;
+    int64_t step = 0;
+    int slots = 0;
+};
+
+namespace {
+nl_status mlp_slots(nl_mlp *mlp, int slots)
+{
+    if (mlp->slots >= slots) return NL_OK;
+    CK(mlp->partial.ensure((size_t)slots * kMlpParams * 4));
+    CK(mlp->loss.ensure((size_t)slots * 4));
+    mlp->slots = slots;
+    return NL_OK;
+}
+
+nl_status features_of(const nl_list *cnl, cudaStream_t s)
+{
+    nl_list *nl = const_cast<nl_list *>(cnl);
+    CK(nl->ml_X.ensure((size_t)nl->ncl * kMlpF * 4));
+    CK(nl->ml_e64.ensure((size_t)nl->nsc * 4));
+    CK(nl->ml_slo.ensure((size_t)nl->nsc * 16));
+    CK(nl->ml_shi.ensure((size_t)nl->nsc * 16));
+    CK(mlp_features(nl->nsc, nl->p.cluster, nl->tables(), nl->clo.as<float4>(), nl->chi.as<float4>(),
+                    nl->perm_pad.as<uint32_t>(), nl->ml_slo.as<float4>(), nl->ml_shi.as<float4>(),
+                    nl->ml_X.as<float>(), nl->ml_e64.as<float>(), s));
+    return NL_OK;
+}
+
+nl_status learned_start(nl_list *nl, float *hq, cudaStream_t s)
+{
+    nl_status st = features_of(nl, s);
+    if (st != NL_OK) return st;
+    CK(nl->ml_pred.ensure((size_t)nl->ncl * 4));
+    CK(mlp_predict(nl->ncl, nl->ml_X.as<float>(), nl->mlp->P.as<float>(), nl->ml_pred.as<float>(),
+                   nl->num_sms, s));
+    CK(mlp_apply_h0(nl->npad, nl->p.cluster, nl->perm_pad.as<uint32_t>(), nl->ml_pred.as<float>(),
+                    nl->ml_e64.as<float>(), hq, s));
+    return NL_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int64_t nl_mlp_nparams(void) { return kMlpParams; }
+
+nl_status nl_mlp_create(uint64_t seed, nl_mlp **out)
+{
+    if (!out) return fail(NL_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    nl_mlp *mlp = new (std::nothrow) nl_mlp();
+    if (!mlp) return fail(NL_ERR_OOM, "host allocation failed");
+    std::vector<float> P(kMlpParams, 0.f);
+    std::mt19937_64 rng(seed);
+    std::normal_distribution<float> nd(0.f, 1.f);
+    size_t o = 0;
+    const int fan[4] = {kMlpF, kMlpH, kMlpH, kMlpH}, outs[4] = {kMlpH, kMlpH, kMlpH, 1};
+    for (int l = 0; l < 4; ++l) {
+        const float sd = 1.f / std::sqrt((float)fan[l]);
+        for (int k = 0; k < outs[l] * fan[l]; ++k) P[o++] = sd * nd(rng);
+        o += outs[l];  // biases stay zero
+    }
+    cudaError_t e = mlp->P.ensure(kMlpParams * 4);
+    if (e == cudaSuccess) e = mlp->m.ensure(kMlpParams * 4);
+    if (e == cudaSuccess) e = mlp->v.ensure(kMlpParams * 4);
+    if (e == cudaSuccess) e = mlp->grad.ensure(kMlpParams * 4);
+    if (e == cudaSuccess) e = cudaMemcpy(mlp->P.p, P.data(), kMlpParams * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(mlp->m.p, 0, kMlpParams * 4);
+    if (e == cudaSuccess) e = cudaMemset(mlp->v.p, 0, kMlpParams * 4);
+    if (e != cudaSuccess) {
+        delete mlp;
+        return cuda_fail(e, "nl_mlp_create", __LINE__);
+    }
+    *out = mlp;
+    return NL_OK;
+}
+
+nl_status nl_mlp_free(nl_mlp *mlp)
+{
+    if (!mlp) return NL_OK;
+    cudaDeviceSynchronize();
+    DevBuf *all[] = {&mlp->P, &mlp->m, &mlp->v, &mlp->grad, &mlp->partial, &mlp->loss, &mlp->idx};
+    for (DevBuf *b : all) b->release();
+    delete mlp;
+    return NL_OK;
+}
+
+nl_status nl_mlp_get_params(const nl_mlp *mlp, float *params)
+{
+    if (!mlp || !params) return fail(NL_ERR_ARG, "NULL argument");
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(params, mlp->P.p, kMlpParams * 4, cudaMemcpyDeviceToHost));
+    return NL_OK;
+}
+
+nl_status nl_mlp_set_params(nl_mlp *mlp, const float *params)
+{
+    if (!mlp || !params) return fail(NL_ERR_ARG, "NULL argument");
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(mlp->P.p, params, kMlpParams * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemset(mlp->m.p, 0, kMlpParams * 4));
+    CK(cudaMemset(mlp->v.p, 0, kMlpParams * 4));
+    mlp->step = 0;
+    return NL_OK;
+}
+
+nl_status nl_mlp_features(const nl_list *nl, float *X, float *e64, void *stream)
+{
+    nl_status st = check_list(nl);
+    if (st != NL_OK) return st;
+    if (!X || !e64) return fail(NL_ERR_ARG, "NULL output");
+    cudaStream_t s = (cudaStream_t)stream;
+    st = features_of(nl, s);
+    if (st != NL_OK) return st;
+    CK(cudaMemcpyAsync(X, nl->ml_X.p, (size_t)nl->ncl * kMlpF * 4, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(e64, nl->ml_e64.p, (size_t)nl->nsc * 4, cudaMemcpyDeviceToDevice, s));
+    return NL_OK;
+}
+
+nl_status nl_mlp_targets(const nl_list *nl, const float *h, const float *e64, float *y, float *w,
+                         void *stream)
+{
+    nl_status st = check_list(nl);
+    if (st != NL_OK) return st;
+    if (!h || !e64 || !y || !w) return fail(NL_ERR_ARG, "NULL argument");
+    CK(mlp_targets(nl->ncl, nl->p.cluster, nl->perm_pad.as<uint32_t>(), h, e64, y, w,
+                   (cudaStream_t)stream));
+    return NL_OK;
+}
+
+static nl_status mlp_run(nl_mlp *mlp, const float *X, const float *y, const float *w, int64_t n,
+                         const int64_t *idx_dev, int64_t nb, float *grad, int adam, float lr,
+                         float inv_n, float *loss_host, cudaStream_t s)
+{
+    const int slots = (int)std::min<int64_t>((nb + 63) / 64, 4096);
+    nl_status st = mlp_slots(mlp, slots);
+    if (st != NL_OK) return st;
+    if (adam) ++mlp->step;
+    CK(mlp_train_step(nb, idx_dev, X, y, w, mlp->P.as<float>(), mlp->m.as<float>(),
+                      mlp->v.as<float>(), mlp->partial.as<float>(), slots, grad,
+                      mlp->loss.as<float>(), adam, lr, (int)std::max<int64_t>(mlp->step, 1), inv_n, s));
+    if (loss_host) {
+        std::vector<float> l(slots);
+        CK(cudaMemcpyAsync(l.data(), mlp->loss.p, (size_t)slots * 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        double t = 0.0;
+        for (float v : l) t += v;
+        *loss_host = (float)(t * inv_n);
+    }
+    (void)n;
+    return NL_OK;
+}
+
+nl_status nl_mlp_grad(nl_mlp *mlp, const float *X, const float *y, const float *w, int64_t n,
+                      float *grad, float *loss, void *stream)
+{
+    if (!mlp || !X || !y || !w || !grad || n < 1) return fail(NL_ERR_ARG, "bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int64_t> idx(n);
+    for (int64_t k = 0; k < n; ++k) idx[k] = k;
+    CK(mlp->idx.ensure((size_t)n * 8));
+    CK(cudaMemcpyAsync(mlp->idx.p, idx.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
+    nl_status st = mlp_run(mlp, X, y, w, n, mlp->idx.as<int64_t>(), n, grad, 0, 0.f,
+                           1.f / (float)n, loss, s);
+    if (st != NL_OK) return st;
+    CK(cudaStreamSynchronize(s));
+    return NL_OK;
+}
+
+nl_status nl_mlp_train(nl_mlp *mlp, const float *X, const float *y, const float *w, int64_t n,
+                       int32_t epochs, int32_t batch, float lr, uint64_t seed, float *loss,
+                       void *stream)
+{
+    if (!mlp || !X || !y || !w || n < 1 || epochs < 1 || batch < 64 || !(lr > 0.f))
+        return fail(NL_ERR_ARG, "bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int64_t> idx(n);
+    for (int64_t k = 0; k < n; ++k) idx[k] = k;
+    std::mt19937_64 rng(seed);
+    CK(mlp->idx.ensure((size_t)n * 8));
+    float last = 0.f;
+    for (int ep = 0; ep < epochs; ++ep) {
+        std::shuffle(idx.begin(), idx.end(), rng);
+        CK(cudaMemcpyAsync(mlp->idx.p, idx.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
+        double tot = 0.0;
+        for (int64_t b0 = 0; b0 < n; b0 += batch) {
+            const int64_t nb = std::min<int64_t>(batch, n - b0);
+            float lb = 0.f;
+            const bool want = (ep == epochs - 1);
+            nl_status st = mlp_run(mlp, X, y, w, n, mlp->idx.as<int64_t>() + b0, nb, nullptr, 1, lr,
+                                   1.f / (float)nb, want ? &lb : nullptr, s);
+            if (st != NL_OK) return st;
+            tot += (double)lb * nb;
+        }
+        if (ep == epochs - 1) last = (float)(tot / (double)n);
+        CK(cudaStreamSynchronize(s));  // idx is rewritten by the next epoch
+    }
+    if (loss) *loss = last;
+    return NL_OK;
+}
+
+nl_status nl_mlp_predict(const nl_mlp *mlp, const float *X, int64_t n, float *pred, void *stream)
+{
+    if (!mlp || !X || !pred || n < 1) return fail(NL_ERR_ARG, "bad argument");
+    int dev, sms;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(mlp_predict(n, X, mlp->P.as<float>(), pred, sms, (cudaStream_t)stream));
+    return NL_OK;
+}
+
+nl_status nl_set_mlp(nl_list *nl, const nl_mlp *mlp)
+{
+    if (!nl) return fail(NL_ERR_ARG, "list is NULL");
+    nl->mlp = mlp;
+    return NL_OK;
+}
+
 static nl_status do_iterate_h(nl_list *nl, const float *x, const float *y, const float *z,
                               float *h, int64_t n, int32_t nsys, const int64_t *offs,
                               const nl_box *boxes, const nl_params *p, float n_target, float tol,
@@ -657,8 +883,9 @@ static nl_status do_iterate_h(nl_list *nl, const float *x, const float *y, const
     if (!h) return fail(NL_ERR_ARG, "h is NULL");
     if (!(n_target >= 1.f) || !(tol >= 0.f) || max_iter < 1 || !(margin >= 0.f) || !(margin < 4.f))
         return fail(NL_ERR_ARG, "need n_target >= 1, tol >= 0, max_iter >= 1, 0 <= margin < 4");
-    if (start != NL_HSTART_GIVEN && start != NL_HSTART_PLAIN)
+    if (start != NL_HSTART_GIVEN && start != NL_HSTART_PLAIN && start != NL_HSTART_LEARNED)
         return fail(NL_ERR_ARG, "unknown start %d", start);
+    if (start == NL_HSTART_LEARNED && !nl->mlp) return fail(NL_ERR_ARG, "no model attached");
     if (n < 1 || n > (int64_t)1 << 30) return fail(NL_ERR_ARG, "bad n %lld", (long long)n);
     nl->n = 0;
     const uint32_t N = (uint32_t)n;
@@ -687,11 +914,15 @@ static nl_status do_iterate_h(nl_list *nl, const float *x, const float *y, const
                   nl->it_aflag.as<uint32_t>(), nl->it_alist.as<uint32_t>(),
                   nl->it_words.as<unsigned int>(), nl->perm_pad.as<uint32_t>(),
                   nl->sys_hcap.as<float>()};
-    if (start == NL_HSTART_GIVEN)
+    if (start == NL_HSTART_GIVEN) {
         CK(launch_pos_h_to(npad, nl->pos.as<float4>(), hs.hq, s));
-    else
+    } else if (start == NL_HSTART_PLAIN) {
         CK(launch_plain_h0(nsc, M, hs.perm_pad, nl->clo.as<float4>(), nl->chi.as<float4>(),
                            n_target, hs.hq, s));
+    } else {
+        st = learned_start(nl, hs.hq, s);
+        if (st != NL_OK) return st;
+    }
     CK(cudaMemsetAsync(hs.hlo, 0, (size_t)npad * 4, s));
     CK(launch_fill(hs.hhi, npad, INFINITY, s));
     CK(cudaMemsetAsync(hs.conv, 0, (size_t)npad, s));

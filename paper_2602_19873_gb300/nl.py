@@ -77,11 +77,23 @@ _SIGS = {
     "nl_graph_check": (C.c_int, [P, P]),
     "nl_graph_free": (C.c_int, [P]),
     "nl_autotune_batch": (C.c_int, [P, P, P, P, P, C.c_int32, P, P, P, C.c_int32, P, P, P]),
+    "nl_mlp_nparams": (C.c_int64, []),
+    "nl_mlp_create": (C.c_int, [C.c_uint64, P]),
+    "nl_mlp_free": (C.c_int, [P]),
+    "nl_mlp_get_params": (C.c_int, [P, P]),
+    "nl_mlp_set_params": (C.c_int, [P, P]),
+    "nl_mlp_features": (C.c_int, [P, P, P, P]),
+    "nl_mlp_targets": (C.c_int, [P, P, P, P, P, P]),
+    "nl_mlp_grad": (C.c_int, [P, P, P, P, C.c_int64, P, P, P]),
+    "nl_mlp_train": (C.c_int, [P, P, P, P, C.c_int64, C.c_int32, C.c_int32, C.c_float,
+                               C.c_uint64, P, P]),
+    "nl_mlp_predict": (C.c_int, [P, P, C.c_int64, P, P]),
+    "nl_set_mlp": (C.c_int, [P, P]),
     "nl_iterate_h": (C.c_int, [P, P, P, P, P, C.c_int64, P, P, C.c_float, C.c_float, C.c_int32,
                                C.c_float, C.c_int32, P, P, P]),
 }
 
-NL_HSTART_GIVEN, NL_HSTART_PLAIN = 0, 1
+NL_HSTART_GIVEN, NL_HSTART_PLAIN, NL_HSTART_LEARNED = 0, 1, 2
 NL_FORCE_SPH_PRESSURE, NL_FORCE_LJ = 0, 1
 
 
@@ -213,6 +225,50 @@ class Graph:
             self.handle = None
 
 
+class MLP:
+    """nl_mlp: the smoothing-length network (device parameters)."""
+
+    def __init__(self, seed=0):
+        self.handle = C.c_void_p()
+        _check(load().nl_mlp_create(int(seed), C.byref(self.handle)))
+
+    @staticmethod
+    def nparams():
+        return int(load().nl_mlp_nparams())
+
+    def get_params(self):
+        out = np.zeros(self.nparams(), np.float32)
+        _check(load().nl_mlp_get_params(self.handle, out.ctypes.data))
+        return out
+
+    def set_params(self, params):
+        arr = np.ascontiguousarray(params, dtype=np.float32)
+        assert len(arr) == self.nparams()
+        _check(load().nl_mlp_set_params(self.handle, arr.ctypes.data))
+
+    def grad(self, X, y, w, grad_out, stream=None):
+        loss = C.c_float()
+        _check(load().nl_mlp_grad(self.handle, _ptr(X), _ptr(y), _ptr(w), int(y.numel()),
+                                  _ptr(grad_out), C.byref(loss), _stream(stream)))
+        return loss.value
+
+    def train(self, X, y, w, epochs, batch=4096, lr=3e-3, seed=0, stream=None):
+        loss = C.c_float()
+        _check(load().nl_mlp_train(self.handle, _ptr(X), _ptr(y), _ptr(w), int(y.numel()),
+                                   int(epochs), int(batch), float(lr), int(seed), C.byref(loss),
+                                   _stream(stream)))
+        return loss.value
+
+    def predict(self, X, out, stream=None):
+        _check(load().nl_mlp_predict(self.handle, _ptr(X), int(out.numel()), _ptr(out),
+                                     _stream(stream)))
+
+    def free(self):
+        if self.handle:
+            load().nl_mlp_free(self.handle)
+            self.handle = None
+
+
 class NeighborList:
     """Owner of one nl_list handle.  Positions x, y, z and smoothing lengths h
     are float32 CUDA tensors in caller order."""
@@ -312,6 +368,28 @@ class NeighborList:
         if st != NL_OK and (check or st != 6):
             _check(st)
         return out
+
+    def set_mlp(self, mlp):
+        self.ensure_handle()
+        _check(load().nl_set_mlp(self.handle, mlp.handle if mlp is not None else None))
+
+    def mlp_features(self, stream=None):
+        """(X [n_clusters x 8], e64 [n_superclusters]) CUDA tensors of this list."""
+        import torch
+        s = self.sizes()
+        X = torch.empty((s["n_clusters"], 8), dtype=torch.float32, device="cuda")
+        e64 = torch.empty(s["n_superclusters"], dtype=torch.float32, device="cuda")
+        _check(load().nl_mlp_features(self.handle, _ptr(X), _ptr(e64), _stream(stream)))
+        return X, e64
+
+    def mlp_targets(self, h, e64, stream=None):
+        import torch
+        nc = self.sizes()["n_clusters"]
+        y = torch.empty(nc, dtype=torch.float32, device="cuda")
+        w = torch.empty(nc, dtype=torch.float32, device="cuda")
+        _check(load().nl_mlp_targets(self.handle, _ptr(h), _ptr(e64), _ptr(y), _ptr(w),
+                                     _stream(stream)))
+        return y, w
 
     def density_pass(self, m, rho, stream=None):
         _check(load().nl_density_pass(self.handle, _ptr(m), _ptr(rho), _stream(stream)))
