@@ -105,9 +105,9 @@ def workload(seed, n=N_FULL):
 
 
 def converge_h(L, dev, d, params, start, stream):
-    """Exact h iteration to 200 +- 2 neighbors; returns (h tensor, info, ms)."""
+    """Exact h iteration to 200 +- 2 neighbors; returns (h tensor, info, ms).
+    The learned start runs its feature and MLP kernels inside the timing."""
     import torch
-    from paper_2602_19873_gb300 import nl
     h = dev["h"].clone()
     torch.cuda.synchronize()
     t = time.perf_counter()
@@ -115,6 +115,47 @@ def converge_h(L, dev, d, params, start, stream):
                        max_iter=60, margin=0.15, start=start, stream=stream)
     torch.cuda.synchronize()
     return h, info, (time.perf_counter() - t) * 1e3
+
+
+TRAIN_SEEDS = list(range(100, 108))
+TRAIN_N = 1 << 19
+
+
+def train_mlp(params, stream, reuse):
+    """Train the smoothing-length MLP on the GPU: 8 systems of the benchmark
+    generator (2^19 particles, seeds 100..107), h from the exact iteration,
+    per-cluster features and targets from the list kernels, Adam."""
+    import torch
+    from paper_2602_19873_gb300 import nl
+    cache = os.path.join(__import__("tempfile").gettempdir(), "nlgb_workloads",
+                         "mlp_%d_%d.npy" % (TRAIN_N, len(TRAIN_SEEDS)))
+    mlp = nl.MLP(seed=0)
+    if reuse and os.path.exists(cache):
+        mlp.set_params(np.load(cache))
+        return mlp, {"cached": True}
+    t0 = time.perf_counter()
+    Xs, ys, ws = [], [], []
+    for seed in TRAIN_SEEDS:
+        d = workload(seed, TRAIN_N)
+        dev = {k: torch.from_numpy(d[k]).cuda() for k in ("x", "y", "z", "h")}
+        L = nl.NeighborList()
+        h = dev["h"].clone()
+        L.iterate_h(dev["x"], dev["y"], dev["z"], h, d["box"], params, 200.0, 2.0, max_iter=60,
+                    start=nl.NL_HSTART_PLAIN, stream=stream)
+        X, e64 = L.mlp_features(stream)
+        y, w = L.mlp_targets(h, e64, stream)
+        Xs.append(X), ys.append(y), ws.append(w)
+        L.free()
+    X, y, w = torch.cat(Xs), torch.cat(ys), torch.cat(ws)
+    t1 = time.perf_counter()
+    loss = mlp.train(X, y, w, epochs=40, batch=8192, lr=3e-3, seed=1, stream=stream)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    np.save(cache, mlp.get_params())
+    return mlp, {"samples": int(y.numel()), "epochs": 40, "final_loss": loss,
+                 "data_ms": (t1 - t0) * 1e3, "train_ms": (t2 - t1) * 1e3,
+                 "systems": "%d x %d particles, seeds %d..%d" % (len(TRAIN_SEEDS), TRAIN_N,
+                                                                 TRAIN_SEEDS[0], TRAIN_SEEDS[-1])}
 
 
 def run_native(args):
@@ -138,6 +179,7 @@ def run_native(args):
     H = nl.NeighborList()
     hcache = os.path.join(__import__("tempfile").gettempdir(), "nlgb_workloads",
                           "hconv_%d_%d.npy" % (n, 4 + rank))
+    learned = None
     if args.reuse_h and os.path.exists(hcache):
         hconv = torch.from_numpy(np.load(hcache)).cuda()
         hinfo, hms = {"iterations": None, "rebuilds": None, "unconverged": None}, None
@@ -145,6 +187,16 @@ def run_native(args):
         converge_h(H, dev, d, params, nl.NL_HSTART_PLAIN, stream)       # warm-up
         hconv, hinfo, hms = converge_h(H, dev, d, params, nl.NL_HSTART_PLAIN, stream)
         np.save(hcache, hconv.cpu().numpy())
+        if not args.no_learned:
+            mlp, tinfo = train_mlp(params, stream, args.reuse_h)
+            H.set_mlp(mlp)
+            converge_h(H, dev, d, params, nl.NL_HSTART_LEARNED, stream)  # warm-up
+            hl, linfo, lms = converge_h(H, dev, d, params, nl.NL_HSTART_LEARNED, stream)
+            learned = {"ms": lms, "iterations": linfo["iterations"], "rebuilds": linfo["rebuilds"],
+                       "unconverged": linfo["unconverged"], "training": tinfo,
+                       "speedup_vs_plain": hms / lms}
+            H.set_mlp(None)
+            mlp.free()
     H.free()
     dev["h"] = hconv
     d["h"] = hconv.cpu().numpy()
@@ -243,7 +295,11 @@ def run_native(args):
             "h2d_bytes_per_step": 20 * n, "d2h_bytes_per_step": 4 * n},
         "h_iteration": {"plain": {"ms": hms, "iterations": hinfo["iterations"],
                                   "rebuilds": hinfo["rebuilds"],
-                                  "unconverged": hinfo["unconverged"]}},
+                                  "unconverged": hinfo["unconverged"]},
+                        "learned": learned,
+                        "end_to_end_ms": None if hms is None else {
+                            "plain": hms + ms,
+                            "learned": None if learned is None else learned["ms"] + ms}},
         "gpu_launches": None,
         "clocks": clk,
     }
@@ -415,6 +471,7 @@ def main():
     ap.add_argument("--reuse-h", action="store_true",
                     help="reuse converged h cached by an earlier run with the same n")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-h comparison")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched_256"])
     args = ap.parse_args()
     if args.impl == "reference":
