@@ -82,7 +82,7 @@ def lib():
                 "orc_brute_neighbors": (P, [I64, P, P, P, P, P, F32, C.c_int, I64, P]),
                 "orc_gather_all": (P, [I64, P, P, P, P, P, F32]),
                 "orc_symmetrize": (P, [P]),
-                "orc_cluster_lists": (P, [I64, C.c_int, P, P, I64, P]),
+                "orc_cluster_lists": (P, [I64, C.c_int, C.c_int, P, P, I64, P]),
                 "orc_clist_nnz": (I64, [P]),
                 "orc_clist_copy": (None, [P, P, P, P]),
                 "orc_clist_free": (None, [P]),
@@ -232,15 +232,17 @@ def symmetrize(off, idx):
     return _csr_take(s)
 
 
-def cluster_lists(n, cluster, off, idx, rows, sc_ids):
+def cluster_lists(n, cluster, off, idx, rows, sc_ids, jcluster=None):
     """Canonical (J, mask) lists of the super-clusters sc_ids from the
-    symmetric sets (off, idx) of the particles rows."""
+    symmetric sets (off, idx) of the particles rows; J counts j-clusters of
+    `jcluster` particles (default: the i-cluster size)."""
     h, keep = _csr_make(off, idx)
     rows = _i64(rows)
     sc = _i64(sc_ids)
     L = lib()
+    jc = cluster if jcluster is None else jcluster
     try:
-        c = L.orc_cluster_lists(int(n), int(cluster), h, _p(rows), len(sc), _p(sc))
+        c = L.orc_cluster_lists(int(n), int(cluster), int(jc), h, _p(rows), len(sc), _p(sc))
     finally:
         L.orc_csr_free(h)
     nnz = L.orc_clist_nnz(c)

@@ -677,12 +677,14 @@ static int cmp_jbit(const void *a, const void *b)
 }
 
 /* P: symmetric neighbor sets of the rows listed in `rows` (rows[k] = sorted
- * particle index of CSR row k), over particles [0,n).  The super-clusters
+ * particle index of CSR row k), over particles [0,n).  i-clusters hold
+ * `cluster` particles (8 per super-cluster, one mask bit each), j-clusters
+ * `jcluster` particles (the unit of the stored indices).  The super-clusters
  * built are those whose particles all appear in rows (rows covering whole
  * super-clusters, e.g. all of [0,n)).  sc_ids[t] = super-cluster index of the
  * t-th output record, in ascending order. */
-orc_clist *orc_cluster_lists(int64_t n, int cluster, const orc_csr *P, const int64_t *rows,
-                             int64_t nsc_out, const int64_t *sc_ids)
+orc_clist *orc_cluster_lists(int64_t n, int cluster, int jcluster, const orc_csr *P,
+                             const int64_t *rows, int64_t nsc_out, const int64_t *sc_ids)
 {
     const int64_t sp = (int64_t)cluster * 8;
     orc_clist *c = (orc_clist *)calloc(1, sizeof(orc_clist));
@@ -709,7 +711,7 @@ orc_clist *orc_cluster_lists(int64_t n, int cluster, const orc_csr *P, const int
             int64_t r = rowof[i];
             if (r < 0) continue;
             for (int64_t q = P->off[r]; q < P->off[r + 1]; ++q) {
-                v[m].J = (int32_t)(P->idx[q] / cluster);
+                v[m].J = (int32_t)(P->idx[q] / jcluster);
                 v[m].bit = (int32_t)((i - a) / cluster);
                 ++m;
             }

@@ -155,3 +155,25 @@ def test_self_tile_and_isolated_particle(orc):
     assert g_idx.tolist() == [1, 0]
     o, J, m = orc.cluster_lists(4, 4, g_off, g_idx, np.arange(4), np.arange(1))
     assert J.tolist() == [0] and m.tolist() == [1]
+
+
+@pytest.mark.parametrize("M,MJ", [(8, 4), (16, 8)])
+def test_cluster_lists_with_half_j_clusters(orc, M, MJ):
+    """j-clusters of half the i-cluster size: J counts j-clusters, masks
+    still mark the 8 i-clusters of the super-cluster."""
+    d = _small("evrard", 1500)
+    xs, ys, zs, hs, ms = _sorted(orc, d)
+    refs = _brute_numpy(xs, ys, zs, hs, d["box"], 2.0, 1)
+    g_off, g_idx = orc.gather_all(xs, ys, zs, hs, d["box"], 2.0)
+    p_off, p_idx = orc.symmetrize(g_off, g_idx)
+    n = len(xs)
+    nsc = (n + 8 * M - 1) // (8 * M)
+    o, J, m = orc.cluster_lists(n, M, p_off, p_idx, np.arange(n), np.arange(nsc), jcluster=MJ)
+    for s in range(nsc):
+        want = {}
+        for i in range(s * 8 * M, min(n, (s + 1) * 8 * M)):
+            for j in refs[i]:
+                want[j // MJ] = want.get(j // MJ, 0) | (1 << ((i - s * 8 * M) // M))
+        Js = sorted(want)
+        assert J[o[s]:o[s + 1]].tolist() == Js
+        assert m[o[s]:o[s + 1]].tolist() == [want[x] for x in Js]
