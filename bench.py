@@ -170,8 +170,9 @@ def run_native(args):
     d = workload(4 + rank, args.n)
     n = len(d["x"])
     dev = {k: torch.from_numpy(d[k]).cuda() for k in ("x", "y", "z", "h", "m")}
-    params = nl.make_params(key=d["kind"], cluster=8, support=d["support"], compress=1,
-                            leaf_bucket=64)
+    M, MJ = (int(v) for v in args.tile.split("x"))
+    params = nl.make_params(key=d["kind"], cluster=M, support=d["support"], compress=1,
+                            leaf_bucket=64, j_cluster=MJ)
     L = nl.NeighborList()
     stream = torch.cuda.current_stream()
     # smoothing lengths at 200 +- 2 neighbors from the plain start (untimed
@@ -258,7 +259,7 @@ def run_native(args):
     hbm, hbm_kind, sm_max = peaks()
     alu_peak = 152 * 128 * sm_max * 1e6 / 1e12  # FP32 instructions per second, Tops
     search_ms = stages.get("search", float("nan"))
-    pairs = sizes["n_tiles"] * params.cluster * params.cluster
+    pairs = sizes["n_tiles"] * params.cluster * sizes["j_cluster"]
     achieved = pairs * ALU_OPS_PER_PAIR_SEARCH / (search_ms * 1e-3) / 1e12
     step_bytes = ALGO_BYTES_PER_PARTICLE * n
     out = {
@@ -267,9 +268,10 @@ def run_native(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": "%s: 2^24 particles in 64 Plummer spheres (scale radii "
-                               "log-uniform 1e-3..1e-1), Hilbert keys, 8x8 clusters, "
-                               "compressed list" % WORKLOAD,
-                   "n": n, "cluster": params.cluster, "leaf_bucket": params.leaf_bucket,
+                               "log-uniform 1e-3..1e-1), Hilbert keys, %dx%d clusters, "
+                               "compressed list" % (WORKLOAD, M, MJ),
+                   "n": n, "cluster": params.cluster, "j_cluster": sizes["j_cluster"],
+                   "leaf_bucket": params.leaf_bucket,
                    "h": "iterated on the GPU to 200 +- 2 gather neighbors (plain start)",
                    "l2": "inputs larger than L2 (268 MB of positions), no flush",
                    "parallelism": "replicas" if ws > 1 else "single"},
@@ -389,7 +391,7 @@ def run_batched(args):
                                                                          "unconverged")}}},
            "autotune_best_ms": tune_ms,
            "list": {"bytes_per_particle": sizes["list_bytes"] / n, "entries": sizes["n_entries"],
-                    "computed_pairs": sizes["n_tiles"] * best.cluster ** 2},
+                    "computed_pairs": sizes["n_tiles"] * best.cluster * sizes["j_cluster"]},
            "per_system_max_rel_density_err": worst,
            "per_system_error_sample": [int(len(systems[k]["x"])) for k in sample],
            "gpu_launches": args.steps * (1 + 3 * 9 + 1 + 10 + 1 + 2), "clocks": clk}
@@ -471,6 +473,8 @@ def main():
     ap.add_argument("--reuse-h", action="store_true",
                     help="reuse converged h cached by an earlier run with the same n")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tile", default="8x8", choices=["8x8", "8x4", "16x8", "16x16", "4x4"],
+                    help="i-cluster x j-cluster size of the single-system bench")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-h comparison")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched_256"])
     args = ap.parse_args()

@@ -67,15 +67,18 @@ typedef struct {
 /* Build options (Sec. II-D: cluster and super-cluster sizes, compression). */
 typedef struct {
     int32_t key;          /* NL_KEY_MORTON or NL_KEY_HILBERT (63-bit keys, 21 bits/axis) */
-    int32_t cluster;      /* particles per cluster M: 4, 8 or 16; super-cluster = 8 clusters */
+    int32_t cluster;      /* particles per i-cluster M: 4, 8 or 16; super-cluster = 8 i-clusters */
     float support;        /* interaction radius r_i = support * h_i (2 for the cubic spline) */
     int32_t compress;     /* 1: nibble codec (Sec. II-B); 0: raw u32 cluster indices */
     int32_t leaf_bucket;  /* octree leaf capacity B in particles, 8..1024 (default 64) */
     int32_t threads_per_block; /* search / pass block shape: 128 or 256 threads (0 = 256) */
     int32_t blocks_per_sm;     /* persistent grids: blocks per SM, 1..8 (0 = 3 search, 4 pass) */
+    int32_t j_cluster;    /* particles per j-cluster MJ: 0 (= M), M, or M / 2 when M >= 8;
+                             the M x MJ tiles of Sec. II-A / III-A (8 x 4 is the paper's
+                             NVIDIA choice).  Stored list indices count j-clusters. */
 } nl_params;
 
-/* Fills p with {NL_KEY_HILBERT, 8, 2.0f, 1, 64, 0, 0}. */
+/* Fills p with {NL_KEY_HILBERT, 8, 2.0f, 1, 64, 0, 0, 0}. */
 void nl_default_params(nl_params *p);
 
 typedef struct nl_list nl_list; /* opaque; owns all of its device memory */
@@ -97,6 +100,8 @@ typedef struct {
     int64_t leaf_visits;     /* leaves reached */
     int64_t j_examined;      /* j-clusters box-tested against a super-cluster */
     int64_t tile_tests;      /* (i-cluster, j-cluster) tiles decided by the exact predicate */
+    int32_t j_cluster;       /* MJ */
+    int32_t pad0;
 } nl_sizes;
 
 /* Builds a new list (Sec. II-A, Listing "build"): keys, sort, clusters,
@@ -284,7 +289,7 @@ nl_status nl_graph_check(nl_graph *g, void *stream);
 nl_status nl_graph_free(nl_graph *g);
 
 /* Autotuner: times build + density of the given batch for every candidate
- * cluster size M in {4, 8, 16}, block shape in {128, 256} threads and
+ * tile shape M x MJ in {4x4, 8x8, 8x4, 16x16, 16x8}, block shape in {128, 256} threads and
  * persistent-grid occupancy in {2, 3, 4} blocks per SM (reps timed runs
  * each after one warm-up, CUDA events on `stream`) and writes the fastest
  * parameters (other fields copied from *base) to *best and its mean time

@@ -104,8 +104,8 @@ struct nl_list {
     uint32_t stage_cap = kStageCap0;
     int stage_grown = 0;
     int64_t n_prepared = 0;
-    DevBuf keys, keys_alt, vals, vals_alt, hist, pos, clo, chi, lcp, lev, leaf_first, leaf_lev,
-        nodeoff, bsum;
+    DevBuf keys, keys_alt, vals, vals_alt, hist, pos, clo, chi, jlo, jhi, lcp, lev, leaf_first,
+        leaf_lev, nodeoff, bsum;
     DevBuf nlo, nhi, nrng, nlevel, nparent, nchild, narrive;
     DevBuf stageJ, stageM, list, rec_off, redo, work, aux, status;
     DevBuf perm_pad, sys_off, sys_pad, sys_box, sys_root, sys_hcap;
@@ -155,7 +155,8 @@ struct nl_list {
 
     void release_all()
     {
-        DevBuf *all[] = {&keys, &keys_alt, &vals, &vals_alt, &hist, &pos, &clo, &chi, &lcp, &lev,
+        DevBuf *all[] = {&keys, &keys_alt, &vals, &vals_alt, &hist, &pos, &clo, &chi, &jlo, &jhi,
+                         &lcp, &lev,
                          &leaf_first, &leaf_lev, &nodeoff, &bsum, &nlo, &nhi, &nrng, &nlevel,
                          &nparent, &nchild, &narrive, &stageJ, &stageM, &list, &rec_off, &redo,
                          &work, &aux, &status, &hx, &hy, &hz, &hh, &hm, &hrho, &perm_pad,
@@ -172,6 +173,9 @@ struct nl_list {
 
 namespace {
 
+// j-cluster size MJ (0 in the parameters means MJ = M)
+inline int jcl(const nl_params *p) { return p->j_cluster ? p->j_cluster : p->cluster; }
+
 nl_status check_params(const nl_params *p, const nl_box *box)
 {
     if (!p || !box) return fail(NL_ERR_ARG, "params or box is NULL");
@@ -179,6 +183,10 @@ nl_status check_params(const nl_params *p, const nl_box *box)
         return fail(NL_ERR_ARG, "unknown key kind %d", p->key);
     if (p->cluster != 4 && p->cluster != 8 && p->cluster != 16)
         return fail(NL_ERR_ARG, "cluster size must be 4, 8 or 16 (got %d)", p->cluster);
+    if (p->j_cluster != 0 && p->j_cluster != p->cluster &&
+        !(p->cluster >= 8 && p->j_cluster * 2 == p->cluster))
+        return fail(NL_ERR_ARG, "j_cluster must be 0, cluster or cluster / 2 >= 4 (got %d for cluster %d)",
+                    p->j_cluster, p->cluster);
     if (!(p->support > 0.f) || !std::isfinite(p->support))
         return fail(NL_ERR_ARG, "support must be finite and > 0");
     if (p->compress != 0 && p->compress != 1) return fail(NL_ERR_ARG, "compress must be 0 or 1");
@@ -274,6 +282,7 @@ nl_status do_prep(nl_list *nl, const float *x, const float *y, const float *z, c
         }
         hcap[k] = cap;
     }
+    const int MJ = jcl(p);
     const uint32_t npad = pad[nsys], ncl = npad / M, nsc = npad / scp;
     nl->p = *p;
     nl->box = boxes[0];
@@ -290,6 +299,10 @@ nl_status do_prep(nl_list *nl, const float *x, const float *y, const float *z, c
     CK(nl->perm_pad.ensure((size_t)npad * 4));
     CK(nl->clo.ensure((size_t)ncl * 16));
     CK(nl->chi.ensure((size_t)ncl * 16));
+    if (MJ != M) {
+        CK(nl->jlo.ensure((size_t)(npad / MJ) * 16));
+        CK(nl->jhi.ensure((size_t)(npad / MJ) * 16));
+    }
     CK(nl->lcp.ensure((size_t)N));
     CK(nl->lev.ensure((size_t)N));
     CK(nl->leaf_first.ensure((size_t)(N + 1) * 4));
@@ -327,9 +340,9 @@ nl_status do_prep(nl_list *nl, const float *x, const float *y, const float *z, c
                             nl->keys_alt.as<uint64_t>(), nl->vals_alt.as<uint32_t>(), N,
                             nl->sys_off.as<uint32_t>(), (uint32_t)nsys, nl->hist.as<uint32_t>(), s));
     CK(nl->mark(2, s));
-    CK(launch_permute(npad, M, T, nl->vals.as<uint32_t>(), x, y, z, h, p->support,
+    CK(launch_permute(npad, M, MJ, T, nl->vals.as<uint32_t>(), x, y, z, h, p->support,
                       nl->pos.as<float4>(), nl->perm_pad.as<uint32_t>(), nl->clo.as<float4>(),
-                      nl->chi.as<float4>(), s));
+                      nl->chi.as<float4>(), nl->jlo.as<float4>(), nl->jhi.as<float4>(), s));
     // 4. octree
     CK(nl->mark(3, s));
     CK(octree_leaves(nl->keys.as<uint64_t>(), N, p->leaf_bucket, T, nl->lcp.as<uint8_t>(),
@@ -409,6 +422,9 @@ nl_status do_search(nl_list *nl, cudaStream_t s)
     sa.pos = nl->pos.as<float4>();
     sa.clo = nl->clo.as<float4>();
     sa.chi = nl->chi.as<float4>();
+    sa.mj = jcl(p);
+    sa.jlo = sa.mj == M ? sa.clo : nl->jlo.as<float4>();
+    sa.jhi = sa.mj == M ? sa.chi : nl->jhi.as<float4>();
     sa.nlo = nl->nlo.as<float4>();
     sa.nhi = nl->nhi.as<float4>();
     sa.nrng = nl->nrng.as<int2>();
@@ -516,6 +532,7 @@ PassArgs pass_args(const nl_list *nl)
     a.sys = nl->tables();
     a.support = nl->p.support;
     a.compress = nl->p.compress;
+    a.mj = jcl(&nl->p);
     a.st = nl->status.as<Status>();
     return a;
 }
@@ -534,6 +551,7 @@ void nl_default_params(nl_params *p)
     p->leaf_bucket = 64;
     p->threads_per_block = 0;
     p->blocks_per_sm = 0;
+    p->j_cluster = 0;
 }
 
 const char *nl_last_error(void) { return g_err.c_str(); }
@@ -935,8 +953,9 @@ static nl_status do_iterate_h(nl_list *nl, const float *x, const float *y, const
         if (rebuild) {
             CK(launch_hsearch(npad, hs.hq, margin, hs.hcap_sys, T, hs.hs, s));
             CK(launch_pos_h(npad, hs.hs, nl->pos.as<float4>(), s));
-            CK(launch_cluster_boxes(npad, M, nl->pos.as<float4>(), p->support,
-                                    nl->clo.as<float4>(), nl->chi.as<float4>(), s));
+            CK(launch_cluster_boxes(npad, M, jcl(p), nl->pos.as<float4>(), p->support,
+                                    nl->clo.as<float4>(), nl->chi.as<float4>(),
+                                    nl->jlo.as<float4>(), nl->jhi.as<float4>(), s));
             CK(octree_boxes(nl->node_cap, nl->pos.as<float4>(), p->support, oo,
                             nl->status.as<Status>(), s));
             st = do_search(nl, s);
@@ -1128,15 +1147,18 @@ nl_status nl_autotune_batch(const float *x, const float *y, const float *z, cons
     CK(cudaEventCreate(&e1));
     nl_list *nl = new (std::nothrow) nl_list();
     if (!nl) return fail(NL_ERR_OOM, "host allocation failed");
-    const int Ms[3] = {4, 8, 16}, T[2] = {128, 256}, B[3] = {2, 3, 4};
+    // tile shapes M x MJ
+    const int Ms[5] = {4, 8, 8, 16, 16}, MJs[5] = {4, 8, 4, 16, 8};
+    const int T[2] = {128, 256}, B[3] = {2, 3, 4};
     float bms = INFINITY;
     nl_params bp = *base;
     nl_status st = NL_OK;
-    for (int mi = 0; mi < 3 && st == NL_OK; ++mi)
+    for (int mi = 0; mi < 5 && st == NL_OK; ++mi)
         for (int ti = 0; ti < 2 && st == NL_OK; ++ti)
             for (int bi = 0; bi < 3 && st == NL_OK; ++bi) {
                 nl_params c = *base;
                 c.cluster = Ms[mi];
+                c.j_cluster = MJs[mi];
                 c.threads_per_block = T[ti];
                 c.blocks_per_sm = B[bi];
                 float tot = 0.f;
@@ -1265,6 +1287,7 @@ nl_status nl_get_sizes(const nl_list *nl, nl_sizes *out)
     out->list_bytes = (int64_t)nl->list_bytes;
     out->cluster = nl->p.cluster;
     out->compress = nl->p.compress;
+    out->j_cluster = jcl(&nl->p);
     out->node_visits = (int64_t)nl->node_visits;
     out->leaf_visits = (int64_t)nl->leaf_visits;
     out->j_examined = (int64_t)nl->j_examined;

@@ -54,41 +54,29 @@ cudaError_t launch_pos_h_to(uint32_t npad, const float4 *pos, float *hq, cudaStr
 template <int M>
 __global__ void __launch_bounds__(256) k_cluster_boxes(uint32_t npad, const float4 *__restrict__ pos,
                                                        float support, float4 *__restrict__ clo,
-                                                       float4 *__restrict__ chi)
+                                                       float4 *__restrict__ chi, int MJ,
+                                                       float4 *__restrict__ jlo,
+                                                       float4 *__restrict__ jhi)
 {
     uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;  // npad is a multiple of 32
     if (k >= npad) return;
     float4 p = pos[k];
     bool real = p.x == p.x;
     float r = real ? __fmul_rn(support, p.w) : 0.f;
-    float lx = real ? p.x : INFINITY, ly = real ? p.y : INFINITY, lz = real ? p.z : INFINITY;
-    float hx = real ? p.x : -INFINITY, hy = real ? p.y : -INFINITY, hz = real ? p.z : -INFINITY;
-    float rmin = real ? r : INFINITY;
-#pragma unroll
-    for (int o = 1; o < M; o <<= 1) {
-        rmin = fminf(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
-        lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
-        ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
-        lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
-        hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
-        hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
-        hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
-        r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
-    }
-    if ((k & (M - 1)) == 0) {
-        clo[k / M] = make_float4(lx, ly, lz, r);
-        chi[k / M] = make_float4(hx, hy, hz, rmin);
-    }
+    cluster_box_reduce<M>(k, real, p, r, MJ, clo, chi, jlo, jhi);
 }
 
-cudaError_t launch_cluster_boxes(uint32_t npad, int M, const float4 *pos, float support,
-                                 float4 *clo, float4 *chi, cudaStream_t s)
+cudaError_t launch_cluster_boxes(uint32_t npad, int M, int MJ, const float4 *pos, float support,
+                                 float4 *clo, float4 *chi, float4 *jlo, float4 *jhi,
+                                 cudaStream_t s)
 {
     unsigned grid = (npad + 255) / 256;
+    if (MJ == M) jlo = jhi = nullptr;
+    else if (!jlo || !jhi || MJ < 1 || M % MJ) return cudaErrorInvalidValue;
     switch (M) {
-    case 4: k_cluster_boxes<4><<<grid, 256, 0, s>>>(npad, pos, support, clo, chi); break;
-    case 8: k_cluster_boxes<8><<<grid, 256, 0, s>>>(npad, pos, support, clo, chi); break;
-    case 16: k_cluster_boxes<16><<<grid, 256, 0, s>>>(npad, pos, support, clo, chi); break;
+    case 4: k_cluster_boxes<4><<<grid, 256, 0, s>>>(npad, pos, support, clo, chi, MJ, jlo, jhi); break;
+    case 8: k_cluster_boxes<8><<<grid, 256, 0, s>>>(npad, pos, support, clo, chi, MJ, jlo, jhi); break;
+    case 16: k_cluster_boxes<16><<<grid, 256, 0, s>>>(npad, pos, support, clo, chi, MJ, jlo, jhi); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

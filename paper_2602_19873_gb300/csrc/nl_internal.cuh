@@ -364,13 +364,50 @@ cudaError_t radix_sort_by_system(uint64_t *keys, uint32_t *vals, uint64_t *keys_
                                  uint32_t *vals_alt, uint32_t n, const uint32_t *sys_off,
                                  uint32_t nsys, uint32_t *hist, cudaStream_t s);
 
+// Boxes of the aligned groups of M consecutive lanes (one particle per lane,
+// M | 32, whole warps present): lo = (min xyz, max r), hi = (max xyz, min r),
+// empty boxes for all-dummy groups (real == false everywhere).  With
+// jlo != NULL the boxes of the aligned sub-groups of MJ < M lanes (the
+// j-clusters) are written too.
+template <int M>
+__device__ __forceinline__ void cluster_box_reduce(uint32_t k, bool real, float4 p, float r,
+                                                   int MJ, float4 *clo, float4 *chi,
+                                                   float4 *jlo, float4 *jhi)
+{
+    float lx = real ? p.x : INFINITY, ly = real ? p.y : INFINITY, lz = real ? p.z : INFINITY;
+    float hx = real ? p.x : -INFINITY, hy = real ? p.y : -INFINITY, hz = real ? p.z : -INFINITY;
+    float rmin = real ? r : INFINITY;
+    if (!real) r = 0.f;
+#pragma unroll
+    for (int o = 1; o < M; o <<= 1) {
+        if (jlo && o == MJ && (k & (uint32_t)(MJ - 1)) == 0) {
+            jlo[k / MJ] = make_float4(lx, ly, lz, r);
+            jhi[k / MJ] = make_float4(hx, hy, hz, rmin);
+        }
+        rmin = fminf(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+        lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+        ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+        lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+        hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
+        hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
+        hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
+        r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+    }
+    if ((k & (uint32_t)(M - 1)) == 0) {
+        clo[k / M] = make_float4(lx, ly, lz, r);
+        chi[k / M] = make_float4(hx, hy, hz, rmin);
+    }
+}
+
 // Permute into padded SFC order as float4 (x, y, z, h) with NaN dummies,
 // record the caller index of every padded slot (perm_pad, ~0 for dummies),
-// and per-cluster boxes: clo = (lo, max r), chi = (hi, min r).
-cudaError_t launch_permute(uint32_t npad, int M, const SysTables &t, const uint32_t *perm,
+// and per-cluster boxes: clo = (lo, max r), chi = (hi, min r) per i-cluster
+// of M particles, jlo / jhi the same per j-cluster of MJ < M particles
+// (NULL when MJ == M: the i-cluster boxes serve both).
+cudaError_t launch_permute(uint32_t npad, int M, int MJ, const SysTables &t, const uint32_t *perm,
                            const float *x, const float *y, const float *z, const float *h,
                            float support, float4 *pos, uint32_t *perm_pad, float4 *clo,
-                           float4 *chi, cudaStream_t s);
+                           float4 *chi, float4 *jlo, float4 *jhi, cudaStream_t s);
 
 // Octree, steps 1-2: leaf level per particle, leaf starts; n_leaves lands
 // in st->n_leaves.  Scratch: lev (n bytes), bsum (scan_bsum_words(n)).
@@ -402,7 +439,9 @@ cudaError_t octree_emit(const uint64_t *keys, uint32_t n, uint32_t node_cap, con
 
 struct SearchArgs {
     const float4 *pos;
-    const float4 *clo, *chi;
+    const float4 *clo, *chi;   // i-cluster boxes (M particles)
+    const float4 *jlo, *jhi;   // j-cluster boxes (MJ particles; == clo, chi when MJ == M)
+    int mj;                    // j-cluster size MJ
     const float4 *nlo, *nhi;
     const int2 *nrng;
     uint32_t n, nsc, nnodes;
@@ -432,6 +471,7 @@ struct PassArgs {
     SysTables sys;
     float support;
     int compress;
+    int mj;                // j-cluster size MJ (units of the stored indices)
     float p0, p1;          // LJ: eps, sigma
     float *out0, *out1, *out2;
     uint32_t *outc;
@@ -457,8 +497,9 @@ cudaError_t octree_boxes(uint32_t node_cap, const float4 *pos, float support, co
 cudaError_t launch_fill(float *a, uint32_t n, float v, cudaStream_t s);
 cudaError_t launch_pos_h(uint32_t npad, const float *hs, float4 *pos, cudaStream_t s);
 cudaError_t launch_pos_h_to(uint32_t npad, const float4 *pos, float *hq, cudaStream_t s);
-cudaError_t launch_cluster_boxes(uint32_t npad, int M, const float4 *pos, float support,
-                                 float4 *clo, float4 *chi, cudaStream_t s);
+cudaError_t launch_cluster_boxes(uint32_t npad, int M, int MJ, const float4 *pos, float support,
+                                 float4 *clo, float4 *chi, float4 *jlo, float4 *jhi,
+                                 cudaStream_t s);
 cudaError_t launch_plain_h0(uint32_t nsc, int M, const uint32_t *perm_pad, const float4 *clo,
                             const float4 *chi, float n_target, float *hq, cudaStream_t s);
 cudaError_t launch_hsearch(uint32_t npad, const float *hq, float margin, const float *hcap_sys,

@@ -8,8 +8,9 @@
 // popcount and its data nibbles by a warp scan of data lengths, and a warp
 // scan of the differences rebuilds the j-cluster indices.  For every decoded
 // (J, mask) entry the lanes hold one i particle of each of the 8 i-clusters
-// (lane % M) and 1..8 j particles of J, and accumulate per i-cluster in
-// registers; masked-off i-clusters cost nothing (warp-uniform branches).
+// (lane % M) and 1..8 of the MJ particles of j-cluster J, and accumulate per
+// i-cluster in registers; masked-off i-clusters cost nothing (warp-uniform
+// branches).  The j particles of 32 entries are staged in shared memory.
 // The self pair is excluded on the fly by index (Sec. II-A).
 #pragma once
 #include "nl_internal.cuh"
@@ -90,27 +91,27 @@ __device__ __forceinline__ void acc_end_block(Acc<KIND> &acc)
 
 // Shared memory per warp: the j particles (and pass inputs) of one block
 // of 32 list entries, loaded in bulk before the block is computed.
-template <int M, int KIND>
+template <int MJ, int KIND>
 constexpr size_t pass_smem_per_warp()
 {
-    return (size_t)32 * M * (sizeof(float4) + ((KIND == PASS_DENSITY || KIND == PASS_SPH) ? sizeof(float2) : 0));
+    return (size_t)32 * MJ * (sizeof(float4) + ((KIND == PASS_DENSITY || KIND == PASS_SPH) ? sizeof(float2) : 0));
 }
 
-template <int M, bool PER, int KIND>
+template <int M, int MJ, bool PER, int KIND>
 __global__ void __launch_bounds__(PS_THREADS) k_pass(PassArgs a)
 {
-    constexpr int NP = (M * M) / 32 > 0 ? (M * M) / 32 : 1;
+    constexpr int NP = (M * MJ) / 32 > 0 ? (M * MJ) / 32 : 1;
     constexpr int JSTEP = 32 / M;
     constexpr bool AUX = (KIND == PASS_DENSITY || KIND == PASS_SPH);
     extern __shared__ __align__(16) unsigned char pass_smem[];
-    float4 *sp = reinterpret_cast<float4 *>(pass_smem + (threadIdx.x >> 5) * pass_smem_per_warp<M, KIND>());
-    float2 *sa = reinterpret_cast<float2 *>(sp + 32 * M);
+    float4 *sp = reinterpret_cast<float4 *>(pass_smem + (threadIdx.x >> 5) * pass_smem_per_warp<MJ, KIND>());
+    float2 *sa = reinterpret_cast<float2 *>(sp + 32 * MJ);
     const unsigned lane = lane_id();
     const unsigned lt = lanemask_lt();
     const uint32_t II = lane % M;
-    const uint32_t JJ0 = (lane / M) % M;
-    // lanes that hold a distinct (i, j) pair; for M = 4 lanes 16..31 repeat
-    const bool owner = (M * M >= 32) || lane < (uint32_t)(M * M);
+    const uint32_t JJ0 = (lane / M) % MJ;
+    // lanes that hold a distinct (i, j) pair; for M x MJ = 4 x 4 lanes 16..31 repeat
+    const bool owner = (M * MJ >= 32) || lane < (uint32_t)(M * MJ);
 
     for (;;) {
         uint32_t s = 0;
@@ -182,14 +183,14 @@ __global__ void __launch_bounds__(PS_THREADS) k_pass(PassArgs a)
             const uint32_t mk = valid ? masks[t] : 0u;
             const uint32_t nb = min(32u, cnt - b0);
             acc_begin_block<KIND>(acc);
-            // stage the block's j clusters: entry e's particles at sp[e*M ..]
+            // stage the block's j clusters: entry e's particles at sp[e*MJ ..]
             __syncwarp();
 #pragma unroll 4
-            for (uint32_t q0 = 0; q0 < nb * M; q0 += 32) {  // whole warp in every shuffle
+            for (uint32_t q0 = 0; q0 < nb * MJ; q0 += 32) {  // whole warp in every shuffle
                 const uint32_t q = q0 + lane;
-                const uint32_t e = min(q / M, 31u);
-                const uint32_t src = __shfl_sync(0xffffffffu, J, e) * M + (q % M);
-                if (q < nb * M) {
+                const uint32_t e = min(q / MJ, 31u);
+                const uint32_t src = __shfl_sync(0xffffffffu, J, e) * MJ + (q % MJ);
+                if (q < nb * MJ) {
                     sp[q] = a.pos[src];
                     if constexpr (AUX) sa[q] = a.aux[src];
                 }
@@ -200,10 +201,10 @@ __global__ void __launch_bounds__(PS_THREADS) k_pass(PassArgs a)
                 const uint32_t me = __shfl_sync(0xffffffffu, mk, e);
 #pragma unroll
                 for (int tt = 0; tt < NP; ++tt) {
-                    const uint32_t jj = Je * M + JJ0 + tt * JSTEP;
-                    const float4 pj = sp[e * M + JJ0 + tt * JSTEP];
+                    const uint32_t jj = Je * MJ + JJ0 + tt * JSTEP;
+                    const float4 pj = sp[e * MJ + JJ0 + tt * JSTEP];
                     float2 aj = make_float2(0.f, 0.f);
-                    if constexpr (AUX) aj = sa[e * M + JJ0 + tt * JSTEP];
+                    if constexpr (AUX) aj = sa[e * MJ + JJ0 + tt * JSTEP];
 #pragma unroll
                     for (int k = 0; k < kSC; ++k) {
                         if (!((me >> k) & 1u)) continue;
@@ -298,34 +299,36 @@ __global__ void __launch_bounds__(PS_THREADS) k_pass(PassArgs a)
     }
 }
 
-template <int M, int KIND>
+template <int M, int MJ, int KIND>
 static void launch_mk(const PassArgs &a, int per, int grid, int threads, cudaStream_t s)
 {
     // the attribute is set for the largest block so that any shape fits
-    const size_t smax = (size_t)(PS_THREADS / 32) * pass_smem_per_warp<M, KIND>();
-    const size_t smem = (size_t)(threads / 32) * pass_smem_per_warp<M, KIND>();
+    const size_t smax = (size_t)(PS_THREADS / 32) * pass_smem_per_warp<MJ, KIND>();
+    const size_t smem = (size_t)(threads / 32) * pass_smem_per_warp<MJ, KIND>();
     static bool attr[2] = {false, false};
     if (!attr[per ? 1 : 0]) {
         if (per)
-            cudaFuncSetAttribute(k_pass<M, true, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+            cudaFuncSetAttribute(k_pass<M, MJ, true, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
         else
-            cudaFuncSetAttribute(k_pass<M, false, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+            cudaFuncSetAttribute(k_pass<M, MJ, false, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
         attr[per ? 1 : 0] = true;
     }
     if (per)
-        k_pass<M, true, KIND><<<grid, threads, smem, s>>>(a);
+        k_pass<M, MJ, true, KIND><<<grid, threads, smem, s>>>(a);
     else
-        k_pass<M, false, KIND><<<grid, threads, smem, s>>>(a);
+        k_pass<M, MJ, false, KIND><<<grid, threads, smem, s>>>(a);
 }
 
 template <int KIND>
 static cudaError_t launch_k(const PassArgs &a, int M, int per, int grid, int threads, cudaStream_t s)
 {
     if (threads != 128 && threads != PS_THREADS) return cudaErrorInvalidValue;
-    switch (M) {
-    case 4: launch_mk<4, KIND>(a, per, grid, threads, s); break;
-    case 8: launch_mk<8, KIND>(a, per, grid, threads, s); break;
-    case 16: launch_mk<16, KIND>(a, per, grid, threads, s); break;
+    switch (M * 100 + a.mj) {
+    case 404: launch_mk<4, 4, KIND>(a, per, grid, threads, s); break;
+    case 808: launch_mk<8, 8, KIND>(a, per, grid, threads, s); break;
+    case 804: launch_mk<8, 4, KIND>(a, per, grid, threads, s); break;
+    case 1616: launch_mk<16, 16, KIND>(a, per, grid, threads, s); break;
+    case 1608: launch_mk<16, 8, KIND>(a, per, grid, threads, s); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -2,12 +2,14 @@
 //
 // One warp per super-cluster (8 i-clusters of M particles), taken from an
 // atomic work counter by a persistent grid.  The warp walks the pre-order
-// octree without a stack (skip indices); lanes test the node box against
-// their i-cluster box (lane & 7) inflated by the larger of the two maximum
-// radii, with monotone round-to-nearest gaps so that no pair accepted by the
-// FP32 predicate can be pruned.  At a leaf, 4 j-clusters x 8 i-clusters are
-// box-tested per round (one lane each); each surviving (i-cluster, j-cluster)
-// tile is decided by the exact FP32 predicate on its M x M pairs.  Depth-first
+// octree without a stack (skip indices); every particle of the super-cluster
+// (2 to 4 per lane) is tested against the node box inflated by the larger of
+// its radius and the node's maximum radius, with monotone round-to-nearest
+// gaps so that no pair accepted by the FP32 predicate can be pruned.  At a
+// leaf, 4 j-clusters (MJ particles each, MJ = M or M / 2: the M x MJ tiles of
+// Sec. II-A / III-A) x 8 i-clusters are box-tested per round (one lane
+// each); each surviving (i-cluster, j-cluster) tile is decided by the exact
+// FP32 predicate on its M x MJ pairs.  Depth-first
 // order yields ascending j-clusters (Sec. II-A), so the (J, mask) list is
 // produced sorted; it is staged per warp (L2 resident) and then encoded:
 // u32 count | u8 masks | nibble blocks of 32 differences (Sec. II-B, the
@@ -131,11 +133,12 @@ __device__ bool encode_record(uint32_t cnt, const uint32_t *stJ, const uint8_t *
     return true;
 }
 
-template <int M, bool PER>
+template <int M, int MJ, bool PER>
 __global__ void __launch_bounds__(SR_THREADS, 3) k_search(SearchArgs a, SearchCtl ctl)
 {
-    constexpr int NP = (M * M) / 32 > 0 ? (M * M) / 32 : 1;  // pairs per lane per tile
+    constexpr int NP = (M * MJ) / 32 > 0 ? (M * MJ) / 32 : 1;  // pairs per lane per tile
     constexpr int JSTEP = 32 / M;
+    constexpr uint32_t R = M / MJ;        // j-clusters per i-cluster
     constexpr int NPI = (kSC * M) / 32;   // i particles per lane for the pruning tests
     constexpr int CPB = 32 / M;           // clusters covered by one 32-particle ballot
     __shared__ uint32_t wins[SR_WARPS][WIN_WORDS];
@@ -145,7 +148,7 @@ __global__ void __launch_bounds__(SR_THREADS, 3) k_search(SearchArgs a, SearchCt
     uint32_t *stJ = a.stageJ + (size_t)slot * a.stage_cap;
     uint8_t *stM = a.stageM + (size_t)slot * a.stage_cap;
     const uint32_t II = lane % M;
-    const uint32_t JJ0 = (lane / M) % M;
+    const uint32_t JJ0 = (lane / M) % MJ;
 
     for (;;) {
         uint32_t tk = 0;
@@ -202,8 +205,8 @@ __global__ void __launch_bounds__(SR_THREADS, 3) k_search(SearchArgs a, SearchCt
                 continue;
             }
             const int2 rg = a.nrng[v];
-            const int Jlo = max(rg.x / M, lastJ + 1);
-            const int Jhi = (rg.y - 1) / M;
+            const int Jlo = max(rg.x / MJ, lastJ + 1);
+            const int Jhi = (rg.y - 1) / MJ;
             ++lvis;
             jex += Jhi >= Jlo ? (uint32_t)(Jhi - Jlo + 1) : 0u;
             for (int Jb = Jlo; Jb <= Jhi; Jb += 4) {
@@ -212,9 +215,9 @@ __global__ void __launch_bounds__(SR_THREADS, 3) k_search(SearchArgs a, SearchCt
                 const int Jl = Jb + (int)(lane >> 3);
                 bool cand = false, sure = false;
                 if (Jl <= Jhi) {
-                    const float4 jlo = a.clo[Jl], jhi = a.chi[Jl];
+                    const float4 jlo = a.jlo[Jl], jhi = a.jhi[Jl];
                     cand = boxes_near<PER>(ilo, ihi, jlo, jhi, box);
-                    sure = cand && (uint32_t)Jl != s * kSC + (lane & 7) &&
+                    sure = cand && (uint32_t)Jl / R != s * kSC + (lane & 7) &&
                            boxes_all_near<PER>(ilo, ihi, jlo, jhi, box);
                 }
                 const uint32_t bal = __ballot_sync(0xffffffffu, cand);
@@ -235,7 +238,7 @@ __global__ void __launch_bounds__(SR_THREADS, 3) k_search(SearchArgs a, SearchCt
                     }
                     if (__popc(cm) > 1) {
                         // round 2: every i particle against the j-cluster box
-                        const float4 jlo = a.clo[J], jhi = a.chi[J];
+                        const float4 jlo = a.jlo[J], jhi = a.jhi[J];
                         uint32_t pm = 0;
 #pragma unroll
                         for (int t = 0; t < NPI; ++t) {
@@ -253,7 +256,7 @@ __global__ void __launch_bounds__(SR_THREADS, 3) k_search(SearchArgs a, SearchCt
                     ttests += __popc(cm & ~sm);
 #pragma unroll
                     for (int t = 0; t < NP; ++t) {
-                        const uint32_t jj = (uint32_t)J * M + JJ0 + t * JSTEP;
+                        const uint32_t jj = (uint32_t)J * MJ + JJ0 + t * JSTEP;
                         const float4 pj = a.pos[jj];
                         const float rj = __fmul_rn(a.support, pj.w);
 #pragma unroll
@@ -304,14 +307,14 @@ __global__ void __launch_bounds__(SR_THREADS, 3) k_search(SearchArgs a, SearchCt
     }
 }
 
-template <int M>
+template <int M, int MJ>
 static void launch_m(const SearchArgs &a, const SearchCtl &c, int per, int grid, int threads,
                      cudaStream_t s)
 {
     if (per)
-        k_search<M, true><<<grid, threads, 0, s>>>(a, c);
+        k_search<M, MJ, true><<<grid, threads, 0, s>>>(a, c);
     else
-        k_search<M, false><<<grid, threads, 0, s>>>(a, c);
+        k_search<M, MJ, false><<<grid, threads, 0, s>>>(a, c);
 }
 
 cudaError_t launch_search_ctl(const SearchArgs &a, const uint32_t *work, uint32_t count,
@@ -320,10 +323,12 @@ cudaError_t launch_search_ctl(const SearchArgs &a, const uint32_t *work, uint32_
 {
     SearchCtl c{work, count, redo};
     if (threads != 128 && threads != SR_THREADS) return cudaErrorInvalidValue;
-    switch (M) {
-    case 4: launch_m<4>(a, c, any_periodic, grid, threads, s); break;
-    case 8: launch_m<8>(a, c, any_periodic, grid, threads, s); break;
-    case 16: launch_m<16>(a, c, any_periodic, grid, threads, s); break;
+    switch (M * 100 + a.mj) {
+    case 404: launch_m<4, 4>(a, c, any_periodic, grid, threads, s); break;
+    case 808: launch_m<8, 8>(a, c, any_periodic, grid, threads, s); break;
+    case 804: launch_m<8, 4>(a, c, any_periodic, grid, threads, s); break;
+    case 1616: launch_m<16, 16>(a, c, any_periodic, grid, threads, s); break;
+    case 1608: launch_m<16, 8>(a, c, any_periodic, grid, threads, s); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -37,7 +37,8 @@ class nl_box(C.Structure):
 class nl_params(C.Structure):
     _fields_ = [("key", C.c_int32), ("cluster", C.c_int32), ("support", C.c_float),
                 ("compress", C.c_int32), ("leaf_bucket", C.c_int32),
-                ("threads_per_block", C.c_int32), ("blocks_per_sm", C.c_int32)]
+                ("threads_per_block", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("j_cluster", C.c_int32)]
 
 
 class nl_sizes(C.Structure):
@@ -45,7 +46,8 @@ class nl_sizes(C.Structure):
                 ("n_leaves", C.c_int64), ("n_nodes", C.c_int64), ("n_entries", C.c_int64),
                 ("n_tiles", C.c_int64), ("list_bytes", C.c_int64), ("cluster", C.c_int32),
                 ("compress", C.c_int32), ("node_visits", C.c_int64), ("leaf_visits", C.c_int64),
-                ("j_examined", C.c_int64), ("tile_tests", C.c_int64)]
+                ("j_examined", C.c_int64), ("tile_tests", C.c_int64), ("j_cluster", C.c_int32),
+                ("pad0", C.c_int32)]
 
 
 P = C.c_void_p
@@ -161,12 +163,14 @@ def make_box(box):
 
 
 def make_params(key=NL_KEY_HILBERT, cluster=8, support=2.0, compress=1, leaf_bucket=64,
-                threads_per_block=0, blocks_per_sm=0):
+                threads_per_block=0, blocks_per_sm=0, j_cluster=0):
+    """Build options; j_cluster 0 means j-clusters of `cluster` particles."""
     p = nl_params()
     load().nl_default_params(C.byref(p))
     p.key, p.cluster, p.support = int(key), int(cluster), float(support)
     p.compress, p.leaf_bucket = int(compress), int(leaf_bucket)
     p.threads_per_block, p.blocks_per_sm = int(threads_per_block), int(blocks_per_sm)
+    p.j_cluster = int(j_cluster)
     return p
 
 

@@ -7,18 +7,21 @@ from paper_2602_19873_gb300 import nl
 
 DENSITY_RTOL = 1e-5   # FP32 density vs the FP64 oracle, max relative error
 
+# tile shapes (i-cluster M, j-cluster MJ) the library supports
+TILES = [(4, 4), (8, 8), (8, 4), (16, 16), (16, 8)]
+
 
 def to_dev(d, keys=("x", "y", "z", "h", "m")):
     import torch
     return {k: torch.from_numpy(np.ascontiguousarray(d[k], dtype=np.float32)).cuda() for k in keys}
 
 
-def gpu_build(d, cluster=8, compress=1, bucket=64, kind=None, support=None):
+def gpu_build(d, cluster=8, compress=1, bucket=64, kind=None, support=None, j_cluster=0):
     import torch
     t = to_dev(d)
     p = nl.make_params(key=d["kind"] if kind is None else kind, cluster=cluster,
                        support=d["support"] if support is None else support, compress=compress,
-                       leaf_bucket=bucket)
+                       leaf_bucket=bucket, j_cluster=j_cluster)
     L = nl.NeighborList().build(t["x"], t["y"], t["z"], t["h"], d["box"], p)
     torch.cuda.synchronize()
     return L, t
@@ -44,11 +47,12 @@ def gpu_records(L, sc_ids):
     return out
 
 
-def compare_records(L, o, d, cluster, compress, sc_ids, rows, p_off, p_idx):
+def compare_records(L, o, d, cluster, compress, sc_ids, rows, p_off, p_idx, jcluster=None):
     """Byte-exact comparison of the GPU records of sc_ids with the oracle's
     independent encoding of the canonical lists built from (rows, P)."""
     n = len(o["xs"])
-    so, J, m = orc.cluster_lists(n, cluster, p_off, p_idx, rows, sc_ids)
+    so, J, m = orc.cluster_lists(n, cluster, p_off, p_idx, rows, sc_ids,
+                                 jcluster=jcluster or cluster)
     off, data = L.records()
     total = 0
     for t, s in enumerate(sc_ids):

@@ -38,12 +38,12 @@ def _pad_offsets(systems, M):
     return pad
 
 
-@pytest.mark.parametrize("cluster", [4, 8, 16])
-def test_batch_matches_systems_alone(cluster):
+@pytest.mark.parametrize("cluster,jcl", [(4, 4), (8, 8), (8, 4), (16, 16), (16, 8)])
+def test_batch_matches_systems_alone(cluster, jcl):
     import torch
     systems = _batch(seed=401 + cluster, log_n=(2.7, 3.6))
     offs, cat, dev = _concat(systems)
-    p = nl.make_params(key=1, cluster=cluster, support=2.0)
+    p = nl.make_params(key=1, cluster=cluster, support=2.0, j_cluster=jcl)
     L = nl.NeighborList().build_batch(dev["x"], dev["y"], dev["z"], dev["h"], offs,
                                       [d["box"] for d in systems], p)
     n = int(offs[-1])
@@ -62,8 +62,9 @@ def test_batch_matches_systems_alone(cluster):
         g_off, g_idx = orc.gather_all(o["xs"], o["ys"], o["zs"], o["hs"], d["box"], 2.0)
         p_off, p_idx = orc.symmetrize(g_off, g_idx)
         nsc = (ns + 8 * cluster - 1) // (8 * cluster)
-        so, J, m = orc.cluster_lists(ns, cluster, p_off, p_idx, np.arange(ns), np.arange(nsc))
-        sc0, cl0 = pad[k] // (8 * cluster), pad[k] // cluster
+        so, J, m = orc.cluster_lists(ns, cluster, p_off, p_idx, np.arange(ns), np.arange(nsc),
+                                     jcluster=jcl)
+        sc0, cl0 = pad[k] // (8 * cluster), pad[k] // jcl
         for t in range(nsc):
             want = orc.encode_record(J[so[t]:so[t + 1]] + cl0, m[so[t]:so[t + 1]], 32, True)
             b = int(rec_off[sc0 + t])

@@ -83,6 +83,7 @@ def test_autotuner_returns_a_valid_faster_choice():
         best, ms = nl.autotune_batch(dev["x"], dev["y"], dev["z"], dev["h"], dev["m"], offs, boxes,
                                      base, reps=1, stream=stream)
         assert best.cluster in (4, 8, 16) and best.threads_per_block in (128, 256)
+        assert best.j_cluster in (best.cluster, best.cluster // 2) and best.j_cluster >= 4
         assert best.blocks_per_sm in (2, 3, 4) and ms > 0
         # the tuned parameters give the same densities within the FP32 tolerance
         a = _normal_density(dev, offs, boxes, base, stream)

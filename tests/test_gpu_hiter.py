@@ -13,10 +13,10 @@ from nlcheck import oracle_sorted, to_dev
 pytestmark = pytest.mark.gpu
 
 
-def _iterate(d, n_target, tol, start, max_iter=60, cluster=8):
+def _iterate(d, n_target, tol, start, max_iter=60, cluster=8, jcl=0):
     import torch
     t = to_dev(d)
-    p = nl.make_params(key=d["kind"], cluster=cluster, support=d["support"])
+    p = nl.make_params(key=d["kind"], cluster=cluster, support=d["support"], j_cluster=jcl)
     L = nl.NeighborList()
     conv = torch.zeros(len(d["x"]), dtype=torch.uint8, device="cuda")
     info = L.iterate_h(t["x"], t["y"], t["z"], t["h"], d["box"], p, n_target, tol,
@@ -39,12 +39,12 @@ def _oracle_counts(d, h):
                                         ("plummer", nl.NL_HSTART_PLAIN),
                                         ("uniform", nl.NL_HSTART_GIVEN),
                                         ("plummer", nl.NL_HSTART_GIVEN)])
-@pytest.mark.parametrize("cluster", [4, 8])
-def test_h_in_window(name, start, cluster):
+@pytest.mark.parametrize("cluster,jcl", [(4, 4), (8, 8), (8, 4)])
+def test_h_in_window(name, start, cluster, jcl):
     d = {"evrard": lambda: wl.evrard(30011, seed=201, n_target=100),
          "plummer": lambda: wl.plummer(30001, n_spheres=4, seed=202, n_target=100),
          "uniform": lambda: wl.uniform(30011, seed=203, n_target=100)}[name]()
-    L, h, conv, info = _iterate(d, 100.0, 2.0, start, cluster=cluster)
+    L, h, conv, info = _iterate(d, 100.0, 2.0, start, cluster=cluster, jcl=jcl)
     assert info["status"] == 0, info
     assert conv.all()
     cnt = _oracle_counts(d, h)

@@ -8,8 +8,8 @@ import oracle as orc
 from paper_2602_19873_gb300 import nl
 from paper_2602_19873_gb300 import workloads as wl
 
-from nlcheck import (DENSITY_RTOL, compare_records, full_reference, gpu_build, gpu_counts,
-                     gpu_density, oracle_sorted)
+from nlcheck import (DENSITY_RTOL, TILES, compare_records, full_reference, gpu_build,
+                     gpu_counts, gpu_density, oracle_sorted)
 
 pytestmark = pytest.mark.gpu
 
@@ -66,17 +66,18 @@ def test_octree_bit_exact(cases, name, bucket):
 
 
 @pytest.mark.parametrize("name", ["uniform", "evrard", "lj_fluid", "plummer"])
-@pytest.mark.parametrize("cluster", [4, 8, 16])
+@pytest.mark.parametrize("cluster,jcl", TILES)
 @pytest.mark.parametrize("compress", [1, 0])
-def test_records_byte_exact(cases, name, cluster, compress):
+def test_records_byte_exact(cases, name, cluster, jcl, compress):
     d, o, (g_off, g_idx, p_off, p_idx) = cases[name]
-    L, t = gpu_build(d, cluster=cluster, compress=compress)
+    L, t = gpu_build(d, cluster=cluster, compress=compress, j_cluster=jcl)
     s = L.sizes()
     n = len(o["xs"])
     nsc = s["n_superclusters"]
     assert nsc == (n + 8 * cluster - 1) // (8 * cluster)
     total, so, J, m = compare_records(L, o, d, cluster, compress, np.arange(nsc), np.arange(n),
-                                      p_off, p_idx)
+                                      p_off, p_idx, jcluster=jcl)
+    assert s["j_cluster"] == jcl
     assert s["list_bytes"] == total
     assert s["n_entries"] == len(J)
     assert s["n_tiles"] == int(sum(bin(int(v)).count("1") for v in m))
@@ -84,10 +85,10 @@ def test_records_byte_exact(cases, name, cluster, compress):
 
 
 @pytest.mark.parametrize("name", ["uniform", "evrard", "lj_fluid", "plummer"])
-@pytest.mark.parametrize("cluster", [4, 8, 16])
-def test_density_and_counts(cases, name, cluster):
+@pytest.mark.parametrize("cluster,jcl", TILES)
+def test_density_and_counts(cases, name, cluster, jcl):
     d, o, (g_off, g_idx, p_off, p_idx) = cases[name]
-    L, t = gpu_build(d, cluster=cluster)
+    L, t = gpu_build(d, cluster=cluster, j_cluster=jcl)
     n = len(o["xs"])
     rho = gpu_density(L, t, n)[o["perm"]]
     want = orc.density(o["xs"], o["ys"], o["zs"], o["hs"], o["ms"], d["box"], g_off, g_idx,
@@ -135,14 +136,14 @@ def _tiny(n, seed, per=True, h=0.05):
 
 
 @pytest.mark.parametrize("n", [1, 2, 5, 63, 64, 65, 130, 4097])
-@pytest.mark.parametrize("cluster", [4, 8, 16])
-def test_small_and_ragged_sizes(n, cluster):
+@pytest.mark.parametrize("cluster,jcl", TILES)
+def test_small_and_ragged_sizes(n, cluster, jcl):
     d = _tiny(n, seed=n, h=0.2 if n < 100 else 0.05)
     o = oracle_sorted(d)
     g_off, g_idx, p_off, p_idx = full_reference(o, d)
-    L, t = gpu_build(d, cluster=cluster, bucket=8)
+    L, t = gpu_build(d, cluster=cluster, bucket=8, j_cluster=jcl)
     nsc = L.sizes()["n_superclusters"]
-    compare_records(L, o, d, cluster, 1, np.arange(nsc), np.arange(n), p_off, p_idx)
+    compare_records(L, o, d, cluster, 1, np.arange(nsc), np.arange(n), p_off, p_idx, jcluster=jcl)
     rho = gpu_density(L, t, n)[o["perm"]]
     want = orc.density(o["xs"], o["ys"], o["zs"], o["hs"], o["ms"], d["box"], g_off, g_idx,
                        np.arange(n))
@@ -180,7 +181,7 @@ def test_invalid_inputs_are_rejected():
     d = _tiny(200, seed=9)
     base = {k: d[k].copy() for k in ("x", "y", "z", "h", "m")}
 
-    def run(mod=None, box=None, cluster=8, h=None):
+    def run(mod=None, box=None, cluster=8, h=None, jcl=0):
         dd = dict(d)
         for k in base:
             dd[k] = base[k].copy()
@@ -190,7 +191,7 @@ def test_invalid_inputs_are_rejected():
             dd["box"] = box
         from nlcheck import to_dev
         t = to_dev(dd)
-        p = nl.make_params(key=1, cluster=cluster, support=2.0)
+        p = nl.make_params(key=1, cluster=cluster, support=2.0, j_cluster=jcl)
         with pytest.raises(nl.NLError) as e:
             nl.NeighborList().build(t["x"], t["y"], t["z"], t["h"], dd["box"], p)
         return e.value.status
@@ -212,6 +213,8 @@ def test_invalid_inputs_are_rejected():
     assert run(zero_h) == 1
     assert run(big_h) == 2
     assert run(cluster=6) == 1
+    for c, j in ((8, 2), (4, 2), (8, 16), (16, 4), (8, -1)):
+        assert run(cluster=c, jcl=j) == 1
     # a good build on the same process still works afterwards
     o = oracle_sorted(d)
     L, t = gpu_build(d)
@@ -220,16 +223,18 @@ def test_invalid_inputs_are_rejected():
     L.free()
 
 
-def test_overflow_rounds_keep_records_exact(cases, monkeypatch):
+@pytest.mark.parametrize("jcl", [8, 4])
+def test_overflow_rounds_keep_records_exact(cases, monkeypatch, jcl):
     """Tiny initial staging and list buffers force the redo rounds (staging
     growth and list-buffer growth); records stay byte-exact with no holes."""
     d, o, (g_off, g_idx, p_off, p_idx) = cases["evrard"]
     monkeypatch.setenv("NLGB_STAGE_CAP0", "40")
     monkeypatch.setenv("NLGB_LIST_CAP0", "20000")
-    L, t = gpu_build(d)
+    L, t = gpu_build(d, j_cluster=jcl)
     n = len(o["xs"])
     nsc = L.sizes()["n_superclusters"]
-    total, so, J, m = compare_records(L, o, d, 8, 1, np.arange(nsc), np.arange(n), p_off, p_idx)
+    total, so, J, m = compare_records(L, o, d, 8, 1, np.arange(nsc), np.arange(n), p_off, p_idx,
+                                      jcluster=jcl)
     assert L.sizes()["list_bytes"] == total
     rho = gpu_density(L, t, n)[o["perm"]]
     want = orc.density(o["xs"], o["ys"], o["zs"], o["hs"], o["ms"], d["box"], g_off, g_idx,
@@ -241,8 +246,8 @@ def test_overflow_rounds_keep_records_exact(cases, monkeypatch):
 FORCE_RTOL = 1e-5   # |a_gpu - a_64| / sum_j |f_ij|_64, per particle
 
 
-@pytest.mark.parametrize("cluster", [4, 8, 16])
-def test_sph_pressure_force(cases, cluster):
+@pytest.mark.parametrize("cluster,jcl", TILES)
+def test_sph_pressure_force(cases, cluster, jcl):
     """Inputs rho and P are the oracle's FP64 density rounded to FP32 and
     P = (gamma - 1) rho u, so both sides read identical values."""
     import torch
@@ -255,7 +260,7 @@ def test_sph_pressure_force(cases, cluster):
     ax, ay, az, fa = orc.sph_force(o["xs"], o["ys"], o["zs"], o["hs"], o["ms"],
                                    rho32.astype(np.float64), pres32.astype(np.float64), d["box"],
                                    p_off, p_idx, np.arange(n))
-    L, t = gpu_build(d, cluster=cluster)
+    L, t = gpu_build(d, cluster=cluster, j_cluster=jcl)
     inv = np.empty(n, np.int64)
     inv[o["perm"]] = np.arange(n)
     rho_c = torch.from_numpy(rho32[inv]).cuda()       # caller order
@@ -273,14 +278,14 @@ def test_sph_pressure_force(cases, cluster):
     L.free()
 
 
-@pytest.mark.parametrize("cluster", [4, 8, 16])
-def test_lj_force(cases, cluster):
+@pytest.mark.parametrize("cluster,jcl", TILES)
+def test_lj_force(cases, cluster, jcl):
     import torch
     d, o, (g_off, g_idx, p_off, p_idx) = cases["lj_fluid"]
     n = len(o["xs"])
     fx, fy, fz, fa = orc.lj_force(o["xs"], o["ys"], o["zs"], d["box"], 1.0, 0.3, g_off, g_idx,
                                   np.arange(n))
-    L, t = gpu_build(d, cluster=cluster)
+    L, t = gpu_build(d, cluster=cluster, j_cluster=jcl)
     out = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
     L.force_pass(nl.NL_FORCE_LJ, *out, eps=1.0, sigma=0.3)
     torch.cuda.synchronize()
