@@ -131,6 +131,7 @@ struct nl_list {
     int profiling = 0;
     cudaEvent_t ev[kStages + 1] = {};
     float stage_ms[kStages] = {};
+    int pass_timed = 0;   // the pass events (5..7) have been recorded
     // device copies of host inputs for nl_density_from_host
     DevBuf hx, hy, hz, hh, hm, hrho;
     // h iteration state (sorted order)
@@ -144,6 +145,7 @@ struct nl_list {
                 cudaError_t e = cudaEventCreate(&ev[i]);
                 if (e != cudaSuccess) return e;
             }
+        if (k == kStages) pass_timed = 1;
         return cudaEventRecord(ev[k], s);
     }
     void collect(int from, int to)
@@ -635,7 +637,7 @@ nl_status nl_get_stage_times(const nl_list *cnl, float *ms, int32_t cap, int32_t
 {
     if (!cnl) return fail(NL_ERR_ARG, "list is NULL");
     nl_list *nl = const_cast<nl_list *>(cnl);
-    if (nl->profiling && nl->ev[7]) {
+    if (nl->profiling && nl->pass_timed) {
         CK(cudaEventSynchronize(nl->ev[7]));
         CK(cudaEventElapsedTime(&nl->stage_ms[5], nl->ev[5], nl->ev[6]));
         CK(cudaEventElapsedTime(&nl->stage_ms[6], nl->ev[6], nl->ev[7]));

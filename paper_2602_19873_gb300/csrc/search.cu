@@ -23,6 +23,7 @@ namespace nlg {
 constexpr int SR_THREADS = 256;
 constexpr int SR_WARPS = SR_THREADS / 32;
 constexpr int WIN_WORDS = 64;
+constexpr uint32_t SR_QCAP = 128;   // j-cluster queue entries per warp (multiple of 4)
 
 struct SearchCtl {
     const uint32_t *work;   // NULL: super-clusters 0..count-1, else ids
@@ -133,22 +134,37 @@ __device__ bool encode_record(uint32_t cnt, const uint32_t *stJ, const uint8_t *
     return true;
 }
 
+// Shared memory of one warp: the super-cluster's particles, a chunk of 32
+// consecutive octree nodes, the queue of candidate j-clusters, the particles
+// and boxes of the 4 j-clusters being tested, and the encoder window.
+template <int M, int MJ>
+struct SearchSmem {
+    float4 ip[kSC * M];            // i particles (x, y, z, h)
+    float4 nlo[32], nhi[32];       // node chunk
+    int2 nrg[32];
+    uint32_t jq[SR_QCAP];          // candidate j-clusters, ascending
+    float4 jp[4 * MJ];             // particles of the 4 j-clusters under test
+    float4 jb[8];                  // their boxes (lo, hi) x 4
+    uint32_t win[WIN_WORDS];
+};
+
 template <int M, int MJ, bool PER>
-__global__ void __launch_bounds__(SR_THREADS, 3) k_search(SearchArgs a, SearchCtl ctl)
+__global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCtl ctl)
 {
     constexpr int NP = (M * MJ) / 32 > 0 ? (M * MJ) / 32 : 1;  // pairs per lane per tile
     constexpr int JSTEP = 32 / M;
     constexpr uint32_t R = M / MJ;        // j-clusters per i-cluster
     constexpr int NPI = (kSC * M) / 32;   // i particles per lane for the pruning tests
     constexpr int CPB = 32 / M;           // clusters covered by one 32-particle ballot
-    __shared__ uint32_t wins[SR_WARPS][WIN_WORDS];
+    extern __shared__ __align__(16) unsigned char search_smem[];
+    SearchSmem<M, MJ> &S = reinterpret_cast<SearchSmem<M, MJ> *>(search_smem)[threadIdx.x >> 5];
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
-    uint32_t *win = wins[warp];
     const uint32_t slot = blockIdx.x * (blockDim.x >> 5) + warp;
     uint32_t *stJ = a.stageJ + (size_t)slot * a.stage_cap;
     uint8_t *stM = a.stageM + (size_t)slot * a.stage_cap;
     const uint32_t II = lane % M;
     const uint32_t JJ0 = (lane / M) % MJ;
+    const uint32_t grp = lane >> 3;       // j-cluster slot of this lane in round 1
 
     for (;;) {
         uint32_t tk = 0;
@@ -168,30 +184,130 @@ __global__ void __launch_bounds__(SR_THREADS, 3) k_search(SearchArgs a, SearchCt
         // i-cluster box of this lane's cluster (lane & 7)
         const float4 ilo = a.clo[s * kSC + (lane & 7)];
         const float4 ihi = a.chi[s * kSC + (lane & 7)];
-        // pruning particles: base + lane + 32 t
+        // pruning particles base + lane + 32 t, also staged for the tile tests
         float4 qp[NPI];
         float qr[NPI];
+        __syncwarp();
 #pragma unroll
         for (int t = 0; t < NPI; ++t) {
             qp[t] = a.pos[base + lane + 32 * t];
             qr[t] = __fmul_rn(a.support, qp[t].w);
-        }
-        // tile-test particles: lane's particle II of every i-cluster
-        float4 pi[kSC];
-        float ri[kSC];
-#pragma unroll
-        for (int k = 0; k < kSC; ++k) {
-            pi[k] = a.pos[base + k * M + II];
-            ri[k] = __fmul_rn(a.support, pi[k].w);
+            S.ip[lane + 32 * t] = qp[t];
         }
 
-        uint32_t cnt = 0, tiles = 0, nvis = 0, lvis = 0, jex = 0, ttests = 0;
+        uint32_t cnt = 0, tiles = 0, nvis = 0, lvis = 0, jex = 0, ttests = 0, qn = 0;
         int lastJ = -1;
-        uint32_t v = vroot;
+
+        // Test the queued j-clusters, 4 per round, and stage the hits.
+        auto flush = [&]() {
+            for (uint32_t b = 0; b < qn; b += 4) {
+                const uint32_t nq = min(4u, qn - b);
+                // stage the particles and boxes of up to 4 j-clusters
+                __syncwarp();
+                bool cand = false, sure = false;
+                if (grp < nq) {
+                    const uint32_t Jl = S.jq[b + grp];
+#pragma unroll
+                    for (uint32_t jl = lane & 7; jl < (uint32_t)MJ; jl += 8)
+                        S.jp[grp * MJ + jl] = a.pos[Jl * MJ + jl];
+                    const float4 jlo = a.jlo[Jl], jhi = a.jhi[Jl];
+                    if ((lane & 7) == 0) {
+                        S.jb[2 * grp] = jlo;
+                        S.jb[2 * grp + 1] = jhi;
+                    }
+                    // round 1: 4 j-clusters x 8 i-cluster boxes, one per lane:
+                    // may some pair be neighbors, and are all pairs neighbors?
+                    cand = boxes_near<PER>(ilo, ihi, jlo, jhi, box);
+                    sure = cand && Jl / R != s * kSC + (lane & 7) &&
+                           boxes_all_near<PER>(ilo, ihi, jlo, jhi, box);
+                }
+                const uint32_t bal = __ballot_sync(0xffffffffu, cand);
+                const uint32_t sbal = __ballot_sync(0xffffffffu, sure);
+                __syncwarp();
+                for (uint32_t q = 0; q < nq; ++q) {
+                    uint32_t cm = (bal >> (8 * q)) & 0xffu;
+                    if (!cm) continue;
+                    const uint32_t J = S.jq[b + q];
+                    const uint32_t sm = (sbal >> (8 * q)) & 0xffu;
+                    if (sm == cm) {  // every candidate tile is a sure hit
+                        if (lane == 0 && cnt < a.stage_cap) {
+                            stJ[cnt] = J;
+                            stM[cnt] = (uint8_t)sm;
+                        }
+                        ++cnt;
+                        tiles += __popc(sm);
+                        continue;
+                    }
+                    if (__popc(cm) > 1) {
+                        // round 2: every i particle against the j-cluster box
+                        const float4 jlo = S.jb[2 * q], jhi = S.jb[2 * q + 1];
+                        uint32_t pm = 0;
+#pragma unroll
+                        for (int t = 0; t < NPI; ++t) {
+                            const uint32_t bt = __ballot_sync(
+                                0xffffffffu, point_near<PER>(qp[t], qr[t], jlo, jhi, box));
+#pragma unroll
+                            for (int c = 0; c < CPB; ++c)
+                                if ((bt >> (c * M)) & ((M == 32) ? 0xffffffffu : ((1u << M) - 1u)))
+                                    pm |= 1u << (t * CPB + c);
+                        }
+                        cm &= pm | sm;
+                        if (!cm) continue;
+                    }
+                    // exact FP32 test of the remaining M x MJ tiles
+                    uint32_t mask = sm;
+                    ttests += __popc(cm & ~sm);
+#pragma unroll
+                    for (int k = 0; k < kSC; ++k) {
+                        if (!((cm >> k) & 1u) || ((mask >> k) & 1u)) continue;
+                        const uint32_t ii = base + k * M + II;
+                        const float4 pik = S.ip[k * M + II];
+                        const float rik = __fmul_rn(a.support, pik.w);
+                        bool hit = false;
+#pragma unroll
+                        for (int t = 0; t < NP; ++t) {
+                            const uint32_t jl = JJ0 + t * JSTEP;
+                            const float4 pj = S.jp[q * MJ + jl];
+                            const float rj = __fmul_rn(a.support, pj.w);
+                            const float d2 = pair_d2<PER>(pik, pj, box);
+                            const float r = fmaxf(rik, rj);
+                            hit |= (ii != J * MJ + jl) && d2 < __fmul_rn(r, r);
+                        }
+                        if (__any_sync(0xffffffffu, hit)) mask |= 1u << k;
+                    }
+                    if (mask) {
+                        if (lane == 0 && cnt < a.stage_cap) {
+                            stJ[cnt] = J;
+                            stM[cnt] = (uint8_t)mask;
+                        }
+                        ++cnt;
+                        tiles += __popc(mask);
+                    }
+                }
+            }
+            qn = 0;
+        };
+
+        // Stackless pre-order walk of the system's subtree; nodes are read in
+        // coalesced chunks of 32 consecutive nodes staged in shared memory.
+        uint32_t v = vroot, cb = 0;
+        bool have = false;
         while (v < vend) {
+            if (!have || v - cb >= 32u) {
+                cb = v;
+                have = true;
+                __syncwarp();
+                const uint32_t u = cb + lane;
+                if (u < vend) {
+                    S.nlo[lane] = a.nlo[u];
+                    S.nhi[lane] = a.nhi[u];
+                    S.nrg[lane] = a.nrng[u];
+                }
+                __syncwarp();
+            }
             ++nvis;
-            const float4 nlo = a.nlo[v];
-            const float4 nhi = a.nhi[v];
+            const float4 nlo = S.nlo[v - cb];
+            const float4 nhi = S.nhi[v - cb];
             const uint32_t skip = (uint32_t)__float_as_int(nhi.w);
             bool near = false;
 #pragma unroll
@@ -204,90 +320,33 @@ __global__ void __launch_bounds__(SR_THREADS, 3) k_search(SearchArgs a, SearchCt
                 ++v;
                 continue;
             }
-            const int2 rg = a.nrng[v];
-            const int Jlo = max(rg.x / MJ, lastJ + 1);
+            // leaf: queue its j-clusters not queued yet (leaves can share one)
+            const int2 rg = S.nrg[v - cb];
+            int Jlo = max(rg.x / MJ, lastJ + 1);
             const int Jhi = (rg.y - 1) / MJ;
             ++lvis;
-            jex += Jhi >= Jlo ? (uint32_t)(Jhi - Jlo + 1) : 0u;
-            for (int Jb = Jlo; Jb <= Jhi; Jb += 4) {
-                // round 1: 4 j-clusters x 8 i-cluster boxes, one per lane:
-                // may some pair be neighbors, and are all pairs neighbors?
-                const int Jl = Jb + (int)(lane >> 3);
-                bool cand = false, sure = false;
-                if (Jl <= Jhi) {
-                    const float4 jlo = a.jlo[Jl], jhi = a.jhi[Jl];
-                    cand = boxes_near<PER>(ilo, ihi, jlo, jhi, box);
-                    sure = cand && (uint32_t)Jl / R != s * kSC + (lane & 7) &&
-                           boxes_all_near<PER>(ilo, ihi, jlo, jhi, box);
-                }
-                const uint32_t bal = __ballot_sync(0xffffffffu, cand);
-                const uint32_t sbal = __ballot_sync(0xffffffffu, sure);
-                for (int q = 0; q < 4; ++q) {
-                    uint32_t cm = (bal >> (8 * q)) & 0xffu;
-                    if (!cm) continue;
-                    const int J = Jb + q;
-                    const uint32_t sm = (sbal >> (8 * q)) & 0xffu;
-                    if (sm == cm) {  // every candidate tile is a sure hit
-                        if (lane == 0 && cnt < a.stage_cap) {
-                            stJ[cnt] = (uint32_t)J;
-                            stM[cnt] = (uint8_t)sm;
-                        }
-                        ++cnt;
-                        tiles += __popc(sm);
-                        continue;
-                    }
-                    if (__popc(cm) > 1) {
-                        // round 2: every i particle against the j-cluster box
-                        const float4 jlo = a.jlo[J], jhi = a.jhi[J];
-                        uint32_t pm = 0;
-#pragma unroll
-                        for (int t = 0; t < NPI; ++t) {
-                            const uint32_t b = __ballot_sync(
-                                0xffffffffu, point_near<PER>(qp[t], qr[t], jlo, jhi, box));
-#pragma unroll
-                            for (int c = 0; c < CPB; ++c)
-                                if ((b >> (c * M)) & ((M == 32) ? 0xffffffffu : ((1u << M) - 1u)))
-                                    pm |= 1u << (t * CPB + c);
-                        }
-                        cm &= pm | sm;
-                        if (!cm) continue;
-                    }
-                    uint32_t mask = sm;
-                    ttests += __popc(cm & ~sm);
-#pragma unroll
-                    for (int t = 0; t < NP; ++t) {
-                        const uint32_t jj = (uint32_t)J * MJ + JJ0 + t * JSTEP;
-                        const float4 pj = a.pos[jj];
-                        const float rj = __fmul_rn(a.support, pj.w);
-#pragma unroll
-                        for (int k = 0; k < kSC; ++k) {
-                            if (!((cm >> k) & 1u) || ((mask >> k) & 1u)) continue;
-                            const uint32_t ii = base + k * M + II;
-                            const float d2 = pair_d2<PER>(pi[k], pj, box);
-                            const float r = fmaxf(ri[k], rj);
-                            const bool hit = (ii != jj) && d2 < __fmul_rn(r, r);
-                            if (__any_sync(0xffffffffu, hit)) mask |= 1u << k;
-                        }
-                    }
-                    if (mask) {
-                        if (lane == 0 && cnt < a.stage_cap) {
-                            stJ[cnt] = (uint32_t)J;
-                            stM[cnt] = (uint8_t)mask;
-                        }
-                        ++cnt;
-                        tiles += __popc(mask);
-                    }
+            if (Jhi >= Jlo) {
+                jex += (uint32_t)(Jhi - Jlo + 1);
+                lastJ = Jhi;
+                while (Jlo <= Jhi) {
+                    if (qn == SR_QCAP) flush();
+                    const uint32_t c = min((uint32_t)(Jhi - Jlo + 1), SR_QCAP - qn);
+                    __syncwarp();
+                    for (uint32_t e = lane; e < c; e += 32) S.jq[qn + e] = (uint32_t)Jlo + e;
+                    __syncwarp();
+                    qn += c;
+                    Jlo += (int)c;
                 }
             }
-            lastJ = max(lastJ, Jhi);
             ++v;
         }
+        flush();
         __syncwarp();
         bool ok = cnt <= a.stage_cap;
         if (!ok) {
             if (lane == 0) atomicMax(&a.st->max_count, cnt);
         } else {
-            ok = encode_record(cnt, stJ, stM, win, a, s);
+            ok = encode_record(cnt, stJ, stM, S.win, a, s);
             if (!ok && lane == 0) atomicExch(&a.st->list_overflow, 1u);
         }
         if (lane == 0) {
@@ -311,10 +370,20 @@ template <int M, int MJ>
 static void launch_m(const SearchArgs &a, const SearchCtl &c, int per, int grid, int threads,
                      cudaStream_t s)
 {
+    const size_t smem = (size_t)(threads / 32) * sizeof(SearchSmem<M, MJ>);
+    const size_t smax = (size_t)SR_WARPS * sizeof(SearchSmem<M, MJ>);
+    static bool attr[2] = {false, false};
+    if (!attr[per ? 1 : 0]) {
+        if (per)
+            cudaFuncSetAttribute(k_search<M, MJ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+        else
+            cudaFuncSetAttribute(k_search<M, MJ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+        attr[per ? 1 : 0] = true;
+    }
     if (per)
-        k_search<M, MJ, true><<<grid, threads, 0, s>>>(a, c);
+        k_search<M, MJ, true><<<grid, threads, smem, s>>>(a, c);
     else
-        k_search<M, MJ, false><<<grid, threads, 0, s>>>(a, c);
+        k_search<M, MJ, false><<<grid, threads, smem, s>>>(a, c);
 }
 
 cudaError_t launch_search_ctl(const SearchArgs &a, const uint32_t *work, uint32_t count,

@@ -295,3 +295,20 @@ def test_lj_force(cases, cluster, jcl):
     assert err.max() <= FORCE_RTOL, err.max()
     assert np.abs(got.sum(0)).max() <= 1e-5 * fa.sum()
     L.free()
+
+
+def test_stage_times_before_and_after_a_pass():
+    """Stage timing is readable after a build alone (pass stages zero) and
+    after a pass (every stage timed)."""
+    d = _tiny(5000, seed=77)
+    L, t = gpu_build(d)
+    L.set_profiling(True)
+    from nlcheck import to_dev
+    p = nl.make_params(key=1, cluster=8, support=2.0)
+    L.build(t["x"], t["y"], t["z"], t["h"], d["box"], p)
+    st = L.stage_times()
+    assert st["search"] > 0 and st["pass"] == 0
+    gpu_density(L, t, 5000)
+    st = L.stage_times()
+    assert st["pass"] > 0
+    L.free()
