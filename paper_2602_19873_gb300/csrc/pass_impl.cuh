@@ -98,7 +98,7 @@ constexpr size_t pass_smem_per_warp()
 }
 
 template <int M, int MJ, bool PER, int KIND>
-__global__ void __launch_bounds__(PS_THREADS) k_pass(PassArgs a)
+__global__ void __launch_bounds__(PS_THREADS, 3) k_pass(PassArgs a)
 {
     constexpr int NP = (M * MJ) / 32 > 0 ? (M * MJ) / 32 : 1;
     constexpr int JSTEP = 32 / M;

@@ -2,16 +2,19 @@
 //
 // One warp per super-cluster (8 i-clusters of M particles), taken from an
 // atomic work counter by a persistent grid.  The warp walks the pre-order
-// octree without a stack (skip indices); every particle of the super-cluster
-// (2 to 4 per lane) is tested against the node box inflated by the larger of
-// its radius and the node's maximum radius, with monotone round-to-nearest
-// gaps so that no pair accepted by the FP32 predicate can be pruned.  At a
-// leaf, 4 j-clusters (MJ particles each, MJ = M or M / 2: the M x MJ tiles of
-// Sec. II-A / III-A) x 8 i-clusters are box-tested per round (one lane
-// each); each surviving (i-cluster, j-cluster) tile is decided by the exact
-// FP32 predicate on its M x MJ pairs.  Depth-first
-// order yields ascending j-clusters (Sec. II-A), so the (J, mask) list is
-// produced sorted; it is staged per warp (L2 resident) and then encoded:
+// octree without a stack (skip indices), reading nodes in coalesced chunks
+// of 32 staged in shared memory.  Every particle of the super-cluster (1 to
+// 4 per lane) is tested against the node box inflated by the larger of its
+// radius and the node's maximum radius, with monotone round-to-nearest gaps
+// so that no pair accepted by the FP32 predicate can be pruned.  Accepted leaves append
+// their j-clusters (MJ particles each, MJ = M or M / 2: the M x MJ tiles of
+// Sec. II-A / III-A) to a per-warp queue, drained 4 j-clusters at a time:
+// their particles and boxes are staged in shared memory, 4 x 8 (i-cluster,
+// j-cluster) box pairs are tested in one round (one lane each), the i
+// particles refine the candidate i-clusters, and each surviving tile is decided
+// by the exact FP32 predicate on its M x MJ pairs.  Depth-first order yields
+// ascending j-clusters (Sec. II-A), so the (J, mask) list is produced
+// sorted; it is staged per warp (L2 resident) and then encoded:
 // u32 count | u8 masks | nibble blocks of 32 differences (Sec. II-B, the
 // layout of Sec. II-C with w = 32), reserved with one atomicAdd in the list
 // buffer.  Super-clusters whose list exceeds the staging capacity or the
@@ -184,15 +187,22 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
         // i-cluster box of this lane's cluster (lane & 7)
         const float4 ilo = a.clo[s * kSC + (lane & 7)];
         const float4 ihi = a.chi[s * kSC + (lane & 7)];
-        // pruning particles base + lane + 32 t, also staged for the tile tests
+        // pruning particles base + lane + 32 t (dummies moved to infinity,
+        // so they are never near anything), staged as (x, y, z, r) for the
+        // tile tests.  Per-particle tests, not boxes of several particles:
+        // particles adjacent on the curve can lie far apart in sparse
+        // regions, and a box around them would admit far too many nodes.
         float4 qp[NPI];
         float qr[NPI];
         __syncwarp();
 #pragma unroll
         for (int t = 0; t < NPI; ++t) {
-            qp[t] = a.pos[base + lane + 32 * t];
-            qr[t] = __fmul_rn(a.support, qp[t].w);
-            S.ip[lane + 32 * t] = qp[t];
+            const float4 p = a.pos[base + lane + 32 * t];
+            const float r = __fmul_rn(a.support, p.w);
+            S.ip[lane + 32 * t] = make_float4(p.x, p.y, p.z, r);
+            const bool real = p.x == p.x;
+            qp[t] = real ? p : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+            qr[t] = real ? r : 0.f;
         }
 
         uint32_t cnt = 0, tiles = 0, nvis = 0, lvis = 0, jex = 0, ttests = 0, qn = 0;
@@ -208,8 +218,10 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
                 if (grp < nq) {
                     const uint32_t Jl = S.jq[b + grp];
 #pragma unroll
-                    for (uint32_t jl = lane & 7; jl < (uint32_t)MJ; jl += 8)
-                        S.jp[grp * MJ + jl] = a.pos[Jl * MJ + jl];
+                    for (uint32_t jl = lane & 7; jl < (uint32_t)MJ; jl += 8) {
+                        const float4 p = a.pos[Jl * MJ + jl];
+                        S.jp[grp * MJ + jl] = make_float4(p.x, p.y, p.z, __fmul_rn(a.support, p.w));
+                    }
                     const float4 jlo = a.jlo[Jl], jhi = a.jhi[Jl];
                     if ((lane & 7) == 0) {
                         S.jb[2 * grp] = jlo;
@@ -262,18 +274,17 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
                         if (!((cm >> k) & 1u) || ((mask >> k) & 1u)) continue;
                         const uint32_t ii = base + k * M + II;
                         const float4 pik = S.ip[k * M + II];
-                        const float rik = __fmul_rn(a.support, pik.w);
-                        bool hit = false;
 #pragma unroll
-                        for (int t = 0; t < NP; ++t) {
+                        for (int t = 0; t < NP; ++t) {  // stops at the first hit
                             const uint32_t jl = JJ0 + t * JSTEP;
                             const float4 pj = S.jp[q * MJ + jl];
-                            const float rj = __fmul_rn(a.support, pj.w);
                             const float d2 = pair_d2<PER>(pik, pj, box);
-                            const float r = fmaxf(rik, rj);
-                            hit |= (ii != J * MJ + jl) && d2 < __fmul_rn(r, r);
+                            const float r = fmaxf(pik.w, pj.w);
+                            if (__any_sync(0xffffffffu, (ii != J * MJ + jl) && d2 < __fmul_rn(r, r))) {
+                                mask |= 1u << k;
+                                break;
+                            }
                         }
-                        if (__any_sync(0xffffffffu, hit)) mask |= 1u << k;
                     }
                     if (mask) {
                         if (lane == 0 && cnt < a.stage_cap) {
