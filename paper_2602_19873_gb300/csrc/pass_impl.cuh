@@ -97,8 +97,13 @@ constexpr size_t pass_smem_per_warp()
     return (size_t)32 * MJ * (sizeof(float4) + ((KIND == PASS_DENSITY || KIND == PASS_SPH) ? sizeof(float2) : 0));
 }
 
+// Resident blocks per SM the register budget is cut for: the scalar passes
+// fit 80 registers with small spills; the vector passes keep 128.
+template <int KIND>
+constexpr int ps_min_blocks() { return (KIND == PASS_DENSITY || KIND == PASS_COUNT) ? 3 : 2; }
+
 template <int M, int MJ, bool PER, int KIND>
-__global__ void __launch_bounds__(PS_THREADS, 3) k_pass(PassArgs a)
+__global__ void __launch_bounds__(PS_THREADS, ps_min_blocks<KIND>()) k_pass(PassArgs a)
 {
     constexpr int NP = (M * MJ) / 32 > 0 ? (M * MJ) / 32 : 1;
     constexpr int JSTEP = 32 / M;
@@ -196,58 +201,79 @@ __global__ void __launch_bounds__(PS_THREADS, 3) k_pass(PassArgs a)
                 }
             }
             __syncwarp();
+            // one (i-cluster k, j particle) term per lane
+            auto term = [&](int k, const float4 &pj, const float2 &aj, uint32_t jj) {
+                const uint32_t ii = (s * kSC + k) * M + II;
+                // canonical distance decides the pair; the sums use the
+                // accurate vector (identical unless wrapped)
+                const float d2 = pair_d2<PER>(pi[k], pj, box);
+                if constexpr (KIND == PASS_DENSITY) {
+                    if (owner && ii != jj && d2 < ri2[k]) {
+                        const float e2 = PER ? d2_of(pair_dx_acc<PER>(pi[k], pj, box)) : d2;
+                        // |x_i - x_j| = e2 / sqrt(e2); coincident particles give q = 0
+                        const float q = e2 > 0.f ? e2 * rsqrtf(e2) * hinv[k] : 0.f;
+                        acc.b[k] += aj.x * spline_w(q);
+                    }
+                } else if constexpr (KIND == PASS_COUNT) {
+                    if (owner && ii != jj && d2 < ri2[k]) acc.v[k] += 1u;
+                } else if constexpr (KIND == PASS_SPH) {
+                    const float rj = __fmul_rn(a.support, pj.w);
+                    const float rr = fmaxf(ri[k], rj);
+                    if (owner && ii != jj && d2 < __fmul_rn(rr, rr)) {
+                        // a_i -= m_j (c_i gW_i + c_j gW_j) (x_i - x_j) / r
+                        const float3 dv = pair_dx_acc<PER>(pi[k], pj, box);
+                        const float e2 = d2_of(dv);
+                        const float ir = e2 > 0.f ? rsqrtf(e2) : 0.f;  // grad W(0) = 0
+                        const float r = e2 * ir;
+                        const float hji = 1.f / pj.w;
+                        const float gi = spline_dw(r * hinv[k]) * hinv[k] * hinv[k] * hinv[k] * hinv[k];
+                        const float gj = spline_dw(r * hji) * hji * hji * hji * hji;
+                        const float sc = aj.x * (ci[k] * gi + aj.y * gj) * 0.318309886183790672f * ir;
+                        // x_i - x_j = -dv
+                        acc.bx[k] += sc * dv.x;
+                        acc.by[k] += sc * dv.y;
+                        acc.bz[k] += sc * dv.z;
+                    }
+                } else {  // LJ: F_i += 24 eps (2 s^12/r^14 - s^6/r^8)(x_i - x_j)
+                    if (owner && ii != jj && d2 < ri2[k]) {
+                        const float3 dv = pair_dx_acc<PER>(pi[k], pj, box);
+                        const float ir2 = 1.f / d2_of(dv);
+                        const float s2 = a.p1 * a.p1 * ir2;
+                        const float s6 = s2 * s2 * s2;
+                        const float c = 24.f * a.p0 * ir2 * s6 * (2.f * s6 - 1.f);
+                        acc.bx[k] -= c * dv.x;
+                        acc.by[k] -= c * dv.y;
+                        acc.bz[k] -= c * dv.z;
+                    }
+                }
+            };
             for (uint32_t e = 0; e < nb; ++e) {
                 const uint32_t Je = __shfl_sync(0xffffffffu, J, e);
                 const uint32_t me = __shfl_sync(0xffffffffu, mk, e);
+                if constexpr (NP <= 2) {
+                    // the entry's j particles in registers; the NP terms of one
+                    // i-cluster are independent (instruction-level parallelism)
+                    float4 pj[NP];
+                    float2 aj[NP];
 #pragma unroll
-                for (int tt = 0; tt < NP; ++tt) {
-                    const uint32_t jj = Je * MJ + JJ0 + tt * JSTEP;
-                    const float4 pj = sp[e * MJ + JJ0 + tt * JSTEP];
-                    float2 aj = make_float2(0.f, 0.f);
-                    if constexpr (AUX) aj = sa[e * MJ + JJ0 + tt * JSTEP];
+                    for (int tt = 0; tt < NP; ++tt) {
+                        pj[tt] = sp[e * MJ + JJ0 + tt * JSTEP];
+                        aj[tt] = AUX ? sa[e * MJ + JJ0 + tt * JSTEP] : make_float2(0.f, 0.f);
+                    }
 #pragma unroll
                     for (int k = 0; k < kSC; ++k) {
                         if (!((me >> k) & 1u)) continue;
-                        const uint32_t ii = (s * kSC + k) * M + II;
-                        // canonical distance decides the pair; the sums use the
-                        // accurate vector (identical unless wrapped)
-                        const float d2 = pair_d2<PER>(pi[k], pj, box);
-                        if constexpr (KIND == PASS_DENSITY) {
-                            if (owner && ii != jj && d2 < ri2[k]) {
-                                const float3 dv = pair_dx_acc<PER>(pi[k], pj, box);
-                                float q = sqrtf(d2_of(dv)) * hinv[k];
-                                acc.b[k] += aj.x * spline_w(q);
-                            }
-                        } else if constexpr (KIND == PASS_COUNT) {
-                            if (owner && ii != jj && d2 < ri2[k]) acc.v[k] += 1u;
-                        } else if constexpr (KIND == PASS_SPH) {
-                            const float rj = __fmul_rn(a.support, pj.w);
-                            const float rr = fmaxf(ri[k], rj);
-                            if (owner && ii != jj && d2 < __fmul_rn(rr, rr)) {
-                                // a_i -= m_j (c_i gW_i + c_j gW_j) (x_i - x_j) / r
-                                const float3 dv = pair_dx_acc<PER>(pi[k], pj, box);
-                                float r = sqrtf(d2_of(dv));
-                                float hj = pj.w, hji = 1.f / hj;
-                                float gi = spline_dw(r * hinv[k]) * hinv[k] * hinv[k] * hinv[k] * hinv[k];
-                                float gj = spline_dw(r * hji) * hji * hji * hji * hji;
-                                float sc = aj.x * (ci[k] * gi + aj.y * gj) * 0.318309886183790672f / r;
-                                // x_i - x_j = -dv
-                                acc.bx[k] += sc * dv.x;
-                                acc.by[k] += sc * dv.y;
-                                acc.bz[k] += sc * dv.z;
-                            }
-                        } else {  // LJ: F_i += 24 eps (2 s^12/r^14 - s^6/r^8)(x_i - x_j)
-                            if (owner && ii != jj && d2 < ri2[k]) {
-                                const float3 dv = pair_dx_acc<PER>(pi[k], pj, box);
-                                float ir2 = 1.f / d2_of(dv);
-                                float s2 = a.p1 * a.p1 * ir2;
-                                float s6 = s2 * s2 * s2;
-                                float c = 24.f * a.p0 * ir2 * s6 * (2.f * s6 - 1.f);
-                                acc.bx[k] -= c * dv.x;
-                                acc.by[k] -= c * dv.y;
-                                acc.bz[k] -= c * dv.z;
-                            }
-                        }
+#pragma unroll
+                        for (int tt = 0; tt < NP; ++tt) term(k, pj[tt], aj[tt], Je * MJ + JJ0 + tt * JSTEP);
+                    }
+                } else {
+#pragma unroll
+                    for (int tt = 0; tt < NP; ++tt) {
+                        const float4 pj = sp[e * MJ + JJ0 + tt * JSTEP];
+                        const float2 aj = AUX ? sa[e * MJ + JJ0 + tt * JSTEP] : make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int k = 0; k < kSC; ++k)
+                            if ((me >> k) & 1u) term(k, pj, aj, Je * MJ + JJ0 + tt * JSTEP);
                     }
                 }
             }
