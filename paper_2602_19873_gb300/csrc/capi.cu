@@ -108,12 +108,15 @@ struct nl_list {
         leaf_lev, nodeoff, bsum;
     DevBuf nlo, nhi, nrng, nlevel, nparent, nchild, narrive;
     DevBuf stageJ, stageM, list, rec_off, redo, work, aux, status;
+    // half search: upper entries, transposed tuples (+ sort buffers), per super-cluster tables
+    DevBuf uJ, uM, up_off, up_cnt, lower_cnt, seg_off, tkey, tkey_alt, tval, tval_alt, thist;
     DevBuf perm_pad, sys_off, sys_pad, sys_box, sys_root, sys_hcap;
     int32_t nsys = 1;
     uint32_t node_cap = 0;
     const struct nl_mlp *mlp = nullptr;
     DevBuf ml_X, ml_e64, ml_pred, ml_slo, ml_shi;
     int graph_mode = 0;   // build without host reads or allocations (stream capture)
+    int force_full = 0;   // use the full search (sizing the buffers of a graph capture)
     Status *hst = nullptr;
 
     SysTables tables() const
@@ -164,7 +167,9 @@ struct nl_list {
                          &work, &aux, &status, &hx, &hy, &hz, &hh, &hm, &hrho, &perm_pad,
                          &sys_off, &sys_pad, &sys_box, &sys_root, &sys_hcap, &it_hq,
                          &it_hlo, &it_hhi, &it_hs, &it_counts, &it_conv, &it_aflag, &it_alist,
-                         &it_words, &it_tmp, &ml_X, &ml_e64, &ml_pred, &ml_slo, &ml_shi};
+                         &it_words, &it_tmp, &ml_X, &ml_e64, &ml_pred, &ml_slo, &ml_shi,
+                         &uJ, &uM, &up_off, &up_cnt, &lower_cnt, &seg_off, &tkey, &tkey_alt,
+                         &tval, &tval_alt, &thist};
         for (DevBuf *b : all) b->release();
         for (int i = 0; i <= kStages; ++i)
             if (ev[i]) cudaEventDestroy(ev[i]);
@@ -392,10 +397,195 @@ nl_status do_prep(nl_list *nl, const float *x, const float *y, const float *z, c
     return NL_OK;
 }
 
+// Half search (j-clusters = i-clusters): every super-cluster searches only
+// the j-clusters from its own first one on and sends the transposed tiles to
+// the later super-clusters; the tuples are sorted by (target, j-cluster) and
+// each record is assembled from its tuples and its own upper entries.  The
+// records equal those of the full search byte for byte.  Buffer overflows of
+// the upper entries or tuples re-run every super-cluster with buffers of the
+// size the failed run asked for; staging overflows re-run only the
+// super-clusters concerned, as in the full search.
+nl_status do_search_half(nl_list *nl, cudaStream_t s)
+{
+    nl_status st;
+    const nl_params *p = &nl->p;
+    const uint32_t N = (uint32_t)nl->n_prepared, nsc = nl->nsc, ncl = nl->ncl;
+    const int M = p->cluster;
+    Status *dst = nl->status.as<Status>();
+    const size_t search_words = sizeof(Status) - offsetof(Status, ticket);
+    CK(cudaMemsetAsync(&dst->ticket, 0, search_words, s));
+    CK(nl->up_off.ensure((size_t)nsc * 4));
+    CK(nl->up_cnt.ensure((size_t)nsc * 4));
+    CK(nl->lower_cnt.ensure((size_t)nsc * 4));
+    CK(nl->seg_off.ensure((size_t)nsc * 4));
+    CK(cudaMemsetAsync(nl->lower_cnt.p, 0, (size_t)nsc * 4, s));
+    size_t upc = std::max(nl->uM.cap, (size_t)N * 2 + 4096);
+    size_t tuc = std::max(nl->tval.cap / 4, (size_t)N * 2 + 4096);
+    if (const char *e = std::getenv("NLGB_HALF_CAP0")) upc = tuc = std::strtoull(e, nullptr, 10) + 1;
+    CK(nl->uJ.ensure(upc * 4));
+    CK(nl->uM.ensure(upc));
+    CK(nl->tkey.ensure(tuc * 8));
+    CK(nl->tval.ensure(tuc * 4));
+    if (const char *e = std::getenv("NLGB_STAGE_CAP0"))
+        if (!nl->stage_grown) nl->stage_cap = (uint32_t)std::strtoul(e, nullptr, 10);
+    const int tpb = p->threads_per_block ? p->threads_per_block : 256;
+    const int wpb = tpb / 32;
+    const int grid0 = nl->num_sms * (p->blocks_per_sm ? p->blocks_per_sm : kSearchBlocksPerSM);
+    int grid = grid0;
+    size_t slots = (size_t)grid * wpb;
+    CK(nl->stageJ.ensure(slots * nl->stage_cap * 4));
+    CK(nl->stageM.ensure(slots * nl->stage_cap));
+    CK(nl->mark(4, s));
+
+    SearchArgs sa{};
+    sa.pos = nl->pos.as<float4>();
+    sa.clo = nl->clo.as<float4>();
+    sa.chi = nl->chi.as<float4>();
+    sa.mj = M;
+    sa.jlo = sa.clo;
+    sa.jhi = sa.chi;
+    sa.nlo = nl->nlo.as<float4>();
+    sa.nhi = nl->nhi.as<float4>();
+    sa.nrng = nl->nrng.as<int2>();
+    sa.n = N;
+    sa.nsc = nsc;
+    sa.nnodes = nl->node_cap;
+    sa.sys = nl->tables();
+    sa.support = p->support;
+    sa.compress = p->compress;
+    sa.st = dst;
+    sa.rec_off = nl->rec_off.as<uint32_t>();
+    sa.half = 1;
+    sa.ncl = ncl;
+    sa.up_off = nl->up_off.as<uint32_t>();
+    sa.up_cnt = nl->up_cnt.as<uint32_t>();
+    sa.lower_cnt = nl->lower_cnt.as<uint32_t>();
+    sa.seg_off = nl->seg_off.as<uint32_t>();
+
+    unsigned long long nv = 0, lv = 0, jx = 0, tt = 0;
+    const uint32_t *work = nullptr;
+    uint32_t count = nsc;
+    for (int round = 0;; ++round) {
+        if (round >= kMaxRedoRounds)
+            return fail(NL_ERR_CAPACITY, "half search still overflowing after %d rounds", round);
+        sa.stageJ = nl->stageJ.as<uint32_t>();
+        sa.stageM = nl->stageM.as<uint8_t>();
+        sa.stage_cap = nl->stage_cap;
+        sa.uJ = nl->uJ.as<uint32_t>();
+        sa.uM = nl->uM.as<uint8_t>();
+        sa.up_cap = upc;
+        sa.tkey = nl->tkey.as<uint64_t>();
+        sa.tval = nl->tval.as<uint32_t>();
+        sa.tu_cap = tuc;
+        CK(launch_search_ctl(sa, work, count, nl->redo.as<uint32_t>(), M, nl->any_per, grid, tpb, s));
+        st = read_status(nl, s);
+        if (st != NL_OK) return st;
+        nv += nl->hst->node_visits;
+        lv += nl->hst->leaf_visits;
+        jx += nl->hst->j_examined;
+        tt += nl->hst->tile_tests;
+        if (nl->hst->max_count > nl->stage_cap) {
+            nl->stage_cap = nl->hst->max_count + nl->hst->max_count / 4 + 64;
+            nl->stage_grown = 1;
+        }
+        if (nl->hst->half_overflow) {
+            // start over with the sizes the failed run asked for
+            upc = std::max(upc, (size_t)(nl->hst->up_used + nl->hst->up_used / 4 + 4096));
+            tuc = std::max(tuc, (size_t)(nl->hst->tu_used + nl->hst->tu_used / 4 + 4096));
+            CK(nl->uJ.ensure(upc * 4));
+            CK(nl->uM.ensure(upc));
+            CK(nl->tkey.ensure(tuc * 8));
+            CK(nl->tval.ensure(tuc * 4));
+            grid = grid0;
+            slots = (size_t)grid * wpb;
+            CK(nl->stageJ.ensure(slots * nl->stage_cap * 4));
+            CK(nl->stageM.ensure(slots * nl->stage_cap));
+            CK(cudaMemsetAsync(&dst->ticket, 0, search_words, s));
+            CK(cudaMemsetAsync(nl->lower_cnt.p, 0, (size_t)nsc * 4, s));
+            work = nullptr;
+            count = nsc;
+            nv = lv = jx = tt = 0;
+            continue;
+        }
+        const uint32_t nredo = nl->hst->stage_overflow;
+        if (nredo == 0) break;
+        // staging overflow only: re-run the listed super-clusters after growth
+        CK(cudaMemcpyAsync(nl->work.p, nl->redo.p, (size_t)nredo * 4, cudaMemcpyDeviceToDevice, s));
+        work = nl->work.as<uint32_t>();
+        count = nredo;
+        grid = (int)std::min<uint32_t>((uint32_t)grid, (nredo + wpb - 1) / wpb);
+        slots = (size_t)grid * wpb;
+        CK(nl->stageJ.ensure(slots * nl->stage_cap * 4));
+        CK(nl->stageM.ensure(slots * nl->stage_cap));
+        const unsigned long long keep_up = nl->hst->up_used, keep_tu = nl->hst->tu_used;
+        std::memset(&nl->hst->ticket, 0, search_words);
+        nl->hst->up_used = keep_up;
+        nl->hst->tu_used = keep_tu;
+        CK(cudaMemcpyAsync(&dst->ticket, &nl->hst->ticket, search_words, cudaMemcpyHostToDevice, s));
+    }
+    const uint32_t ntu = (uint32_t)nl->hst->tu_used;
+    // sort the tuples by (target super-cluster, j-cluster)
+    int bits = 1;
+    while (bits < 64 && ((unsigned long long)nsc * ncl >> bits) != 0) ++bits;
+    if (ntu > 1) {
+        CK(nl->tkey_alt.ensure((size_t)ntu * 8));
+        CK(nl->tval_alt.ensure((size_t)ntu * 4));
+        CK(nl->thist.ensure(radix_hist_words(ntu) * 4));
+        CK(radix_sort_pairs(nl->tkey.as<uint64_t>(), nl->tval.as<uint32_t>(),
+                            nl->tkey_alt.as<uint64_t>(), nl->tval_alt.as<uint32_t>(), ntu, bits,
+                            nl->thist.as<uint32_t>(), s));
+    }
+    CK(nl->bsum.ensure(scan_bsum_words(nsc) * 4));
+    CK(exclusive_scan_u32(nl->lower_cnt.as<uint32_t>(), nl->seg_off.as<uint32_t>(), nsc,
+                          nl->bsum.as<uint32_t>(), &dst->seg_total, s));
+    // assemble and encode the records
+    size_t est = (size_t)N * (p->compress ? 12 : 48) + 65536;
+    if (const char *e = std::getenv("NLGB_LIST_CAP0")) est = std::strtoull(e, nullptr, 10) + 8;
+    if (nl->list.cap < est) CK(nl->list.ensure(est));
+    for (int round = 0;; ++round) {
+        if (round >= kMaxRedoRounds)
+            return fail(NL_ERR_CAPACITY, "list still overflowing after %d rounds", round);
+        CK(cudaMemsetAsync(&dst->list_used, 0, sizeof(dst->list_used), s));
+        CK(cudaMemsetAsync(&dst->n_entries, 0, sizeof(dst->n_entries), s));
+        CK(cudaMemsetAsync(&dst->n_tiles, 0, sizeof(dst->n_tiles), s));
+        CK(cudaMemsetAsync(&dst->list_overflow, 0, sizeof(dst->list_overflow), s));
+        CK(cudaMemsetAsync(&dst->asm_ticket, 0, sizeof(dst->asm_ticket), s));
+        sa.list = nl->list.as<uint8_t>();
+        sa.list_cap = nl->list.cap - 8;  // 8 bytes of slack behind the last record
+        CK(launch_assemble(sa, grid0, s));
+        st = read_status(nl, s);
+        if (st != NL_OK) return st;
+        if (!nl->hst->list_overflow) break;
+        const size_t need = (size_t)nl->hst->list_used + nl->hst->list_used / 8 + 65536;
+        nl->list.release();
+        CK(nl->list.ensure(need));
+    }
+    CK(nl->mark(5, s));
+    nl->collect(0, 5);
+    nl->n = nl->n_prepared;
+    nl->list_bytes = nl->hst->list_used;
+    nl->n_entries = nl->hst->n_entries;
+    nl->n_tiles = nl->hst->n_tiles;
+    nl->node_visits = nv;
+    nl->leaf_visits = lv;
+    nl->j_examined = jx;
+    nl->tile_tests = tt;
+    return NL_OK;
+}
+
 // Cluster-pair search + encoding over the prepared structures, with redo
 // rounds for overflows.  Sets nl->n on success.
 nl_status do_search(nl_list *nl, cudaStream_t s)
 {
+    {
+        // the half search needs j-clusters = i-clusters and host reads between
+        // its steps (not inside a graph capture); NLGB_SEARCH=full forces the
+        // full search (tests run both)
+        const char *e = std::getenv("NLGB_SEARCH");
+        const bool full = e && std::strcmp(e, "full") == 0;
+        if (!full && !nl->graph_mode && !nl->force_full && jcl(&nl->p) == nl->p.cluster)
+            return do_search_half(nl, s);
+    }
     nl_status st;
     const nl_params *p = &nl->p;
     const uint32_t N = (uint32_t)nl->n_prepared, nsc = nl->nsc;
@@ -1040,7 +1230,10 @@ nl_status nl_graph_create(nl_list *nl, const float *x, const float *y, const flo
     cudaStream_t s = (cudaStream_t)stream;
     if (!s) return fail(NL_ERR_ARG, "graph capture needs a non-default stream");
     // 1. a normal build and pass size every buffer and validate the inputs
+    //    (with the full search, the one a capture records)
+    nl->force_full = 1;
     nl_status st = nl_rebuild_batch(nl, x, y, z, h, nsys, offsets, boxes, p, stream);
+    nl->force_full = 0;
     if (st != NL_OK) return st;
     st = nl_density_pass(nl, m, rho, stream);
     if (st != NL_OK) return st;

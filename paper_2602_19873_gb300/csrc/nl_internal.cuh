@@ -71,6 +71,14 @@ struct Status {
     unsigned long long leaf_visits;
     unsigned long long j_examined;     // j-clusters box-tested against the 8 i-clusters
     unsigned long long tile_tests;     // (i-cluster, j-cluster) tiles decided by the exact predicate
+    // half search (symmetric lists): reservations in the upper-entry and
+    // transposed-tuple buffers (counted even when they do not fit)
+    unsigned long long up_used;
+    unsigned long long tu_used;
+    unsigned int half_overflow;        // some reservation did not fit
+    unsigned int asm_ticket;           // work counter of the record assembly
+    unsigned int seg_total;            // total of the lower-entry scan
+    unsigned int pad2;
 };
 
 // ---------------------------------------------------------------------------
@@ -455,10 +463,32 @@ struct SearchArgs {
     uint32_t *rec_off;
     int compress;
     Status *st;
+    // half search (MJ == M): super-cluster s searches only j-clusters J >= 8s,
+    // keeps them as its upper entries and sends every tile (8s+k, J) with J
+    // beyond its own clusters to super-cluster J/8 as a transposed tuple
+    // (key = (J/8) * ncl + 8s+k, value = bit J%8 of the rows, merged per key)
+    int half;
+    uint32_t ncl;                  // clusters in total (padded)
+    uint32_t *uJ;                  // upper entries (j-cluster, mask)
+    uint8_t *uM;
+    unsigned long long up_cap;
+    uint32_t *up_off, *up_cnt;     // per super-cluster: first upper entry, count
+    uint64_t *tkey;                // transposed tuples
+    uint32_t *tval;
+    unsigned long long tu_cap;
+    uint32_t *lower_cnt;           // per super-cluster: tuples addressed to it
+    const uint32_t *seg_off;       // exclusive scan of lower_cnt (record assembly)
 };
 cudaError_t launch_search_ctl(const SearchArgs &a, const uint32_t *work, uint32_t count,
                               uint32_t *redo, int M, int any_periodic, int grid_blocks,
                               int threads, cudaStream_t s);
+// Record assembly of the half search: the record of super-cluster t is its
+// sorted tuples (lower j-clusters) followed by its upper entries, encoded as
+// by the search.  tkey/tval sorted by key; seg_off from seg_offsets().
+cudaError_t launch_assemble(const SearchArgs &a, int grid_blocks, cudaStream_t s);
+// seg_off[k] = sum of cnt[0..k) over k < n; the total lands in *total.
+cudaError_t exclusive_scan_u32(const uint32_t *cnt, uint32_t *seg_off, uint32_t n, uint32_t *bsum,
+                               uint32_t *total, cudaStream_t s);
 
 enum PassKind { PASS_DENSITY = 0, PASS_COUNT = 1, PASS_SPH = 2, PASS_LJ = 3 };
 struct PassArgs {

@@ -161,6 +161,21 @@ static cudaError_t scan_exclusive(F f, S sink, uint32_t n, const uint32_t *n_dev
     return cudaGetLastError();
 }
 
+struct ArrayVal {
+    const uint32_t *a;
+    __device__ uint32_t operator()(uint32_t k) const { return a[k]; }
+};
+struct ArraySink {
+    uint32_t *o;
+    __device__ void operator()(uint32_t k, uint32_t e, uint32_t) const { o[k] = e; }
+};
+
+cudaError_t exclusive_scan_u32(const uint32_t *cnt, uint32_t *seg_off, uint32_t n, uint32_t *bsum,
+                               uint32_t *total, cudaStream_t s)
+{
+    return scan_exclusive(ArrayVal{cnt}, ArraySink{seg_off}, n, nullptr, bsum, total, s);
+}
+
 // ---------------------------------------------------------------------------
 // Step 1: leaf level of every particle
 // ---------------------------------------------------------------------------

@@ -42,10 +42,12 @@ __device__ __forceinline__ void win_put(uint32_t *win, uint32_t W0, uint32_t p, 
     atomicOr(&win[l >> 3], v << ((l & 7u) * 4u));
 }
 
-// Encode the staged list of one super-cluster.  Returns false when the list
-// buffer is full (nothing written for this super-cluster).
-__device__ bool encode_record(uint32_t cnt, const uint32_t *stJ, const uint8_t *stM,
-                              uint32_t *win, const SearchArgs &a, uint32_t s)
+// Encode the list of one super-cluster: entry t is (getJ(t), getM(t)),
+// ascending in J.  Returns false when the list buffer is full (nothing
+// written for this super-cluster).
+template <class GJ, class GM>
+__device__ bool encode_record(uint32_t cnt, GJ getJ, GM getM, uint32_t *win, const SearchArgs &a,
+                              uint32_t s)
 {
     const unsigned lane = lane_id();
     const unsigned lt = lanemask_lt();
@@ -54,7 +56,7 @@ __device__ bool encode_record(uint32_t cnt, const uint32_t *stJ, const uint8_t *
         uint32_t carry = 0xffffffffu;  // J_{-1} = -1
         for (uint32_t b0 = 0; b0 < cnt; b0 += 32) {
             uint32_t t = b0 + lane;
-            uint32_t J = t < cnt ? stJ[t] : 0u;
+            uint32_t J = t < cnt ? getJ(t) : 0u;
             uint32_t prev = __shfl_up_sync(0xffffffffu, J, 1);
             if (lane == 0) prev = carry;
             uint32_t d = t < cnt ? J - prev : 1u;
@@ -85,13 +87,13 @@ __device__ bool encode_record(uint32_t cnt, const uint32_t *stJ, const uint8_t *
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             uint32_t t = 4 * w + q;
-            if (t < cnt) v |= (uint32_t)stM[t] << (8 * q);
+            if (t < cnt) v |= (getM(t) & 0xffu) << (8 * q);
         }
         rec[1 + w] = v;
     }
     uint32_t *body = rec + 1 + mask_words;
     if (!a.compress) {
-        for (uint32_t t = lane; t < cnt; t += 32) body[t] = stJ[t];
+        for (uint32_t t = lane; t < cnt; t += 32) body[t] = getJ(t);
         return true;
     }
     win[lane] = 0u;
@@ -101,7 +103,7 @@ __device__ bool encode_record(uint32_t cnt, const uint32_t *stJ, const uint8_t *
     for (uint32_t b0 = 0; b0 < cnt; b0 += 32) {
         uint32_t t = b0 + lane;
         bool valid = t < cnt;
-        uint32_t J = valid ? stJ[t] : 0u;
+        uint32_t J = valid ? getJ(t) : 0u;
         uint32_t prev = __shfl_up_sync(0xffffffffu, J, 1);
         if (lane == 0) prev = carry;
         uint32_t d = valid ? J - prev : 1u;
@@ -137,6 +139,99 @@ __device__ bool encode_record(uint32_t cnt, const uint32_t *stJ, const uint8_t *
     return true;
 }
 
+// Half search output of super-cluster s (MJ == M): the staged upper entries
+// (J >= 8s, ascending) go to the upper buffer, and every tile (8s+k, J) with
+// J beyond the own clusters becomes part of a transposed tuple for
+// super-cluster t = J/8: key t * ncl + (8s+k), value = the bits J%8 of all
+// such J with the same t (entries of one t are consecutive, at most 8 of
+// them, so a group spans at most two 32-entry chunks and is carried over).
+// Returns false when a buffer was too small (the reservations still count,
+// so the host learns the sizes it needs).
+__device__ bool half_output(uint32_t cnt, const uint32_t *stJ, const uint8_t *stM,
+                            const SearchArgs &a, uint32_t s)
+{
+    const unsigned lane = lane_id();
+    constexpr uint32_t NONE = 0xffffffffu;
+    unsigned long long off = 0;
+    if (lane == 0) off = atomicAdd(&a.st->up_used, (unsigned long long)cnt);
+    off = __shfl_sync(0xffffffffu, off, 0);
+    if (off + cnt > a.up_cap) {
+        if (lane == 0) atomicExch(&a.st->half_overflow, 1u);
+        return false;
+    }
+    for (uint32_t t = lane; t < cnt; t += 32) {
+        a.uJ[off + t] = stJ[t];
+        a.uM[off + t] = stM[t];
+    }
+    if (lane == 0) {
+        a.up_off[s] = (uint32_t)off;
+        a.up_cnt[s] = cnt;
+    }
+    const uint32_t own_end = (s + 1) * kSC;  // first cluster after the own ones
+    const uint32_t i0 = s * kSC;
+    bool ok = true;
+    uint32_t carry_t = NONE, carry[kSC];
+#pragma unroll
+    for (int k = 0; k < kSC; ++k) carry[k] = 0u;
+    // reserve and write n tuples of group t from this lane
+    auto emit = [&](bool on, uint32_t t, const uint32_t *rows) {
+        uint32_t nrow = 0;
+#pragma unroll
+        for (int k = 0; k < kSC; ++k) nrow += (on && rows[k]) ? 1u : 0u;
+        const uint32_t incl = warp_incl_scan(nrow);
+        const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        if (tot == 0) return;
+        unsigned long long tb = 0;
+        if (lane == 0) tb = atomicAdd(&a.st->tu_used, (unsigned long long)tot);
+        tb = __shfl_sync(0xffffffffu, tb, 0);
+        if (tb + tot > a.tu_cap) {
+            ok = false;
+            return;
+        }
+        if (nrow) {
+            unsigned long long w = tb + incl - nrow;
+#pragma unroll
+            for (int k = 0; k < kSC; ++k)
+                if (rows[k]) {
+                    a.tkey[w] = (uint64_t)t * a.ncl + (i0 + k);
+                    a.tval[w] = rows[k];
+                    ++w;
+                }
+            atomicAdd(&a.lower_cnt[t], nrow);
+        }
+    };
+    for (uint32_t b0 = 0; b0 < cnt; b0 += 32) {
+        const uint32_t e = b0 + lane;
+        const uint32_t J = e < cnt ? stJ[e] : 0u;
+        const bool valid = e < cnt && J >= own_end;
+        const uint32_t m = valid ? (uint32_t)stM[e] : 0u;
+        const uint32_t t = valid ? J / kSC : NONE;
+        // a carried group that does not continue here is complete
+        if (carry_t != NONE && __shfl_sync(0xffffffffu, t, 0) != carry_t) {
+            emit(lane == 0, carry_t, carry);
+            carry_t = NONE;
+        }
+        const uint32_t gm = __match_any_sync(0xffffffffu, t);
+        uint32_t rows[kSC];
+#pragma unroll
+        for (int k = 0; k < kSC; ++k) {
+            rows[k] = __reduce_or_sync(gm, ((m >> k) & 1u) << (J & 7u));
+            if (valid && t == carry_t) rows[k] |= carry[k];
+        }
+        // the group of the chunk's last entry may continue in the next chunk
+        const uint32_t t31 = __shfl_sync(0xffffffffu, t, 31);
+        const bool more = b0 + 32 < cnt;
+        const bool hold = more && t31 != NONE && t == t31;
+#pragma unroll
+        for (int k = 0; k < kSC; ++k) carry[k] = __shfl_sync(0xffffffffu, rows[k], 31);
+        carry_t = (more && t31 != NONE) ? t31 : NONE;
+        emit(valid && lane == (uint32_t)(__ffs(gm) - 1) && !hold, t, rows);
+    }
+    if (carry_t != NONE) emit(lane == 0, carry_t, carry);
+    if (!ok && lane == 0) atomicExch(&a.st->half_overflow, 1u);
+    return ok;
+}
+
 // Shared memory of one warp: the super-cluster's particles, a chunk of 32
 // consecutive octree nodes, the queue of candidate j-clusters, the particles
 // and boxes of the 4 j-clusters being tested, and the encoder window.
@@ -151,7 +246,7 @@ struct SearchSmem {
     uint32_t win[WIN_WORDS];
 };
 
-template <int M, int MJ, bool PER>
+template <int M, int MJ, bool PER, bool HALF>
 __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCtl ctl)
 {
     constexpr int NP = (M * MJ) / 32 > 0 ? (M * MJ) / 32 : 1;  // pairs per lane per tile
@@ -206,7 +301,8 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
         }
 
         uint32_t cnt = 0, tiles = 0, nvis = 0, lvis = 0, jex = 0, ttests = 0, qn = 0;
-        int lastJ = -1;
+        // the half search takes only j-clusters from its own first one on
+        int lastJ = HALF ? (int)(base / MJ) - 1 : -1;
 
         // Test the queued j-clusters, 4 per round, and stage the hits.
         auto flush = [&]() {
@@ -316,10 +412,14 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
                 }
                 __syncwarp();
             }
-            ++nvis;
             const float4 nlo = S.nlo[v - cb];
             const float4 nhi = S.nhi[v - cb];
             const uint32_t skip = (uint32_t)__float_as_int(nhi.w);
+            if (HALF && (uint32_t)S.nrg[v - cb].y <= base) {  // wholly before the own particles
+                v = skip > v ? skip : v + 1;
+                continue;
+            }
+            ++nvis;
             bool near = false;
 #pragma unroll
             for (int t = 0; t < NPI; ++t) near |= point_near<PER>(qp[t], qr[t], nlo, nhi, box);
@@ -353,19 +453,27 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
         }
         flush();
         __syncwarp();
-        bool ok = cnt <= a.stage_cap;
-        if (!ok) {
+        const bool staged = cnt <= a.stage_cap;
+        bool ok = staged;
+        if (!staged) {
             if (lane == 0) atomicMax(&a.st->max_count, cnt);
+        } else if constexpr (HALF) {
+            // a buffer overflow here makes the host re-run every super-cluster
+            ok = half_output(cnt, stJ, stM, a, s);
         } else {
-            ok = encode_record(cnt, stJ, stM, S.win, a, s);
+            ok = encode_record(
+                cnt, [&](uint32_t t) { return stJ[t]; },
+                [&](uint32_t t) { return (uint32_t)stM[t]; }, S.win, a, s);
             if (!ok && lane == 0) atomicExch(&a.st->list_overflow, 1u);
         }
         if (lane == 0) {
             if (!ok) {
-                uint32_t r = atomicAdd(&a.st->stage_overflow, 1u);
-                ctl.redo[r] = s;
+                if (!HALF || !staged) {
+                    uint32_t r = atomicAdd(&a.st->stage_overflow, 1u);
+                    ctl.redo[r] = s;
+                }
                 a.rec_off[s] = kBadRecord;
-            } else {
+            } else if (!HALF) {
                 atomicAdd(&a.st->n_entries, (unsigned long long)cnt);
                 atomicAdd(&a.st->n_tiles, (unsigned long long)tiles);
             }
@@ -377,7 +485,7 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
     }
 }
 
-template <int M, int MJ>
+template <int M, int MJ, bool HALF>
 static void launch_m(const SearchArgs &a, const SearchCtl &c, int per, int grid, int threads,
                      cudaStream_t s)
 {
@@ -386,15 +494,15 @@ static void launch_m(const SearchArgs &a, const SearchCtl &c, int per, int grid,
     static bool attr[2] = {false, false};
     if (!attr[per ? 1 : 0]) {
         if (per)
-            cudaFuncSetAttribute(k_search<M, MJ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+            cudaFuncSetAttribute(k_search<M, MJ, true, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
         else
-            cudaFuncSetAttribute(k_search<M, MJ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+            cudaFuncSetAttribute(k_search<M, MJ, false, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
         attr[per ? 1 : 0] = true;
     }
     if (per)
-        k_search<M, MJ, true><<<grid, threads, smem, s>>>(a, c);
+        k_search<M, MJ, true, HALF><<<grid, threads, smem, s>>>(a, c);
     else
-        k_search<M, MJ, false><<<grid, threads, smem, s>>>(a, c);
+        k_search<M, MJ, false, HALF><<<grid, threads, smem, s>>>(a, c);
 }
 
 cudaError_t launch_search_ctl(const SearchArgs &a, const uint32_t *work, uint32_t count,
@@ -403,14 +511,70 @@ cudaError_t launch_search_ctl(const SearchArgs &a, const uint32_t *work, uint32_
 {
     SearchCtl c{work, count, redo};
     if (threads != 128 && threads != SR_THREADS) return cudaErrorInvalidValue;
+    if (a.half && a.mj != M) return cudaErrorInvalidValue;  // needs j-clusters = i-clusters
     switch (M * 100 + a.mj) {
-    case 404: launch_m<4, 4>(a, c, any_periodic, grid, threads, s); break;
-    case 808: launch_m<8, 8>(a, c, any_periodic, grid, threads, s); break;
-    case 804: launch_m<8, 4>(a, c, any_periodic, grid, threads, s); break;
-    case 1616: launch_m<16, 16>(a, c, any_periodic, grid, threads, s); break;
-    case 1608: launch_m<16, 8>(a, c, any_periodic, grid, threads, s); break;
+    case 404:
+        if (a.half) launch_m<4, 4, true>(a, c, any_periodic, grid, threads, s);
+        else launch_m<4, 4, false>(a, c, any_periodic, grid, threads, s);
+        break;
+    case 808:
+        if (a.half) launch_m<8, 8, true>(a, c, any_periodic, grid, threads, s);
+        else launch_m<8, 8, false>(a, c, any_periodic, grid, threads, s);
+        break;
+    case 804: launch_m<8, 4, false>(a, c, any_periodic, grid, threads, s); break;
+    case 1616:
+        if (a.half) launch_m<16, 16, true>(a, c, any_periodic, grid, threads, s);
+        else launch_m<16, 16, false>(a, c, any_periodic, grid, threads, s);
+        break;
+    case 1608: launch_m<16, 8, false>(a, c, any_periodic, grid, threads, s); break;
     default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+// Record assembly of the half search: one warp per super-cluster t.  Its
+// record is the sorted tuples addressed to it (j-clusters below its own
+// clusters; keys t * ncl + J, values the mask bits) followed by its upper
+// entries, encoded exactly like a record of the full search.
+__global__ void __launch_bounds__(SR_THREADS) k_assemble(SearchArgs a)
+{
+    __shared__ uint32_t wins[SR_WARPS][WIN_WORDS];
+    const unsigned lane = lane_id();
+    uint32_t *win = wins[threadIdx.x >> 5];
+    for (;;) {
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(&a.st->asm_ticket, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= a.nsc) break;
+        const uint32_t lc = a.lower_cnt[t], so = a.seg_off[t];
+        const uint32_t uc = a.up_cnt[t], uo = a.up_off[t];
+        const uint32_t cnt = lc + uc;
+        const uint64_t kb = (uint64_t)t * a.ncl;
+        auto getJ = [&](uint32_t i) -> uint32_t {
+            return i < lc ? (uint32_t)(a.tkey[so + i] - kb) : a.uJ[uo + (i - lc)];
+        };
+        auto getM = [&](uint32_t i) -> uint32_t {
+            return i < lc ? a.tval[so + i] : (uint32_t)a.uM[uo + (i - lc)];
+        };
+        const bool ok = encode_record(cnt, getJ, getM, win, a, t);
+        uint32_t tiles = 0;
+        for (uint32_t i = lane; i < cnt; i += 32) tiles += __popc(getM(i));
+        tiles = warp_sum(tiles);
+        if (lane == 0) {
+            if (!ok) {
+                atomicExch(&a.st->list_overflow, 1u);
+                a.rec_off[t] = kBadRecord;
+            } else {
+                atomicAdd(&a.st->n_entries, (unsigned long long)cnt);
+                atomicAdd(&a.st->n_tiles, (unsigned long long)tiles);
+            }
+        }
+    }
+}
+
+cudaError_t launch_assemble(const SearchArgs &a, int grid, cudaStream_t s)
+{
+    k_assemble<<<grid, SR_THREADS, 0, s>>>(a);
     return cudaGetLastError();
 }
 

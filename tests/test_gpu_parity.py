@@ -312,3 +312,48 @@ def test_stage_times_before_and_after_a_pass():
     st = L.stage_times()
     assert st["pass"] > 0
     L.free()
+
+
+@pytest.mark.parametrize("name", ["uniform", "plummer"])
+@pytest.mark.parametrize("cluster", [4, 8, 16])
+def test_full_and_half_search_give_the_same_records(cases, monkeypatch, name, cluster):
+    """With j-clusters = i-clusters the default search visits only j-clusters
+    from the own super-cluster on and completes the records by transposition;
+    the full search must produce the same bytes (both equal the oracle)."""
+    d, o, (g_off, g_idx, p_off, p_idx) = cases[name]
+    n = len(o["xs"])
+    monkeypatch.setenv("NLGB_SEARCH", "full")
+    L, t = gpu_build(d, cluster=cluster)
+    nsc = L.sizes()["n_superclusters"]
+    total, so, J, m = compare_records(L, o, d, cluster, 1, np.arange(nsc), np.arange(n), p_off, p_idx)
+    assert L.sizes()["list_bytes"] == total
+    full = L.sizes()
+    L.free()
+    monkeypatch.delenv("NLGB_SEARCH")
+    L, t = gpu_build(d, cluster=cluster)
+    compare_records(L, o, d, cluster, 1, np.arange(nsc), np.arange(n), p_off, p_idx)
+    half = L.sizes()
+    assert half["list_bytes"] == full["list_bytes"]
+    assert half["n_entries"] == full["n_entries"] and half["n_tiles"] == full["n_tiles"]
+    assert half["tile_tests"] < full["tile_tests"]
+    L.free()
+
+
+def test_half_search_buffer_growth_keeps_records_exact(cases, monkeypatch):
+    """Tiny upper-entry / tuple buffers force the re-run of every
+    super-cluster, tiny staging the partial re-runs, a tiny list the
+    re-assembly; the records stay byte-exact."""
+    d, o, (g_off, g_idx, p_off, p_idx) = cases["evrard"]
+    monkeypatch.setenv("NLGB_HALF_CAP0", "1000")
+    monkeypatch.setenv("NLGB_STAGE_CAP0", "40")
+    monkeypatch.setenv("NLGB_LIST_CAP0", "20000")
+    L, t = gpu_build(d)
+    n = len(o["xs"])
+    nsc = L.sizes()["n_superclusters"]
+    total, so, J, m = compare_records(L, o, d, 8, 1, np.arange(nsc), np.arange(n), p_off, p_idx)
+    assert L.sizes()["list_bytes"] == total
+    rho = gpu_density(L, t, n)[o["perm"]]
+    want = orc.density(o["xs"], o["ys"], o["zs"], o["hs"], o["ms"], d["box"], g_off, g_idx,
+                       np.arange(n))
+    assert (np.abs(rho - want) / want).max() <= DENSITY_RTOL
+    L.free()
