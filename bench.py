@@ -99,6 +99,23 @@ def dist_init():
     return ws, rank, local
 
 
+def launches_per_step(sizes, batched):
+    """Kernels of one build + density step (graph replay when batched): keys,
+    radix sort (8 passes x 3, a 9th by system in batches), permute, octree
+    (10), search, and for the half search the tuple sort (3 per 8 key bits,
+    plus the fill of unused slots in a graph), the lower-entry scan (3) and
+    the record assembly; then the pass input gather and the pass."""
+    sort_passes = 9 if batched else 8
+    n = 1 + 3 * sort_passes + 1 + 10 + 1
+    if sizes["j_cluster"] == sizes["cluster"]:
+        nsc = sizes["n_superclusters"]
+        bits = 1
+        while bits < 64 and (nsc * 8 * nsc) >> bits:
+            bits += 1
+        n += 3 * ((bits + 7) // 8) + 3 + 1 + (1 if batched else 0)
+    return n + 2
+
+
 def workload(seed, n=N_FULL):
     from paper_2602_19873_gb300 import workloads as wl
     return wl.cached(wl.plummer, "plummer64_%d_%d" % (n, seed), n, n_spheres=64, seed=seed)
@@ -305,7 +322,7 @@ def run_native(args):
         "gpu_launches": None,
         "clocks": clk,
     }
-    out["gpu_launches"] = args.steps * (1 + 3 * 8 + 1 + 10 + 1 + 2)
+    out["gpu_launches"] = args.steps * launches_per_step(sizes, False)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_sample)
     if rank == 0:
@@ -394,7 +411,7 @@ def run_batched(args):
                     "computed_pairs": sizes["n_tiles"] * best.cluster * sizes["j_cluster"]},
            "per_system_max_rel_density_err": worst,
            "per_system_error_sample": [int(len(systems[k]["x"])) for k in sample],
-           "gpu_launches": args.steps * (1 + 3 * 9 + 1 + 10 + 1 + 2), "clocks": clk}
+           "gpu_launches": args.steps * launches_per_step(sizes, True), "clocks": clk}
     if rank == 0:
         print(json.dumps(out))
 
@@ -473,7 +490,7 @@ def main():
     ap.add_argument("--reuse-h", action="store_true",
                     help="reuse converged h cached by an earlier run with the same n")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--leaf-bucket", type=int, default=64,
+    ap.add_argument("--leaf-bucket", type=int, default=256,
                     help="octree leaf capacity of the single-system bench")
     ap.add_argument("--tile", default="8x8", choices=["8x8", "8x4", "16x8", "16x16", "4x4"],
                     help="i-cluster x j-cluster size of the single-system bench")
