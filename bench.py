@@ -32,6 +32,11 @@ WORKLOAD = "plummer64_16m"
 N_FULL = 1 << 24
 ALU_OPS_PER_PAIR_SEARCH = 9      # predicate: 3 sub, 3 mul, 2 add, 1 compare (non-periodic)
 ALGO_BYTES_PER_PARTICLE = 145    # keygen 20 + sort 24 + permute 49 + octree 2 + search 19 + density 31
+# DRAM bytes (read + write) of one k_search launch per particle, from an ncu
+# capture of the half search (8x8 clusters, leaf bucket 256) on this generator
+# at 2^21 particles: 45.1 MB + 13.2 MB; scaled by the particle count (the
+# traffic grows with the particles).  Valid for that kernel version only.
+SEARCH_DRAM_BYTES_PER_PARTICLE = 58.3e6 / 2097152
 
 
 def peaks():
@@ -296,7 +301,9 @@ def run_native(args):
         "roofline": {"bound": "alu", "kernel": "k_search (cluster-pair search + encode)",
                      "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                      "peak_kind": "FP32 lanes x max SM clock (152 SMs x 128 x %.0f MHz)" % sm_max,
-                     "frac": achieved / alu_peak, "traffic": None,
+                     "frac": achieved / alu_peak,
+                     "traffic": (SEARCH_DRAM_BYTES_PER_PARTICLE * n
+                                 if (M, MJ) == (8, 8) and params.leaf_bucket == 256 else None),
                      "algorithmic": "%d FP32 ops per computed pair, %d computed pairs" % (
                          ALU_OPS_PER_PAIR_SEARCH, pairs)},
         "hbm_step": {"achieved_gbs": step_bytes / (ms * 1e-3) / 1e9, "peak_gbs": hbm,

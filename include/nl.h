@@ -70,7 +70,7 @@ typedef struct {
     int32_t cluster;      /* particles per i-cluster M: 4, 8 or 16; super-cluster = 8 i-clusters */
     float support;        /* interaction radius r_i = support * h_i (2 for the cubic spline) */
     int32_t compress;     /* 1: nibble codec (Sec. II-B); 0: raw u32 cluster indices */
-    int32_t leaf_bucket;  /* octree leaf capacity B in particles, 8..1024 (default 64) */
+    int32_t leaf_bucket;  /* octree leaf capacity B in particles, 8..1024 (default 256) */
     int32_t threads_per_block; /* search / pass block shape: 128 or 256 threads (0 = 256) */
     int32_t blocks_per_sm;     /* persistent grids: blocks per SM, 1..8 (0 = 3 search, 4 pass) */
     int32_t j_cluster;    /* particles per j-cluster MJ: 0 (= M), M, or M / 2 when M >= 8;
@@ -78,7 +78,7 @@ typedef struct {
                              NVIDIA choice).  Stored list indices count j-clusters. */
 } nl_params;
 
-/* Fills p with {NL_KEY_HILBERT, 8, 2.0f, 1, 64, 0, 0, 0}. */
+/* Fills p with {NL_KEY_HILBERT, 8, 2.0f, 1, 256, 0, 0, 0}. */
 void nl_default_params(nl_params *p);
 
 typedef struct nl_list nl_list; /* opaque; owns all of its device memory */
@@ -183,8 +183,10 @@ nl_status nl_density_from_host(nl_list *nl, const float *x, const float *y, cons
  * CUDA events on their stream around each stage; nl_get_stage_times writes
  * the durations in milliseconds of the most recent build / pass to ms[0..):
  * 0 keys+validation, 1 radix sort, 2 permute+cluster boxes, 3 octree,
- * 4 cluster-pair search+encode, 5 pass input gather, 6 pass kernel.
- * *count receives the number of stages (7).  Synchronises the device. */
+ * 4 cluster-pair search (+ encoding in the full search), 5 record assembly
+ * of the half search (tuple sort, scan, encoding; 0 for the full search),
+ * 6 pass input gather, 7 pass kernel.
+ * *count receives the number of stages (8).  Synchronises the device. */
 nl_status nl_set_profiling(nl_list *nl, int32_t on);
 nl_status nl_get_stage_times(const nl_list *nl, float *ms, int32_t cap, int32_t *count);
 

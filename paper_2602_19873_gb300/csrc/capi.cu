@@ -116,7 +116,7 @@ struct nl_list {
     const struct nl_mlp *mlp = nullptr;
     DevBuf ml_X, ml_e64, ml_pred, ml_slo, ml_shi;
     int graph_mode = 0;   // build without host reads or allocations (stream capture)
-    int force_full = 0;   // use the full search (sizing the buffers of a graph capture)
+    size_t graph_up_cap = 0, graph_tu_cap = 0;  // half search capacities of a capture
     Status *hst = nullptr;
 
     SysTables tables() const
@@ -130,7 +130,7 @@ struct nl_list {
                          nparent.as<int32_t>(), nchild.as<uint32_t>(), narrive.as<uint32_t>()};
     }
     // stage timing (CUDA events on the launching stream)
-    static constexpr int kStages = 7;
+    static constexpr int kStages = 8;
     int profiling = 0;
     cudaEvent_t ev[kStages + 1] = {};
     float stage_ms[kStages] = {};
@@ -414,27 +414,30 @@ nl_status do_search_half(nl_list *nl, cudaStream_t s)
     Status *dst = nl->status.as<Status>();
     const size_t search_words = sizeof(Status) - offsetof(Status, ticket);
     CK(cudaMemsetAsync(&dst->ticket, 0, search_words, s));
-    CK(nl->up_off.ensure((size_t)nsc * 4));
-    CK(nl->up_cnt.ensure((size_t)nsc * 4));
-    CK(nl->lower_cnt.ensure((size_t)nsc * 4));
-    CK(nl->seg_off.ensure((size_t)nsc * 4));
-    CK(cudaMemsetAsync(nl->lower_cnt.p, 0, (size_t)nsc * 4, s));
-    size_t upc = std::max(nl->uM.cap, (size_t)N * 2 + 4096);
-    size_t tuc = std::max(nl->tval.cap / 4, (size_t)N * 2 + 4096);
-    if (const char *e = std::getenv("NLGB_HALF_CAP0")) upc = tuc = std::strtoull(e, nullptr, 10) + 1;
-    CK(nl->uJ.ensure(upc * 4));
-    CK(nl->uM.ensure(upc));
-    CK(nl->tkey.ensure(tuc * 8));
-    CK(nl->tval.ensure(tuc * 4));
-    if (const char *e = std::getenv("NLGB_STAGE_CAP0"))
-        if (!nl->stage_grown) nl->stage_cap = (uint32_t)std::strtoul(e, nullptr, 10);
+    size_t upc = 0, tuc = 0;
     const int tpb = p->threads_per_block ? p->threads_per_block : 256;
     const int wpb = tpb / 32;
     const int grid0 = nl->num_sms * (p->blocks_per_sm ? p->blocks_per_sm : kSearchBlocksPerSM);
     int grid = grid0;
     size_t slots = (size_t)grid * wpb;
-    CK(nl->stageJ.ensure(slots * nl->stage_cap * 4));
-    CK(nl->stageM.ensure(slots * nl->stage_cap));
+    if (!nl->graph_mode) {
+        CK(nl->up_off.ensure((size_t)nsc * 4));
+        CK(nl->up_cnt.ensure((size_t)nsc * 4));
+        CK(nl->lower_cnt.ensure((size_t)nsc * 4));
+        CK(nl->seg_off.ensure((size_t)nsc * 4));
+        upc = std::max(nl->uM.cap, (size_t)N * 2 + 4096);
+        tuc = std::max(nl->tval.cap / 4, (size_t)N * 2 + 4096);
+        if (const char *e = std::getenv("NLGB_HALF_CAP0")) upc = tuc = std::strtoull(e, nullptr, 10) + 1;
+        CK(nl->uJ.ensure(upc * 4));
+        CK(nl->uM.ensure(upc));
+        CK(nl->tkey.ensure(tuc * 8));
+        CK(nl->tval.ensure(tuc * 4));
+        if (const char *e = std::getenv("NLGB_STAGE_CAP0"))
+            if (!nl->stage_grown) nl->stage_cap = (uint32_t)std::strtoul(e, nullptr, 10);
+        CK(nl->stageJ.ensure(slots * nl->stage_cap * 4));
+        CK(nl->stageM.ensure(slots * nl->stage_cap));
+    }
+    CK(cudaMemsetAsync(nl->lower_cnt.p, 0, (size_t)nsc * 4, s));
     CK(nl->mark(4, s));
 
     SearchArgs sa{};
@@ -461,6 +464,36 @@ nl_status do_search_half(nl_list *nl, cudaStream_t s)
     sa.up_cnt = nl->up_cnt.as<uint32_t>();
     sa.lower_cnt = nl->lower_cnt.as<uint32_t>();
     sa.seg_off = nl->seg_off.as<uint32_t>();
+
+    int bits = 1;
+    while (bits < 64 && ((unsigned long long)nsc * ncl >> bits) != 0) ++bits;
+    if (nl->graph_mode) {
+        // one pass with the capacities reserved before the capture; the sort
+        // covers the whole tuple capacity (unused slots hold the largest key)
+        // and overflows are reported by nl_graph_check
+        const size_t gcap = nl->graph_tu_cap;
+        sa.stageJ = nl->stageJ.as<uint32_t>();
+        sa.stageM = nl->stageM.as<uint8_t>();
+        sa.stage_cap = nl->stage_cap;
+        sa.uJ = nl->uJ.as<uint32_t>();
+        sa.uM = nl->uM.as<uint8_t>();
+        sa.up_cap = nl->graph_up_cap;
+        sa.tkey = nl->tkey.as<uint64_t>();
+        sa.tval = nl->tval.as<uint32_t>();
+        sa.tu_cap = gcap;
+        sa.list = nl->list.as<uint8_t>();
+        sa.list_cap = nl->list.cap - 8;
+        CK(launch_search_ctl(sa, nullptr, nsc, nl->redo.as<uint32_t>(), M, nl->any_per, grid0, tpb, s));
+        CK(launch_fill_keys(nl->tkey.as<uint64_t>(), (uint32_t)gcap, &dst->tu_used,
+                            bits >= 64 ? ~0ull : (1ull << bits) - 1ull, s));
+        CK(radix_sort_pairs(nl->tkey.as<uint64_t>(), nl->tval.as<uint32_t>(),
+                            nl->tkey_alt.as<uint64_t>(), nl->tval_alt.as<uint32_t>(),
+                            (uint32_t)gcap, bits, nl->thist.as<uint32_t>(), s));
+        CK(exclusive_scan_u32(nl->lower_cnt.as<uint32_t>(), nl->seg_off.as<uint32_t>(), nsc,
+                              nl->bsum.as<uint32_t>(), &dst->seg_total, s));
+        CK(launch_assemble(sa, grid0, s));
+        return NL_OK;
+    }
 
     unsigned long long nv = 0, lv = 0, jx = 0, tt = 0;
     const uint32_t *work = nullptr;
@@ -524,9 +557,8 @@ nl_status do_search_half(nl_list *nl, cudaStream_t s)
         CK(cudaMemcpyAsync(&dst->ticket, &nl->hst->ticket, search_words, cudaMemcpyHostToDevice, s));
     }
     const uint32_t ntu = (uint32_t)nl->hst->tu_used;
+    CK(nl->mark(5, s));
     // sort the tuples by (target super-cluster, j-cluster)
-    int bits = 1;
-    while (bits < 64 && ((unsigned long long)nsc * ncl >> bits) != 0) ++bits;
     if (ntu > 1) {
         CK(nl->tkey_alt.ensure((size_t)ntu * 8));
         CK(nl->tval_alt.ensure((size_t)ntu * 4));
@@ -560,8 +592,8 @@ nl_status do_search_half(nl_list *nl, cudaStream_t s)
         nl->list.release();
         CK(nl->list.ensure(need));
     }
-    CK(nl->mark(5, s));
-    nl->collect(0, 5);
+    CK(nl->mark(6, s));
+    nl->collect(0, 6);
     nl->n = nl->n_prepared;
     nl->list_bytes = nl->hst->list_used;
     nl->n_entries = nl->hst->n_entries;
@@ -578,13 +610,11 @@ nl_status do_search_half(nl_list *nl, cudaStream_t s)
 nl_status do_search(nl_list *nl, cudaStream_t s)
 {
     {
-        // the half search needs j-clusters = i-clusters and host reads between
-        // its steps (not inside a graph capture); NLGB_SEARCH=full forces the
-        // full search (tests run both)
+        // the half search needs j-clusters = i-clusters; NLGB_SEARCH=full
+        // forces the full search (tests run both)
         const char *e = std::getenv("NLGB_SEARCH");
         const bool full = e && std::strcmp(e, "full") == 0;
-        if (!full && !nl->graph_mode && !nl->force_full && jcl(&nl->p) == nl->p.cluster)
-            return do_search_half(nl, s);
+        if (!full && jcl(&nl->p) == nl->p.cluster) return do_search_half(nl, s);
     }
     nl_status st;
     const nl_params *p = &nl->p;
@@ -683,7 +713,8 @@ nl_status do_search(nl_list *nl, cudaStream_t s)
         CK(cudaMemcpyAsync(&dst->ticket, &nl->hst->ticket, search_words, cudaMemcpyHostToDevice, s));
     }
     CK(nl->mark(5, s));
-    nl->collect(0, 5);
+    CK(nl->mark(6, s));  // the full search has no assembly stage
+    nl->collect(0, 6);
     nl->n = nl->n_prepared;
     nl->list_bytes = used;
     nl->n_entries = entries;
@@ -740,7 +771,7 @@ void nl_default_params(nl_params *p)
     p->cluster = 8;
     p->support = 2.0f;
     p->compress = 1;
-    p->leaf_bucket = 64;
+    p->leaf_bucket = 256;
     p->threads_per_block = 0;
     p->blocks_per_sm = 0;
     p->j_cluster = 0;
@@ -828,9 +859,9 @@ nl_status nl_get_stage_times(const nl_list *cnl, float *ms, int32_t cap, int32_t
     if (!cnl) return fail(NL_ERR_ARG, "list is NULL");
     nl_list *nl = const_cast<nl_list *>(cnl);
     if (nl->profiling && nl->pass_timed) {
-        CK(cudaEventSynchronize(nl->ev[7]));
-        CK(cudaEventElapsedTime(&nl->stage_ms[5], nl->ev[5], nl->ev[6]));
+        CK(cudaEventSynchronize(nl->ev[nl_list::kStages]));
         CK(cudaEventElapsedTime(&nl->stage_ms[6], nl->ev[6], nl->ev[7]));
+        CK(cudaEventElapsedTime(&nl->stage_ms[7], nl->ev[7], nl->ev[8]));
     }
     for (int k = 0; k < nl_list::kStages && k < cap; ++k) ms[k] = nl->stage_ms[k];
     if (count) *count = nl_list::kStages;
@@ -1230,10 +1261,7 @@ nl_status nl_graph_create(nl_list *nl, const float *x, const float *y, const flo
     cudaStream_t s = (cudaStream_t)stream;
     if (!s) return fail(NL_ERR_ARG, "graph capture needs a non-default stream");
     // 1. a normal build and pass size every buffer and validate the inputs
-    //    (with the full search, the one a capture records)
-    nl->force_full = 1;
     nl_status st = nl_rebuild_batch(nl, x, y, z, h, nsys, offsets, boxes, p, stream);
-    nl->force_full = 0;
     if (st != NL_OK) return st;
     st = nl_density_pass(nl, m, rho, stream);
     if (st != NL_OK) return st;
@@ -1244,6 +1272,22 @@ nl_status nl_graph_create(nl_list *nl, const float *x, const float *y, const flo
         CK(bigger.ensure(want));
         nl->list.release();
         nl->list = bigger;
+    }
+    {
+        // half search buffers: slack over the sizes of this build, and sort
+        // buffers for the whole tuple capacity (a replay sorts all of it)
+        const Status &hs = *nl->hst;
+        const size_t up = (size_t)hs.up_used + hs.up_used / 4 + 4096;
+        const size_t tu = (size_t)hs.tu_used + hs.tu_used / 4 + 4096;
+        CK(nl->uJ.ensure(up * 4));
+        CK(nl->uM.ensure(up));
+        CK(nl->tkey.ensure(tu * 8));
+        CK(nl->tval.ensure(tu * 4));
+        CK(nl->tkey_alt.ensure(tu * 8));
+        CK(nl->tval_alt.ensure(tu * 4));
+        CK(nl->thist.ensure(radix_hist_words((uint32_t)tu) * 4));
+        nl->graph_up_cap = up;
+        nl->graph_tu_cap = tu;
     }
     CK(cudaStreamSynchronize(s));
     const int64_t n = offsets[nsys];
@@ -1305,6 +1349,8 @@ nl_status nl_graph_check(nl_graph *g, void *stream)
     if (h.stage_overflow)
         return fail(NL_ERR_CAPACITY, "%u super-cluster lists did not fit the graph's buffers",
                     h.stage_overflow);
+    if (h.half_overflow || h.list_overflow)
+        return fail(NL_ERR_CAPACITY, "the lists outgrew the buffers the graph reserved");
     nl->n_leaves = h.n_leaves;
     nl->n_nodes = h.n_nodes;
     nl->list_bytes = h.list_used;
@@ -1400,15 +1446,15 @@ nl_status nl_density_pass(const nl_list *cnl, const float *m, float *rho, void *
     nl_list *nl = const_cast<nl_list *>(cnl);
     cudaStream_t s = (cudaStream_t)stream;
     CK(nl->aux.ensure((size_t)nl->npad * 8));
-    CK(nl->mark(5, s));
+    CK(nl->mark(6, s));
     CK(launch_gather_aux(nl->npad, nl->perm_pad.as<uint32_t>(), m, nullptr, nullptr, 0,
                          nl->aux.as<float2>(), s));
-    CK(nl->mark(6, s));
+    CK(nl->mark(7, s));
     PassArgs a = pass_args(nl);
     a.out0 = rho;
     CK(launch_pass(a, PASS_DENSITY, nl->p.cluster, nl->any_per, nl->num_sms, s,
                        nl->p.threads_per_block, nl->p.blocks_per_sm));
-    CK(nl->mark(7, s));
+    CK(nl->mark(8, s));
     return NL_OK;
 }
 
@@ -1430,24 +1476,24 @@ nl_status nl_force_pass(const nl_list *cnl, int32_t kind, const float *params, c
     a.out1 = ay;
     a.out2 = az;
     if (kind == NL_FORCE_SPH_PRESSURE) {
-        CK(nl->mark(5, s));
+        CK(nl->mark(6, s));
         CK(launch_gather_aux(nl->npad, nl->perm_pad.as<uint32_t>(), m, pres, rho, 1,
                              nl->aux.as<float2>(), s));
-        CK(nl->mark(6, s));
+        CK(nl->mark(7, s));
         CK(launch_pass(a, PASS_SPH, nl->p.cluster, nl->any_per, nl->num_sms, s,
                        nl->p.threads_per_block, nl->p.blocks_per_sm));
-        CK(nl->mark(7, s));
+        CK(nl->mark(8, s));
     } else if (kind == NL_FORCE_LJ) {
         if (!params) return fail(NL_ERR_ARG, "LJ force needs params {eps, sigma}");
         if (!std::isfinite(params[0]) || !(params[1] > 0.f))
             return fail(NL_ERR_ARG, "LJ needs finite eps and sigma > 0");
         a.p0 = params[0];
         a.p1 = params[1];
-        CK(nl->mark(5, s));
         CK(nl->mark(6, s));
+        CK(nl->mark(7, s));
         CK(launch_pass(a, PASS_LJ, nl->p.cluster, nl->any_per, nl->num_sms, s,
                        nl->p.threads_per_block, nl->p.blocks_per_sm));
-        CK(nl->mark(7, s));
+        CK(nl->mark(8, s));
     } else {
         return fail(NL_ERR_ARG, "unknown force kind %d", kind);
     }

@@ -486,6 +486,9 @@ cudaError_t launch_search_ctl(const SearchArgs &a, const uint32_t *work, uint32_
 // sorted tuples (lower j-clusters) followed by its upper entries, encoded as
 // by the search.  tkey/tval sorted by key; seg_off from seg_offsets().
 cudaError_t launch_assemble(const SearchArgs &a, int grid_blocks, cudaStream_t s);
+// keys[k] = fill for min(*used, cap) <= k < cap (unused tuple slots of a graph replay)
+cudaError_t launch_fill_keys(uint64_t *keys, uint32_t cap, const unsigned long long *used,
+                             uint64_t fill, cudaStream_t s);
 // seg_off[k] = sum of cnt[0..k) over k < n; the total lands in *total.
 cudaError_t exclusive_scan_u32(const uint32_t *cnt, uint32_t *seg_off, uint32_t n, uint32_t *bsum,
                                uint32_t *total, cudaStream_t s);

@@ -197,22 +197,43 @@ __global__ void __launch_bounds__(LL_THREADS) k_leaf_level(const uint8_t *__rest
                                                            uint32_t n, int B,
                                                            uint8_t *__restrict__ lev)
 {
+    // window values v = lcp + 1, 0 where no window (spans systems or out of
+    // range), so lev = max v over the B+1 windows ending at k (0: no window,
+    // the system root is a leaf).  The sliding maximum comes from a doubling
+    // table: after the steps q = 1, 2, .., P/2 entry i holds max v[i, i+P),
+    // P the largest power of two <= B+1, and two entries cover a window.
     extern __shared__ uint8_t win[];  // LL_THREADS + B entries
+    constexpr int PER = 3;            // entries per thread (B <= 1024)
+    const int L = LL_THREADS + B;
     const int64_t k0 = (int64_t)blockIdx.x * LL_THREADS;
     const int64_t nw = (int64_t)n - B;  // number of windows
-    for (int t = threadIdx.x; t < LL_THREADS + B; t += LL_THREADS) {
+    for (int t = threadIdx.x; t < L; t += LL_THREADS) {
         int64_t s = k0 - B + t;
-        win[t] = (s >= 0 && s < nw) ? lcp[s] : 0xffu;
+        uint8_t v = (s >= 0 && s < nw) ? lcp[s] : 0xffu;
+        win[t] = v == 0xffu ? (uint8_t)0 : (uint8_t)(v + 1);
     }
     __syncthreads();
-    int64_t k = k0 + threadIdx.x;
-    if (k >= n) return;
-    int m = -1;
-    for (int t = 0; t <= B; ++t) {
-        uint8_t v = win[threadIdx.x + t];
-        if (v != 0xffu && (int)v > m) m = v;
+    int P = 1;
+    while (2 * P <= B + 1) P *= 2;
+    for (int q = 1; q < P; q *= 2) {
+        uint8_t r[PER];
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const int i = threadIdx.x + j * LL_THREADS;
+            r[j] = 0;
+            if (i < L) r[j] = (i + q < L) ? max(win[i], win[i + q]) : win[i];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const int i = threadIdx.x + j * LL_THREADS;
+            if (i < L) win[i] = r[j];
+        }
+        __syncthreads();
     }
-    int l = m + 1;  // no window of B+1 in its system: the system root is a leaf
+    const int64_t k = k0 + threadIdx.x;
+    if (k >= n) return;
+    const int l = max(win[threadIdx.x], win[threadIdx.x + (B + 1) - P]);
     lev[k] = (uint8_t)(l > kMaxLevel ? kMaxLevel : l);
 }
 

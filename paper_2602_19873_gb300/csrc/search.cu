@@ -546,6 +546,12 @@ __global__ void __launch_bounds__(SR_THREADS) k_assemble(SearchArgs a)
         if (lane == 0) t = atomicAdd(&a.st->asm_ticket, 1u);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= a.nsc) break;
+        if (a.st->half_overflow || a.st->stage_overflow) {
+            // incomplete tuples or upper entries (a graph replay that outgrew
+            // its buffers, reported by nl_graph_check): empty records
+            if (lane == 0) a.rec_off[t] = kBadRecord;
+            continue;
+        }
         const uint32_t lc = a.lower_cnt[t], so = a.seg_off[t];
         const uint32_t uc = a.up_cnt[t], uo = a.up_off[t];
         const uint32_t cnt = lc + uc;
@@ -570,6 +576,23 @@ __global__ void __launch_bounds__(SR_THREADS) k_assemble(SearchArgs a)
             }
         }
     }
+}
+
+// keys[k] = fill for min(*used, cap) <= k < cap
+__global__ void k_fill_keys(uint64_t *keys, uint32_t cap, const unsigned long long *used,
+                            uint64_t fill)
+{
+    const unsigned long long u = *used;
+    const uint32_t from = u < cap ? (uint32_t)u : cap;
+    for (uint32_t k = from + blockIdx.x * blockDim.x + threadIdx.x; k < cap; k += gridDim.x * blockDim.x)
+        keys[k] = fill;
+}
+
+cudaError_t launch_fill_keys(uint64_t *keys, uint32_t cap, const unsigned long long *used,
+                             uint64_t fill, cudaStream_t s)
+{
+    k_fill_keys<<<1024, 256, 0, s>>>(keys, cap, used, fill);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_assemble(const SearchArgs &a, int grid, cudaStream_t s)

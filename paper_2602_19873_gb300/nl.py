@@ -102,7 +102,7 @@ NL_FORCE_SPH_PRESSURE, NL_FORCE_LJ = 0, 1
 class nl_hiter_info(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("rebuilds", C.c_int32), ("unconverged", C.c_int64)]
 
-STAGES = ["keys", "sort", "permute", "octree", "search", "pass_gather", "pass"]
+STAGES = ["keys", "sort", "permute", "octree", "search", "assemble", "pass_gather", "pass"]
 
 
 def library_path():
@@ -162,7 +162,7 @@ def make_box(box):
     return b
 
 
-def make_params(key=NL_KEY_HILBERT, cluster=8, support=2.0, compress=1, leaf_bucket=64,
+def make_params(key=NL_KEY_HILBERT, cluster=8, support=2.0, compress=1, leaf_bucket=256,
                 threads_per_block=0, blocks_per_sm=0, j_cluster=0):
     """Build options; j_cluster 0 means j-clusters of `cluster` particles."""
     p = nl_params()

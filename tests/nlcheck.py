@@ -16,7 +16,7 @@ def to_dev(d, keys=("x", "y", "z", "h", "m")):
     return {k: torch.from_numpy(np.ascontiguousarray(d[k], dtype=np.float32)).cuda() for k in keys}
 
 
-def gpu_build(d, cluster=8, compress=1, bucket=64, kind=None, support=None, j_cluster=0):
+def gpu_build(d, cluster=8, compress=1, bucket=256, kind=None, support=None, j_cluster=0):
     import torch
     t = to_dev(d)
     p = nl.make_params(key=d["kind"] if kind is None else kind, cluster=cluster,

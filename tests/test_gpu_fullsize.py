@@ -1,5 +1,5 @@
 """Parity at the workloads' full sizes, in the launch configuration the
-benchmark times (8x8 clusters, compressed list, leaf bucket 64).
+benchmark times (8x8 clusters, compressed list, leaf bucket 256).
 
 The oracle sorts all particles itself and computes, by O(n) brute force per
 particle, the symmetric neighbor sets of a sample of whole super-clusters:
@@ -35,7 +35,7 @@ def _rows(sc, n, M=8):
 def _check_sampled(d, name, with_density=True):
     o = oracle_sorted(d)
     n = len(o["xs"])
-    L, t = gpu_build(d, cluster=8, compress=1, bucket=64)
+    L, t = gpu_build(d, cluster=8, compress=1, bucket=256)
     nsc = L.sizes()["n_superclusters"]
     sc = _sample_sc(nsc, seed=n % 1000)
     rows = _rows(sc, n)

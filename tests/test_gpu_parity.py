@@ -44,7 +44,7 @@ def test_keys_and_stable_sort_bit_exact(cases, name):
 
 
 @pytest.mark.parametrize("name", ["uniform", "plummer"])
-@pytest.mark.parametrize("bucket", [16, 64])
+@pytest.mark.parametrize("bucket", [16, 64, 256])
 def test_octree_bit_exact(cases, name, bucket):
     d, o, _ = cases[name]
     L, t = gpu_build(d, bucket=bucket)
