@@ -104,6 +104,53 @@ def dist_init():
     return ws, rank, local
 
 
+def init_ranks(backend):
+    """(world size, rank, local rank); joins the process group when there
+    are several ranks (one process per GPU, env rendezvous)."""
+    ws, rank, local = dist_init()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def max_over_ranks(x, ws, device):
+    """The largest x over all ranks (the slowest rank's time)."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, ws, device):
+    """The sum of x over all ranks."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, ws, ms):
+    """Whole-job throughput in millions of units per second: every rank
+    processes units_per_rank units in the slowest rank's ms."""
+    return ws * units_per_rank / (ms * 1e-3) / 1e6
+
+
+def reference_sample(steps, warmup, requested=None):
+    """Particles per oracle step: the requested size, else a size that keeps
+    warmup + steps oracle steps near 100 s on the host (0.11 Mparticles/s
+    measured for the oracle), between 2^16 and 2^20."""
+    if requested:
+        return requested
+    return int(min(1 << 20, max(1 << 16, 0.11e6 * 100.0 / max(1, steps + warmup))))
+
+
 def launches_per_step(sizes, batched):
     """Kernels of one build + density step (graph replay when batched): keys,
     radix sort (8 passes x 3, a 9th by system in batches), permute, octree
@@ -186,9 +233,9 @@ def run_native(args):
 
     ws, rank, local = dist_init()
     torch.cuda.set_device(local)
+    init_ranks("nccl")
     if ws > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
     d = workload(4 + rank, args.n)
     n = len(d["x"])
     dev = {k: torch.from_numpy(d[k]).cuda() for k in ("x", "y", "z", "h", "m")}
@@ -250,10 +297,8 @@ def run_native(args):
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / args.steps
     clk = clocks.stop()
+    ms = max_over_ranks(ms, ws, "cuda")
     if ws > 1:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
         dist.barrier()
     stages = {k: v / args.steps for k, v in stage_acc.items()}
     sizes = L.sizes()
@@ -273,10 +318,7 @@ def run_native(args):
                             rho_h, stream)
     torch.cuda.synchronize()
     e_ms = (time.perf_counter() - te) * 1e3 / esteps
-    if ws > 1:
-        tt = torch.tensor([e_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e_ms = float(tt.item())
+    e_ms = max_over_ranks(e_ms, ws, "cuda")
 
     hbm, hbm_kind, sm_max = peaks()
     alu_peak = 152 * 128 * sm_max * 1e6 / 1e12  # FP32 instructions per second, Tops
@@ -285,7 +327,7 @@ def run_native(args):
     achieved = pairs * ALU_OPS_PER_PAIR_SEARCH / (search_ms * 1e-3) / 1e12
     step_bytes = ALGO_BYTES_PER_PARTICLE * n
     out = {
-        "metric": METRIC, "value": ws * n / (ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": ws,
+        "metric": METRIC, "value": job_rate(n, ws, ms), "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
@@ -317,7 +359,7 @@ def run_native(args):
                  "search_j_examined": sizes["j_examined"],
                  "search_tile_tests": sizes["tile_tests"]},
         "e2e": None if args.no_e2e else {
-            "value": ws * n / (e_ms * 1e-3) / 1e6, "unit": UNIT,
+            "value": job_rate(n, ws, e_ms), "unit": UNIT,
             "h2d_bytes_per_step": 20 * n, "d2h_bytes_per_step": 4 * n},
         "h_iteration": {"plain": {"ms": hms, "iterations": hinfo["iterations"],
                                   "rebuilds": hinfo["rebuilds"],
@@ -331,7 +373,7 @@ def run_native(args):
     }
     out["gpu_launches"] = args.steps * launches_per_step(sizes, False)
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.cpu_sample)
+        out["cpu_baseline"] = cpu_baseline(args.cpu_sample or (1 << 20))
     if rank == 0:
         print(json.dumps(out))
     if ws > 1:
@@ -349,6 +391,7 @@ def run_batched(args):
 
     ws, rank, local = dist_init()
     torch.cuda.set_device(local)
+    init_ranks("nccl")
     systems = wl.cached(wl.batched, "batched256_%d" % (5 + rank), 256, seed=5 + rank)
     offs = np.zeros(len(systems) + 1, np.int64)
     offs[1:] = np.cumsum([len(d["x"]) for d in systems])
@@ -384,7 +427,8 @@ def run_batched(args):
             G.launch(stream)
         e1.record(stream)
         stream.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
+        ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, ws, "cuda")
+        n_job = sum_over_ranks(n, ws, "cuda")
         clk = clocks.stop()
         G.check(stream)
         sizes = L.sizes()
@@ -404,7 +448,7 @@ def run_batched(args):
         want = oracle.density(*srt, d["box"], g_off, g_idx, np.arange(len(perm)))
         worst = max(worst, float(np.max(np.abs(got[offs[k]:offs[k + 1]][perm] - want) / want)))
     out = {"metric": "batched build+density Mparticles/s (256 systems, one CUDA graph per step)",
-           "value": n / (ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "value": job_rate(n_job, 1, ms), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "batched_256: 256 systems, N log-uniform in [1e3, 1e6], "
@@ -421,6 +465,9 @@ def run_batched(args):
            "gpu_launches": args.steps * launches_per_step(sizes, True), "clocks": clk}
     if rank == 0:
         print(json.dumps(out))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 def oracle_step(d):
@@ -463,23 +510,24 @@ def run_reference(args):
     import oracle
     from paper_2602_19873_gb300 import workloads as wl
     oracle.build()
-    d = wl.plummer(args.cpu_sample, n_spheres=64, seed=4)
-    for _ in range(min(args.warmup, 1)):
+    ns = reference_sample(args.steps, args.warmup, args.cpu_sample)
+    d = wl.plummer(ns, n_spheres=64, seed=4)
+    for _ in range(args.warmup):
         oracle_step(d)
     t = time.perf_counter()
     for _ in range(args.steps):
         oracle_step(d)
     dt = (time.perf_counter() - t) / args.steps
-    v = args.cpu_sample / dt / 1e6
+    v = ns / dt / 1e6
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
            "config": {"workload": "%s generator at %d particles (bounded CPU sample)" % (
-               WORKLOAD, args.cpu_sample)},
+               WORKLOAD, ns)},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(),
                             "kind": "oracle",
-                            "sample": "%d particles of the 64-Plummer-sphere generator" % args.cpu_sample},
+                            "sample": "%d particles of the 64-Plummer-sphere generator" % ns},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -490,7 +538,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--cpu-sample", type=int, default=1 << 20)
+    ap.add_argument("--cpu-sample", type=int, default=None,
+                    help="particles of the CPU oracle sample (default: 2^20 for cpu_baseline; "
+                         "sized to the step count for --impl reference)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=N_FULL,
                     help="particles (smaller cases are for profiling only)")
