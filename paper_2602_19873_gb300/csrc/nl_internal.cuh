@@ -224,6 +224,112 @@ __device__ __forceinline__ bool boxes_all_near(const float4 &alo, const float4 &
 }
 
 // ---------------------------------------------------------------------------
+// The same arithmetic on a compact per-system form for the hot loops: the
+// periodic lengths L (+inf on an open axis) in three registers.  L/2 is
+// rounded as 0.5f * L exactly as in DevBox; with L = +inf an open axis never
+// wraps and its periodic gap terms are +inf, so every value equals the one of
+// the DevBox form without reading any flag.
+// ---------------------------------------------------------------------------
+struct PerLen {
+    float x, y, z;
+};
+
+__device__ __forceinline__ PerLen per_len(const DevBox &b)
+{
+    return PerLen{b.per[0] ? b.len[0] : INFINITY, b.per[1] ? b.len[1] : INFINITY,
+                  b.per[2] ? b.len[2] : INFINITY};
+}
+
+__device__ __forceinline__ float wrap_len(float d, float len)
+{
+    const float half = __fmul_rn(0.5f, len);
+    if (d > half)
+        d = __fsub_rn(d, len);
+    else if (d < -half)
+        d = __fadd_rn(d, len);
+    return d;
+}
+
+template <bool PER>
+__device__ __forceinline__ float pair_d2(const float4 &pi, const float4 &pj, const PerLen &L)
+{
+    float dx = __fsub_rn(pj.x, pi.x);
+    float dy = __fsub_rn(pj.y, pi.y);
+    float dz = __fsub_rn(pj.z, pi.z);
+    if (PER) {
+        dx = wrap_len(dx, L.x);
+        dy = wrap_len(dy, L.y);
+        dz = wrap_len(dz, L.z);
+    }
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+template <bool PER>
+__device__ __forceinline__ float3 pair_dx_acc(const float4 &pi, const float4 &pj, const PerLen &L)
+{
+    if (!PER) return make_float3(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z));
+    return make_float3(wrap_axis_acc(pi.x, pj.x, L.x, __fmul_rn(0.5f, L.x), 1),
+                       wrap_axis_acc(pi.y, pj.y, L.y, __fmul_rn(0.5f, L.y), 1),
+                       wrap_axis_acc(pi.z, pj.z, L.z, __fmul_rn(0.5f, L.z), 1));
+}
+
+template <bool PER>
+__device__ __forceinline__ float axis_gap_len(float a0, float a1, float b0, float b1, float len)
+{
+    float g = fmaxf(0.f, fmaxf(__fsub_rn(b0, a1), __fsub_rn(a0, b1)));
+    if (PER) {
+        float down = __fsub_rn(len, __fsub_rn(b1, a0));  // j wrapped by -L
+        float up = __fadd_rn(__fsub_rn(b0, a1), len);    // j wrapped by +L
+        g = fminf(g, fmaxf(0.f, fminf(down, up)));
+    }
+    return g;
+}
+
+template <bool PER>
+__device__ __forceinline__ bool boxes_near(const float4 &alo, const float4 &ahi, const float4 &blo,
+                                           const float4 &bhi, const PerLen &L)
+{
+    float gx = axis_gap_len<PER>(alo.x, ahi.x, blo.x, bhi.x, L.x);
+    float gy = axis_gap_len<PER>(alo.y, ahi.y, blo.y, bhi.y, L.y);
+    float gz = axis_gap_len<PER>(alo.z, ahi.z, blo.z, bhi.z, L.z);
+    float d2 = __fadd_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)), __fmul_rn(gz, gz));
+    float r = fmaxf(alo.w, blo.w);
+    return d2 <= __fmul_rn(r, r);
+}
+
+// A real (finite) particle only: the periodic gap of a point at infinity
+// is not meaningful.
+template <bool PER>
+__device__ __forceinline__ bool point_near(const float4 &p, float r, const float4 &blo,
+                                           const float4 &bhi, const PerLen &L)
+{
+    float gx = axis_gap_len<PER>(p.x, p.x, blo.x, bhi.x, L.x);
+    float gy = axis_gap_len<PER>(p.y, p.y, blo.y, bhi.y, L.y);
+    float gz = axis_gap_len<PER>(p.z, p.z, blo.z, bhi.z, L.z);
+    float d2 = __fadd_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)), __fmul_rn(gz, gz));
+    float rr = fmaxf(r, blo.w);
+    return d2 <= __fmul_rn(rr, rr);
+}
+
+template <bool PER>
+__device__ __forceinline__ bool boxes_all_near(const float4 &alo, const float4 &ahi,
+                                               const float4 &blo, const float4 &bhi,
+                                               const PerLen &L)
+{
+    float gx = fmaxf(__fsub_rn(bhi.x, alo.x), __fsub_rn(ahi.x, blo.x));
+    float gy = fmaxf(__fsub_rn(bhi.y, alo.y), __fsub_rn(ahi.y, blo.y));
+    float gz = fmaxf(__fsub_rn(bhi.z, alo.z), __fsub_rn(ahi.z, blo.z));
+    if (PER) {
+        if (!(gx <= __fmul_rn(0.5f, L.x)) || !(gy <= __fmul_rn(0.5f, L.y)) ||
+            !(gz <= __fmul_rn(0.5f, L.z)))
+            return false;
+    }
+    float d2 = __fadd_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)), __fmul_rn(gz, gz));
+    float r = fmaxf(ahi.w, bhi.w);
+    return d2 < __fmul_rn(r, r);
+}
+
+// ---------------------------------------------------------------------------
 // SFC keys
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t quantize21(float x, float lo, float qs)

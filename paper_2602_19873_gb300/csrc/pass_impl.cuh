@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(PS_THREADS, ps_min_blocks<KIND>()) k_pass(Pass
         s = __shfl_sync(0xffffffffu, s, 0);
         if (s >= (a.work ? a.nwork : a.nsc)) break;
         if (a.work) s = a.work[s];
-        const DevBox &box = a.sys.box[sys_of(a.sys.pad_off, a.sys.nsys, s * kSC * M)];
+        const PerLen box = per_len(a.sys.box[sys_of(a.sys.pad_off, a.sys.nsys, s * kSC * M)]);
 
         float4 pi[kSC];
         float ri2[kSC], hinv[kSC], ci[kSC], ri[kSC];

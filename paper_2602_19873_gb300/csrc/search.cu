@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
         const uint32_t base = s * kSC * M;
         // the super-cluster's system: its box and its own octree subtree
         const uint32_t sy = sys_of(a.sys.pad_off, a.sys.nsys, base);
-        const DevBox &box = a.sys.box[sy];
+        const PerLen box = per_len(a.sys.box[sy]);
         // (clamped to the node arrays: after a node overflow in a graph replay
         // the tables may be stale, and the replay is reported as failed)
         const uint32_t vroot = min(a.sys.root[sy], a.nnodes - 1);
@@ -282,13 +282,15 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
         // i-cluster box of this lane's cluster (lane & 7)
         const float4 ilo = a.clo[s * kSC + (lane & 7)];
         const float4 ihi = a.chi[s * kSC + (lane & 7)];
-        // pruning particles base + lane + 32 t (dummies moved to infinity,
-        // so they are never near anything), staged as (x, y, z, r) for the
-        // tile tests.  Per-particle tests, not boxes of several particles:
+        // pruning particles base + lane + 32 t, staged as (x, y, z, r) for
+        // the tile tests.  Dummies sit at infinity, which no open axis comes
+        // near; on periodic systems they are flagged off as well (a point at
+        // infinity has no meaningful periodic gap).  Per-particle tests, not boxes of several particles:
         // particles adjacent on the curve can lie far apart in sparse
         // regions, and a box around them would admit far too many nodes.
         float4 qp[NPI];
         float qr[NPI];
+        uint32_t qok = 0;  // bit t: particle t of this lane is real
         __syncwarp();
 #pragma unroll
         for (int t = 0; t < NPI; ++t) {
@@ -298,6 +300,7 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
             const bool real = p.x == p.x;
             qp[t] = real ? p : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
             qr[t] = real ? r : 0.f;
+            qok |= real ? 1u << t : 0u;
         }
 
         uint32_t cnt = 0, tiles = 0, nvis = 0, lvis = 0, jex = 0, ttests = 0, qn = 0;
@@ -353,7 +356,9 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
 #pragma unroll
                         for (int t = 0; t < NPI; ++t) {
                             const uint32_t bt = __ballot_sync(
-                                0xffffffffu, point_near<PER>(qp[t], qr[t], jlo, jhi, box));
+                                0xffffffffu,
+                                (!PER || ((qok >> t) & 1u)) &&
+                                    point_near<PER>(qp[t], qr[t], jlo, jhi, box));
 #pragma unroll
                             for (int c = 0; c < CPB; ++c)
                                 if ((bt >> (c * M)) & ((M == 32) ? 0xffffffffu : ((1u << M) - 1u)))
@@ -422,7 +427,8 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
             ++nvis;
             bool near = false;
 #pragma unroll
-            for (int t = 0; t < NPI; ++t) near |= point_near<PER>(qp[t], qr[t], nlo, nhi, box);
+            for (int t = 0; t < NPI; ++t)
+                near |= (!PER || ((qok >> t) & 1u)) && point_near<PER>(qp[t], qr[t], nlo, nhi, box);
             if (!__any_sync(0xffffffffu, near)) {
                 v = skip > v ? skip : v + 1;  // always advances
                 continue;

@@ -184,11 +184,14 @@ def cached(fn, key, *args, **kw):
     path = os.path.join(d, key + ".npz")
     if os.path.exists(path):
         z = np.load(path, allow_pickle=True)
-        return z["d"].item()
+        v = z["d"]
+        return v.item() if v.shape == () else list(v)
     out = fn(*args, **kw)
     os.makedirs(d, exist_ok=True)
     tmp = path + ".%d.tmp.npz" % os.getpid()
-    np.savez(tmp, d=np.array(out, dtype=object))
+    box = np.empty((), dtype=object)  # a 0-d holder keeps lists and dicts whole
+    box[()] = out
+    np.savez(tmp, d=box)
     os.replace(tmp, path)
     return out
 

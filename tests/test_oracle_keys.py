@@ -144,3 +144,4 @@ def test_octree_duplicate_keys_cap_at_level_21(orc):
     leaves = [(int(l), int(a), int(b)) for l, a, b, f in
               zip(t["level"], t["first"], t["end"], t["leaf"]) if f]
     assert leaves == [(21, 0, 40), (21, 40, 43)]
+
