@@ -151,14 +151,15 @@ def reference_sample(steps, warmup, requested=None):
     return int(min(1 << 20, max(1 << 16, 0.11e6 * 100.0 / max(1, steps + warmup))))
 
 
-def launches_per_step(sizes, batched):
+def launches_per_step(sizes, batched, mixed=False):
     """Kernels of one build + density step (graph replay when batched): keys,
     radix sort (8 passes x 3, a 9th by system in batches), permute, octree
-    (10), search, and for the half search the tuple sort (3 per 8 key bits,
-    plus the fill of unused slots in a graph), the lower-entry scan (3) and
-    the record assembly; then the pass input gather and the pass."""
+    (10), search (two launches when a batch mixes open and periodic systems),
+    and for the half search the tuple sort (3 per 8 key bits, plus the fill of
+    unused slots in a graph), the lower-entry scan (3) and the record
+    assembly; then the pass input gather and the pass (two when mixed)."""
     sort_passes = 9 if batched else 8
-    n = 1 + 3 * sort_passes + 1 + 10 + 1
+    n = 1 + 3 * sort_passes + 1 + 10 + (2 if mixed else 1) + (1 if mixed else 0)
     if sizes["j_cluster"] == sizes["cluster"]:
         nsc = sizes["n_superclusters"]
         bits = 1
@@ -462,7 +463,9 @@ def run_batched(args):
                     "computed_pairs": sizes["n_tiles"] * best.cluster * sizes["j_cluster"]},
            "per_system_max_rel_density_err": worst,
            "per_system_error_sample": [int(len(systems[k]["x"])) for k in sample],
-           "gpu_launches": args.steps * launches_per_step(sizes, True), "clocks": clk}
+           "gpu_launches": args.steps * launches_per_step(
+               sizes, True, mixed=len({bool(np.any(b["periodic"])) for b in boxes}) > 1),
+           "clocks": clk}
     if rank == 0:
         print(json.dumps(out))
     if ws > 1:

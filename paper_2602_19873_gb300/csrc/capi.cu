@@ -110,6 +110,10 @@ struct nl_list {
     DevBuf stageJ, stageM, list, rec_off, redo, work, aux, status;
     // half search: upper entries, transposed tuples (+ sort buffers), per super-cluster tables
     DevBuf uJ, uM, up_off, up_cnt, lower_cnt, seg_off, tkey, tkey_alt, tval, tval_alt, thist;
+    // batches mixing periodic and open systems: their super-clusters, so that
+    // the open ones run the kernels without periodic arithmetic
+    DevBuf sc_open, sc_per;
+    uint32_t n_open = 0, n_per = 0;
     DevBuf perm_pad, sys_off, sys_pad, sys_box, sys_root, sys_hcap;
     int32_t nsys = 1;
     uint32_t node_cap = 0;
@@ -169,7 +173,7 @@ struct nl_list {
                          &it_hlo, &it_hhi, &it_hs, &it_counts, &it_conv, &it_aflag, &it_alist,
                          &it_words, &it_tmp, &ml_X, &ml_e64, &ml_pred, &ml_slo, &ml_shi,
                          &uJ, &uM, &up_off, &up_cnt, &lower_cnt, &seg_off, &tkey, &tkey_alt,
-                         &tval, &tval_alt, &thist};
+                         &tval, &tval_alt, &thist, &sc_open, &sc_per};
         for (DevBuf *b : all) b->release();
         for (int i = 0; i <= kStages; ++i)
             if (ev[i]) cudaEventDestroy(ev[i]);
@@ -330,6 +334,23 @@ nl_status do_prep(nl_list *nl, const float *x, const float *y, const float *z, c
     CK(cudaMemcpyAsync(nl->sys_box.p, dbox.data(), (size_t)nsys * sizeof(DevBox),
                        cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(nl->sys_hcap.p, hcap.data(), (size_t)nsys * 4, cudaMemcpyHostToDevice, s));
+    // super-clusters of open and of periodic systems, when a batch has both
+    std::vector<uint32_t> lo_sc, pe_sc;
+    bool has_open = false;
+    for (int32_t k = 0; k < nsys; ++k)
+        if (!(boxes[k].periodic[0] || boxes[k].periodic[1] || boxes[k].periodic[2])) has_open = true;
+    if (nl->any_per && has_open) {
+        for (int32_t k = 0; k < nsys; ++k) {
+            const bool per = boxes[k].periodic[0] || boxes[k].periodic[1] || boxes[k].periodic[2];
+            for (uint32_t c = pad[k] / scp; c < pad[k + 1] / scp; ++c) (per ? pe_sc : lo_sc).push_back(c);
+        }
+        CK(nl->sc_open.ensure(lo_sc.size() * 4));
+        CK(nl->sc_per.ensure(pe_sc.size() * 4));
+        CK(cudaMemcpyAsync(nl->sc_open.p, lo_sc.data(), lo_sc.size() * 4, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(nl->sc_per.p, pe_sc.data(), pe_sc.size() * 4, cudaMemcpyHostToDevice, s));
+    }
+    nl->n_open = (uint32_t)lo_sc.size();
+    nl->n_per = (uint32_t)pe_sc.size();
     }
     const SysTables T = nl->tables();
     Status *dst = nl->status.as<Status>();
@@ -395,6 +416,44 @@ nl_status do_prep(nl_list *nl, const float *x, const float *y, const float *z, c
     nl->n_nodes = nnodes;
     nl->n_prepared = n;
     return NL_OK;
+}
+
+// First search round over all super-clusters: in a batch that mixes open and
+// periodic systems, the open ones run without periodic arithmetic.
+cudaError_t search_all(nl_list *nl, const SearchArgs &sa, int M, int grid, int tpb, cudaStream_t s)
+{
+    if (nl->n_open && nl->n_per) {
+        cudaError_t e = launch_search_ctl(sa, nl->sc_open.as<uint32_t>(), nl->n_open,
+                                          nl->redo.as<uint32_t>(), M, 0, grid, tpb, s);
+        if (e != cudaSuccess) return e;
+        e = cudaMemsetAsync(&sa.st->ticket, 0, sizeof(sa.st->ticket), s);
+        if (e != cudaSuccess) return e;
+        return launch_search_ctl(sa, nl->sc_per.as<uint32_t>(), nl->n_per, nl->redo.as<uint32_t>(),
+                                 M, 1, grid, tpb, s);
+    }
+    return launch_search_ctl(sa, nullptr, nl->nsc, nl->redo.as<uint32_t>(), M, nl->any_per, grid,
+                             tpb, s);
+}
+
+// A pass over all super-clusters (a.work == NULL) or over a.work; split by
+// system kind as the search is.
+cudaError_t run_pass(const nl_list *nl, const PassArgs &a, int kind, cudaStream_t s)
+{
+    const int M = nl->p.cluster;
+    if (!a.work && nl->n_open && nl->n_per) {
+        PassArgs o = a, q = a;
+        o.work = nl->sc_open.as<uint32_t>();
+        o.nwork = nl->n_open;
+        q.work = nl->sc_per.as<uint32_t>();
+        q.nwork = nl->n_per;
+        cudaError_t e = launch_pass(o, kind, M, 0, nl->num_sms, s, nl->p.threads_per_block,
+                                    nl->p.blocks_per_sm);
+        if (e != cudaSuccess) return e;
+        return launch_pass(q, kind, M, 1, nl->num_sms, s, nl->p.threads_per_block,
+                           nl->p.blocks_per_sm);
+    }
+    return launch_pass(a, kind, M, nl->any_per, nl->num_sms, s, nl->p.threads_per_block,
+                       nl->p.blocks_per_sm);
 }
 
 // Half search (j-clusters = i-clusters): every super-cluster searches only
@@ -483,7 +542,7 @@ nl_status do_search_half(nl_list *nl, cudaStream_t s)
         sa.tu_cap = gcap;
         sa.list = nl->list.as<uint8_t>();
         sa.list_cap = nl->list.cap - 8;
-        CK(launch_search_ctl(sa, nullptr, nsc, nl->redo.as<uint32_t>(), M, nl->any_per, grid0, tpb, s));
+        CK(search_all(nl, sa, M, grid0, tpb, s));
         CK(launch_fill_keys(nl->tkey.as<uint64_t>(), (uint32_t)gcap, &dst->tu_used,
                             bits >= 64 ? ~0ull : (1ull << bits) - 1ull, s));
         CK(radix_sort_pairs(nl->tkey.as<uint64_t>(), nl->tval.as<uint32_t>(),
@@ -510,7 +569,10 @@ nl_status do_search_half(nl_list *nl, cudaStream_t s)
         sa.tkey = nl->tkey.as<uint64_t>();
         sa.tval = nl->tval.as<uint32_t>();
         sa.tu_cap = tuc;
-        CK(launch_search_ctl(sa, work, count, nl->redo.as<uint32_t>(), M, nl->any_per, grid, tpb, s));
+        if (work)
+            CK(launch_search_ctl(sa, work, count, nl->redo.as<uint32_t>(), M, nl->any_per, grid, tpb, s));
+        else
+            CK(search_all(nl, sa, M, grid, tpb, s));
         st = read_status(nl, s);
         if (st != NL_OK) return st;
         nv += nl->hst->node_visits;
@@ -668,7 +730,10 @@ nl_status do_search(nl_list *nl, cudaStream_t s)
         sa.stage_cap = nl->stage_cap;
         sa.list = nl->list.as<uint8_t>();
         sa.list_cap = nl->list.cap - 8;  // 8 bytes of slack behind the last record
-        CK(launch_search_ctl(sa, work, count, nl->redo.as<uint32_t>(), M, nl->any_per, grid, tpb, s));
+        if (work)
+            CK(launch_search_ctl(sa, work, count, nl->redo.as<uint32_t>(), M, nl->any_per, grid, tpb, s));
+        else
+            CK(search_all(nl, sa, M, grid, tpb, s));
         if (nl->graph_mode) return NL_OK;  // overflow is reported by nl_graph_check
         st = read_status(nl, s);
         if (st != NL_OK) return st;
@@ -1193,8 +1258,7 @@ static nl_status do_iterate_h(nl_list *nl, const float *x, const float *y, const
             a.work = hs.active_list;
             a.nwork = words[2];
         }
-        CK(launch_pass(a, PASS_COUNT, M, nl->any_per, nl->num_sms, s, p->threads_per_block,
-                       p->blocks_per_sm));
+        CK(run_pass(nl, a, PASS_COUNT, s));
         ++iters;
         first = false;
         CK(cudaMemsetAsync(hs.words, 0, 16, s));
@@ -1452,8 +1516,7 @@ nl_status nl_density_pass(const nl_list *cnl, const float *m, float *rho, void *
     CK(nl->mark(7, s));
     PassArgs a = pass_args(nl);
     a.out0 = rho;
-    CK(launch_pass(a, PASS_DENSITY, nl->p.cluster, nl->any_per, nl->num_sms, s,
-                       nl->p.threads_per_block, nl->p.blocks_per_sm));
+    CK(run_pass(nl, a, PASS_DENSITY, s));
     CK(nl->mark(8, s));
     return NL_OK;
 }
@@ -1480,8 +1543,7 @@ nl_status nl_force_pass(const nl_list *cnl, int32_t kind, const float *params, c
         CK(launch_gather_aux(nl->npad, nl->perm_pad.as<uint32_t>(), m, pres, rho, 1,
                              nl->aux.as<float2>(), s));
         CK(nl->mark(7, s));
-        CK(launch_pass(a, PASS_SPH, nl->p.cluster, nl->any_per, nl->num_sms, s,
-                       nl->p.threads_per_block, nl->p.blocks_per_sm));
+        CK(run_pass(nl, a, PASS_SPH, s));
         CK(nl->mark(8, s));
     } else if (kind == NL_FORCE_LJ) {
         if (!params) return fail(NL_ERR_ARG, "LJ force needs params {eps, sigma}");
@@ -1491,8 +1553,7 @@ nl_status nl_force_pass(const nl_list *cnl, int32_t kind, const float *params, c
         a.p1 = params[1];
         CK(nl->mark(6, s));
         CK(nl->mark(7, s));
-        CK(launch_pass(a, PASS_LJ, nl->p.cluster, nl->any_per, nl->num_sms, s,
-                       nl->p.threads_per_block, nl->p.blocks_per_sm));
+        CK(run_pass(nl, a, PASS_LJ, s));
         CK(nl->mark(8, s));
     } else {
         return fail(NL_ERR_ARG, "unknown force kind %d", kind);
@@ -1508,8 +1569,7 @@ nl_status nl_neighbor_counts(const nl_list *cnl, uint32_t *counts, void *stream)
     nl_list *nl = const_cast<nl_list *>(cnl);
     PassArgs a = pass_args(nl);
     a.outc = counts;
-    CK(launch_pass(a, PASS_COUNT, nl->p.cluster, nl->any_per, nl->num_sms, (cudaStream_t)stream,
-                   nl->p.threads_per_block, nl->p.blocks_per_sm));
+    CK(run_pass(nl, a, PASS_COUNT, (cudaStream_t)stream));
     return NL_OK;
 }
 
