@@ -154,12 +154,15 @@ def reference_sample(steps, warmup, requested=None):
 def launches_per_step(sizes, batched, mixed=False):
     """Kernels of one build + density step (graph replay when batched): keys,
     radix sort (8 passes x 3, a 9th by system in batches), permute, octree
-    (10), search (two launches when a batch mixes open and periodic systems),
+    (10), search (open, interior and boundary launches plus a classification
+    when a batch mixes open and periodic systems),
     and for the half search the tuple sort (3 per 8 key bits, plus the fill of
     unused slots in a graph), the lower-entry scan (3) and the record
-    assembly; then the pass input gather and the pass (two when mixed)."""
+    assembly; then the pass input gather and the pass (three when mixed)."""
     sort_passes = 9 if batched else 8
-    n = 1 + 3 * sort_passes + 1 + 10 + (2 if mixed else 1) + (1 if mixed else 0)
+    # mixed batches: open, interior and boundary launches of the search and
+    # the pass, plus the interior classification
+    n = 1 + 3 * sort_passes + 1 + 10 + (3 + 1 if mixed else 1) + (2 if mixed else 0)
     if sizes["j_cluster"] == sizes["cluster"]:
         nsc = sizes["n_superclusters"]
         bits = 1

@@ -114,6 +114,8 @@ struct nl_list {
     // the open ones run the kernels without periodic arithmetic
     DevBuf sc_open, sc_per;
     uint32_t n_open = 0, n_per = 0;
+    // periodic super-clusters split by the last search: interior / boundary
+    DevBuf sc_int, sc_bnd;
     DevBuf perm_pad, sys_off, sys_pad, sys_box, sys_root, sys_hcap;
     int32_t nsys = 1;
     uint32_t node_cap = 0;
@@ -173,7 +175,7 @@ struct nl_list {
                          &it_hlo, &it_hhi, &it_hs, &it_counts, &it_conv, &it_aflag, &it_alist,
                          &it_words, &it_tmp, &ml_X, &ml_e64, &ml_pred, &ml_slo, &ml_shi,
                          &uJ, &uM, &up_off, &up_cnt, &lower_cnt, &seg_off, &tkey, &tkey_alt,
-                         &tval, &tval_alt, &thist, &sc_open, &sc_per};
+                         &tval, &tval_alt, &thist, &sc_open, &sc_per, &sc_int, &sc_bnd};
         for (DevBuf *b : all) b->release();
         for (int i = 0; i <= kStages; ++i)
             if (ev[i]) cudaEventDestroy(ev[i]);
@@ -351,6 +353,10 @@ nl_status do_prep(nl_list *nl, const float *x, const float *y, const float *z, c
     }
     nl->n_open = (uint32_t)lo_sc.size();
     nl->n_per = (uint32_t)pe_sc.size();
+    if (nl->any_per) {
+        CK(nl->sc_int.ensure((size_t)(npad / scp) * 4));
+        CK(nl->sc_bnd.ensure((size_t)(npad / scp) * 4));
+    }
     }
     const SysTables T = nl->tables();
     Status *dst = nl->status.as<Status>();
@@ -418,42 +424,62 @@ nl_status do_prep(nl_list *nl, const float *x, const float *y, const float *z, c
     return NL_OK;
 }
 
-// First search round over all super-clusters: in a batch that mixes open and
-// periodic systems, the open ones run without periodic arithmetic.
+// First search round over all super-clusters.  Open systems run without
+// periodic arithmetic; so do the interior super-clusters of periodic systems
+// (classified here, on the device, from this build's boxes and radii); only
+// the boundary ones run the periodic kernels.  The classification stays valid
+// for the passes over this list.
 cudaError_t search_all(nl_list *nl, const SearchArgs &sa, int M, int grid, int tpb, cudaStream_t s)
 {
-    if (nl->n_open && nl->n_per) {
-        cudaError_t e = launch_search_ctl(sa, nl->sc_open.as<uint32_t>(), nl->n_open,
-                                          nl->redo.as<uint32_t>(), M, 0, grid, tpb, s);
+    uint32_t *redo = nl->redo.as<uint32_t>();
+    if (!nl->any_per)
+        return launch_search_ctl(sa, nullptr, nl->nsc, redo, M, 0, grid, tpb, s);
+    const bool mixed = nl->n_open && nl->n_per;
+    const uint32_t *plist = mixed ? nl->sc_per.as<uint32_t>() : nullptr;
+    const uint32_t np = mixed ? nl->n_per : nl->nsc;
+    cudaError_t e = launch_classify(plist, np, M, sa.sys, sa.clo, sa.chi, sa.nlo, sa.nnodes,
+                                    nl->sc_int.as<uint32_t>(), nl->sc_bnd.as<uint32_t>(), sa.st, s);
+    if (e != cudaSuccess) return e;
+    if (mixed) {
+        e = launch_search_ctl(sa, nl->sc_open.as<uint32_t>(), nl->n_open, redo, M, 0, grid, tpb, s);
         if (e != cudaSuccess) return e;
         e = cudaMemsetAsync(&sa.st->ticket, 0, sizeof(sa.st->ticket), s);
         if (e != cudaSuccess) return e;
-        return launch_search_ctl(sa, nl->sc_per.as<uint32_t>(), nl->n_per, nl->redo.as<uint32_t>(),
-                                 M, 1, grid, tpb, s);
     }
-    return launch_search_ctl(sa, nullptr, nl->nsc, nl->redo.as<uint32_t>(), M, nl->any_per, grid,
-                             tpb, s);
+    e = launch_search_ctl(sa, nl->sc_int.as<uint32_t>(), np, redo, M, 0, grid, tpb, s, &sa.st->n_int);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(&sa.st->ticket, 0, sizeof(sa.st->ticket), s);
+    if (e != cudaSuccess) return e;
+    return launch_search_ctl(sa, nl->sc_bnd.as<uint32_t>(), np, redo, M, 1, grid, tpb, s, &sa.st->n_bnd);
 }
 
 // A pass over all super-clusters (a.work == NULL) or over a.work; split by
-// system kind as the search is.
+// system kind and interior / boundary as the last search was.
 cudaError_t run_pass(const nl_list *nl, const PassArgs &a, int kind, cudaStream_t s)
 {
     const int M = nl->p.cluster;
-    if (!a.work && nl->n_open && nl->n_per) {
-        PassArgs o = a, q = a;
+    const int tpb = nl->p.threads_per_block, bps = nl->p.blocks_per_sm;
+    if (a.work || !nl->any_per)
+        return launch_pass(a, kind, M, nl->any_per, nl->num_sms, s, tpb, bps);
+    const bool mixed = nl->n_open && nl->n_per;
+    const uint32_t np = mixed ? nl->n_per : nl->nsc;
+    cudaError_t e;
+    if (mixed) {
+        PassArgs o = a;
         o.work = nl->sc_open.as<uint32_t>();
         o.nwork = nl->n_open;
-        q.work = nl->sc_per.as<uint32_t>();
-        q.nwork = nl->n_per;
-        cudaError_t e = launch_pass(o, kind, M, 0, nl->num_sms, s, nl->p.threads_per_block,
-                                    nl->p.blocks_per_sm);
+        e = launch_pass(o, kind, M, 0, nl->num_sms, s, tpb, bps);
         if (e != cudaSuccess) return e;
-        return launch_pass(q, kind, M, 1, nl->num_sms, s, nl->p.threads_per_block,
-                           nl->p.blocks_per_sm);
     }
-    return launch_pass(a, kind, M, nl->any_per, nl->num_sms, s, nl->p.threads_per_block,
-                       nl->p.blocks_per_sm);
+    PassArgs q = a;
+    q.work = nl->sc_int.as<uint32_t>();
+    q.nwork = np;
+    q.nwork_dev = &a.st->n_int;
+    e = launch_pass(q, kind, M, 0, nl->num_sms, s, tpb, bps);
+    if (e != cudaSuccess) return e;
+    q.work = nl->sc_bnd.as<uint32_t>();
+    q.nwork_dev = &a.st->n_bnd;
+    return launch_pass(q, kind, M, 1, nl->num_sms, s, tpb, bps);
 }
 
 // Half search (j-clusters = i-clusters): every super-cluster searches only
@@ -613,9 +639,12 @@ nl_status do_search_half(nl_list *nl, cudaStream_t s)
         CK(nl->stageJ.ensure(slots * nl->stage_cap * 4));
         CK(nl->stageM.ensure(slots * nl->stage_cap));
         const unsigned long long keep_up = nl->hst->up_used, keep_tu = nl->hst->tu_used;
+        const unsigned int keep_int = nl->hst->n_int, keep_bnd = nl->hst->n_bnd;
         std::memset(&nl->hst->ticket, 0, search_words);
         nl->hst->up_used = keep_up;
         nl->hst->tu_used = keep_tu;
+        nl->hst->n_int = keep_int;  // the passes use the first round's split
+        nl->hst->n_bnd = keep_bnd;
         CK(cudaMemcpyAsync(&dst->ticket, &nl->hst->ticket, search_words, cudaMemcpyHostToDevice, s));
     }
     const uint32_t ntu = (uint32_t)nl->hst->tu_used;
@@ -772,9 +801,12 @@ nl_status do_search(nl_list *nl, cudaStream_t s)
             nl->list = bigger;
             bigger.p = nullptr;
         }
+        const unsigned int keep_int = nl->hst->n_int, keep_bnd = nl->hst->n_bnd;
         std::memset(&nl->hst->ticket, 0, search_words);
         nl->hst->list_used = keep;
         nl->hst->fail_off = ~0ull;
+        nl->hst->n_int = keep_int;  // the passes use the first round's split
+        nl->hst->n_bnd = keep_bnd;
         CK(cudaMemcpyAsync(&dst->ticket, &nl->hst->ticket, search_words, cudaMemcpyHostToDevice, s));
     }
     CK(nl->mark(5, s));

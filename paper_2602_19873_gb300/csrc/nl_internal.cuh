@@ -79,6 +79,8 @@ struct Status {
     unsigned int asm_ticket;           // work counter of the record assembly
     unsigned int seg_total;            // total of the lower-entry scan
     unsigned int pad2;
+    // periodic super-clusters whose neighbors cannot wrap (interior) and the rest
+    unsigned int n_int, n_bnd;
 };
 
 // ---------------------------------------------------------------------------
@@ -587,7 +589,16 @@ struct SearchArgs {
 };
 cudaError_t launch_search_ctl(const SearchArgs &a, const uint32_t *work, uint32_t count,
                               uint32_t *redo, int M, int any_periodic, int grid_blocks,
-                              int threads, cudaStream_t s);
+                              int threads, cudaStream_t s, const uint32_t *count_dev = nullptr);
+// Splits the super-clusters list[0..n) (NULL: 0..n-1) of periodic systems:
+// interior ones (their box widened by the system's largest radius, plus a
+// rounding margin, stays inside the box on every periodic axis, so no
+// neighbor pair of theirs wraps and the open-axis arithmetic gives the same
+// results) go to out_int, the others to out_bnd; counts in st->n_int, n_bnd.
+cudaError_t launch_classify(const uint32_t *list, uint32_t n, int M, const SysTables &t,
+                            const float4 *clo, const float4 *chi, const float4 *nlo,
+                            uint32_t node_cap, uint32_t *out_int, uint32_t *out_bnd, Status *st,
+                            cudaStream_t s);
 // Record assembly of the half search: the record of super-cluster t is its
 // sorted tuples (lower j-clusters) followed by its upper entries, encoded as
 // by the search.  tkey/tval sorted by key; seg_off from seg_offsets().
@@ -619,6 +630,7 @@ struct PassArgs {
     int sorted_out;          // write outputs at the sorted index instead of perm[i]
     const uint32_t *work;    // optional list of super-clusters to process
     uint32_t nwork;
+    const uint32_t *nwork_dev;  // optional device count of work (at most nwork)
 };
 // threads 0 = 256; blocks_per_sm 0 = default
 cudaError_t launch_pass(const PassArgs &a, int kind, int M, int any_periodic, int num_sms,

@@ -118,11 +118,12 @@ __global__ void __launch_bounds__(PS_THREADS, ps_min_blocks<KIND>()) k_pass(Pass
     // lanes that hold a distinct (i, j) pair; for M x MJ = 4 x 4 lanes 16..31 repeat
     const bool owner = (M * MJ >= 32) || lane < (uint32_t)(M * MJ);
 
+    const uint32_t nwork = a.work ? (a.nwork_dev ? min(a.nwork, *a.nwork_dev) : a.nwork) : a.nsc;
     for (;;) {
         uint32_t s = 0;
         if (lane == 0) s = atomicAdd(&a.st->pass_ticket, 1u);
         s = __shfl_sync(0xffffffffu, s, 0);
-        if (s >= (a.work ? a.nwork : a.nsc)) break;
+        if (s >= nwork) break;
         if (a.work) s = a.work[s];
         const PerLen box = per_len(a.sys.box[sys_of(a.sys.pad_off, a.sys.nsys, s * kSC * M)]);
 

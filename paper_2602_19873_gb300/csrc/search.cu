@@ -32,6 +32,7 @@ struct SearchCtl {
     const uint32_t *work;   // NULL: super-clusters 0..count-1, else ids
     uint32_t count;
     uint32_t *redo;         // ids that could not be stored this time
+    const uint32_t *count_dev;  // optional device count (at most count)
 };
 
 __device__ __forceinline__ uint32_t hex_digits(uint32_t v) { return (32u - __clz(v) + 3u) >> 2; }
@@ -263,12 +264,13 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
     const uint32_t II = lane % M;
     const uint32_t JJ0 = (lane / M) % MJ;
     const uint32_t grp = lane >> 3;       // j-cluster slot of this lane in round 1
+    const uint32_t count = ctl.count_dev ? min(ctl.count, *ctl.count_dev) : ctl.count;
 
     for (;;) {
         uint32_t tk = 0;
         if (lane == 0) tk = atomicAdd(&a.st->ticket, 1u);
         tk = __shfl_sync(0xffffffffu, tk, 0);
-        if (tk >= ctl.count) break;
+        if (tk >= count) break;
         const uint32_t s = ctl.work ? ctl.work[tk] : tk;
         const uint32_t base = s * kSC * M;
         // the super-cluster's system: its box and its own octree subtree
@@ -513,9 +515,9 @@ static void launch_m(const SearchArgs &a, const SearchCtl &c, int per, int grid,
 
 cudaError_t launch_search_ctl(const SearchArgs &a, const uint32_t *work, uint32_t count,
                               uint32_t *redo, int M, int any_periodic, int grid, int threads,
-                              cudaStream_t s)
+                              cudaStream_t s, const uint32_t *count_dev)
 {
-    SearchCtl c{work, count, redo};
+    SearchCtl c{work, count, redo, count_dev};
     if (threads != 128 && threads != SR_THREADS) return cudaErrorInvalidValue;
     if (a.half && a.mj != M) return cudaErrorInvalidValue;  // needs j-clusters = i-clusters
     switch (M * 100 + a.mj) {
@@ -582,6 +584,50 @@ __global__ void __launch_bounds__(SR_THREADS) k_assemble(SearchArgs a)
             }
         }
     }
+}
+
+__global__ void k_classify(const uint32_t *__restrict__ list, uint32_t n, int M, SysTables t,
+                           const float4 *__restrict__ clo, const float4 *__restrict__ chi,
+                           const float4 *__restrict__ nlo, uint32_t node_cap,
+                           uint32_t *__restrict__ out_int, uint32_t *__restrict__ out_bnd,
+                           Status *st)
+{
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const uint32_t s = list ? list[k] : k;
+    const uint32_t sy = sys_of(t.pad_off, t.nsys, s * kSC * M);
+    const DevBox &b = t.box[sy];
+    // largest radius of the system: its octree root (clamped as in the search)
+    const float R = nlo[min(t.root[sy], node_cap - 1)].w;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int c = 0; c < kSC; ++c) {
+        const float4 a = clo[s * kSC + c], z = chi[s * kSC + c];
+        lo[0] = fminf(lo[0], a.x); lo[1] = fminf(lo[1], a.y); lo[2] = fminf(lo[2], a.z);
+        hi[0] = fmaxf(hi[0], z.x); hi[1] = fmaxf(hi[1], z.y); hi[2] = fmaxf(hi[2], z.z);
+    }
+    bool interior = true;
+    for (int a = 0; a < 3; ++a) {
+        if (!b.per[a]) continue;
+        // a wrapped pair needs a particle within R of a face; the margin covers
+        // the roundings of the gaps here and of the wrapped differences
+        const float m = R + R * 1e-5f + b.len[a] * 1e-6f;
+        interior = interior && (lo[a] - b.lo[a] > m) && (b.hi[a] - hi[a] > m);
+    }
+    if (interior)
+        out_int[atomicAdd(&st->n_int, 1u)] = s;
+    else
+        out_bnd[atomicAdd(&st->n_bnd, 1u)] = s;
+}
+
+cudaError_t launch_classify(const uint32_t *list, uint32_t n, int M, const SysTables &t,
+                            const float4 *clo, const float4 *chi, const float4 *nlo,
+                            uint32_t node_cap, uint32_t *out_int, uint32_t *out_bnd, Status *st,
+                            cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_classify<<<(n + 255) / 256, 256, 0, s>>>(list, n, M, t, clo, chi, nlo, node_cap, out_int,
+                                               out_bnd, st);
+    return cudaGetLastError();
 }
 
 // keys[k] = fill for min(*used, cap) <= k < cap
