@@ -357,3 +357,32 @@ def test_half_search_buffer_growth_keeps_records_exact(cases, monkeypatch):
                        np.arange(n))
     assert (np.abs(rho - want) / want).max() <= DENSITY_RTOL
     L.free()
+
+
+@pytest.mark.parametrize("h,per", [(0.004, (1, 1, 1)), (0.15, (1, 1, 1)), (0.02, (1, 0, 1)),
+                                   (0.02, (0, 0, 0))])
+def test_periodic_interior_and_boundary_super_clusters(h, per):
+    """Periodic super-clusters far from the faces run the open-axis kernels,
+    the others the periodic ones (tiny radii: almost all interior; large
+    radii: all boundary; mixed periodicity per axis).  Records and density
+    must not depend on the split."""
+    rng = np.random.default_rng(int(h * 1e4) + sum(per))
+    n = 6000
+    p = rng.random((3, n)).astype(np.float32)
+    d = {"x": p[0], "y": p[1], "z": p[2], "h": np.full(n, h, np.float32) *
+         (0.5 + rng.random(n)).astype(np.float32),
+         "m": np.full(n, 1.0 / n, np.float32),
+         "box": {"lo": np.zeros(3, np.float32), "hi": np.ones(3, np.float32),
+                 "periodic": np.array(per, np.int32)}, "kind": 1, "support": 2.0}
+    o = oracle_sorted(d)
+    g_off, g_idx, p_off, p_idx = full_reference(o, d)
+    L, t = gpu_build(d)
+    nsc = L.sizes()["n_superclusters"]
+    total, so, J, m = compare_records(L, o, d, 8, 1, np.arange(nsc), np.arange(n), p_off, p_idx)
+    assert L.sizes()["list_bytes"] == total
+    rho = gpu_density(L, t, n)[o["perm"]]
+    want = orc.density(o["xs"], o["ys"], o["zs"], o["hs"], o["ms"], d["box"], g_off, g_idx,
+                       np.arange(n))
+    assert (np.abs(rho - want) / want).max() <= DENSITY_RTOL
+    assert np.array_equal(gpu_counts(L, n)[o["perm"]], np.diff(g_off))
+    L.free()
