@@ -25,6 +25,25 @@ __device__ __forceinline__ uint32_t get_nibble(const uint8_t *body, uint32_t p)
     return (p & 1u) ? (b >> 4) : (b & 0xfu);
 }
 
+// sqrt.approx.f32: the hardware square root approximation (relative error
+// about 2^-22); exact 0 for 0, so coincident particles need no guard
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// cubic spline shape on q < 2 (a gather pair of the density pass has
+// q < 2 up to one rounding, where the outer branch is 0 to within 1e-20)
+__device__ __forceinline__ float spline_w_inside(float q)
+{
+    const float a = 2.f - q;
+    const float inner = fmaf(q * q, fmaf(0.75f, q, -1.5f), 1.f);
+    const float outer = 0.25f * a * a * a;
+    return q < 1.f ? inner : outer;
+}
+
 // cubic spline shape w(q) (support q < 2) and its derivative
 __device__ __forceinline__ float spline_w(float q)
 {
@@ -211,9 +230,7 @@ __global__ void __launch_bounds__(PS_THREADS, ps_min_blocks<KIND>()) k_pass(Pass
                 if constexpr (KIND == PASS_DENSITY) {
                     if (owner && ii != jj && d2 < ri2[k]) {
                         const float e2 = PER ? d2_of(pair_dx_acc<PER>(pi[k], pj, box)) : d2;
-                        // |x_i - x_j| = e2 / sqrt(e2); coincident particles give q = 0
-                        const float q = e2 > 0.f ? e2 * rsqrtf(e2) * hinv[k] : 0.f;
-                        acc.b[k] += aj.x * spline_w(q);
+                        acc.b[k] += aj.x * spline_w_inside(sqrt_approx(e2) * hinv[k]);
                     }
                 } else if constexpr (KIND == PASS_COUNT) {
                     if (owner && ii != jj && d2 < ri2[k]) acc.v[k] += 1u;
