@@ -159,6 +159,12 @@ __global__ void __launch_bounds__(PS_THREADS, ps_min_blocks<KIND>()) k_pass(Pass
             ci[k] = (KIND == PASS_SPH) ? a.aux[i].y : 0.f;
         }
         Acc<KIND> acc;
+        // density and counts take the self pair i = j inside the loop when the
+        // j-cluster holding i is listed against its i-cluster (d2 = 0, w(0) = 1);
+        // bit k: that entry was seen, so the explicit self term is not added
+        constexpr bool SELF_IN_LOOP = (KIND == PASS_DENSITY || KIND == PASS_COUNT);
+        constexpr uint32_t RJ = M / MJ;
+        uint32_t selfseen = 0;
 #pragma unroll
         for (int k = 0; k < kSC; ++k) {
             if constexpr (KIND == PASS_DENSITY) {
@@ -228,12 +234,12 @@ __global__ void __launch_bounds__(PS_THREADS, ps_min_blocks<KIND>()) k_pass(Pass
                 // accurate vector (identical unless wrapped)
                 const float d2 = pair_d2<PER>(pi[k], pj, box);
                 if constexpr (KIND == PASS_DENSITY) {
-                    if (owner && ii != jj && d2 < ri2[k]) {
+                    if (owner && d2 < ri2[k]) {  // i = j included (see selfseen)
                         const float e2 = PER ? d2_of(pair_dx_acc<PER>(pi[k], pj, box)) : d2;
                         acc.b[k] += aj.x * spline_w_inside(sqrt_approx(e2) * hinv[k]);
                     }
                 } else if constexpr (KIND == PASS_COUNT) {
-                    if (owner && ii != jj && d2 < ri2[k]) acc.v[k] += 1u;
+                    if (owner && d2 < ri2[k]) acc.v[k] += 1u;  // i = j included (see selfseen)
                 } else if constexpr (KIND == PASS_SPH) {
                     const float rj = __fmul_rn(a.support, pj.w);
                     const float rr = fmaxf(ri[k], rj);
@@ -268,6 +274,14 @@ __global__ void __launch_bounds__(PS_THREADS, ps_min_blocks<KIND>()) k_pass(Pass
             for (uint32_t e = 0; e < nb; ++e) {
                 const uint32_t Je = __shfl_sync(0xffffffffu, J, e);
                 const uint32_t me = __shfl_sync(0xffffffffu, mk, e);
+                if constexpr (SELF_IN_LOOP) {
+                    const uint32_t rel = Je - s * kSC * RJ;  // j-cluster within the own ones
+                    if (rel < (uint32_t)(kSC * RJ)) {
+                        const uint32_t kk = rel / RJ;
+                        if (((me >> kk) & 1u) && (RJ == 1 || II / MJ == rel % RJ))
+                            selfseen |= 1u << kk;
+                    }
+                }
                 if constexpr (NP <= 2) {
                     // the entry's j particles in registers; the NP terms of one
                     // i-cluster are independent (instruction-level parallelism)
@@ -325,11 +339,14 @@ __global__ void __launch_bounds__(PS_THREADS, ps_min_blocks<KIND>()) k_pass(Pass
             const uint32_t pc = a.perm[i];
             if (pc == 0xffffffffu) continue;  // dummy slot
             const uint32_t o = a.sorted_out ? i : pc;
+            // the loop took i = j iff its entry was listed and the radius is
+            // nonzero (d2 = 0 < r^2)
+            const bool took_self = ((selfseen >> k) & 1u) && ri2[k] > 0.f;
             if constexpr (KIND == PASS_DENSITY) {
-                float self = a.aux[i].x;  // m_i w(0) = m_i
+                const float self = took_self ? 0.f : a.aux[i].x;  // m_i w(0) = m_i
                 a.out0[o] = (acc.v[k] + self) * (0.318309886183790672f * hinv[k] * hinv[k] * hinv[k]);
             } else if constexpr (KIND == PASS_COUNT) {
-                a.outc[o] = acc.v[k];
+                a.outc[o] = acc.v[k] - (took_self ? 1u : 0u);
             } else if constexpr (KIND == PASS_SPH) {
                 a.out0[o] = acc.x[k];
                 a.out1[o] = acc.y[k];
