@@ -117,9 +117,10 @@ constexpr size_t pass_smem_per_warp()
 }
 
 // Resident blocks per SM the register budget is cut for: the scalar passes
-// fit 80 registers with small spills; the vector passes keep 128.
+// run at 64 registers (4 blocks of 256, some spills; measured faster than 3
+// blocks at 80), the vector passes keep 128.
 template <int KIND>
-constexpr int ps_min_blocks() { return (KIND == PASS_DENSITY || KIND == PASS_COUNT) ? 3 : 2; }
+constexpr int ps_min_blocks() { return (KIND == PASS_DENSITY || KIND == PASS_COUNT) ? 4 : 2; }
 
 template <int M, int MJ, bool PER, int KIND>
 __global__ void __launch_bounds__(PS_THREADS, ps_min_blocks<KIND>()) k_pass(PassArgs a)
