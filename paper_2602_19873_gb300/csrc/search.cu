@@ -9,10 +9,12 @@
 // so that no pair accepted by the FP32 predicate can be pruned.  Accepted leaves append
 // their j-clusters (MJ particles each, MJ = M or M / 2: the M x MJ tiles of
 // Sec. II-A / III-A) to a per-warp queue, drained 4 j-clusters at a time:
-// their particles and boxes are staged in shared memory, 4 x 8 (i-cluster,
-// j-cluster) box pairs are tested in one round (one lane each), the i
-// particles refine the candidate i-clusters, and each surviving tile is decided
-// by the exact FP32 predicate on its M x MJ pairs.  Depth-first order yields
+// their particles are staged in shared memory, 4 x 8 (i-cluster, j-cluster)
+// box pairs are tested in one round (one lane each), and each candidate tile
+// is decided by the exact FP32 predicate on its M x MJ pairs, stopping at the
+// first pair found.  (Finer filters between the two, every i particle against
+// the j-cluster box and a test for tiles whose pairs are all neighbors, cost
+// more than the tile tests they saved.)  Depth-first order yields
 // ascending j-clusters (Sec. II-A), so the (J, mask) list is produced
 // sorted; it is staged per warp (L2 resident) and then encoded:
 // u32 count | u8 masks | nibble blocks of 32 differences (Sec. II-B, the
@@ -243,7 +245,6 @@ struct SearchSmem {
     int2 nrg[32];
     uint32_t jq[SR_QCAP];          // candidate j-clusters, ascending
     float4 jp[4 * MJ];             // particles of the 4 j-clusters under test
-    float4 jb[8];                  // their boxes (lo, hi) x 4
     uint32_t win[WIN_WORDS];
 };
 
@@ -254,7 +255,6 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
     constexpr int JSTEP = 32 / M;
     constexpr uint32_t R = M / MJ;        // j-clusters per i-cluster
     constexpr int NPI = (kSC * M) / 32;   // i particles per lane for the pruning tests
-    constexpr int CPB = 32 / M;           // clusters covered by one 32-particle ballot
     extern __shared__ __align__(16) unsigned char search_smem[];
     SearchSmem<M, MJ> &S = reinterpret_cast<SearchSmem<M, MJ> *>(search_smem)[threadIdx.x >> 5];
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
     uint8_t *stM = a.stageM + (size_t)slot * a.stage_cap;
     const uint32_t II = lane % M;
     const uint32_t JJ0 = (lane / M) % MJ;
-    const uint32_t grp = lane >> 3;       // j-cluster slot of this lane in round 1
+    const uint32_t grp = lane >> 3;       // j-cluster slot of this lane in the box round
     const uint32_t count = ctl.count_dev ? min(ctl.count, *ctl.count_dev) : ctl.count;
 
     for (;;) {
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
                 const uint32_t nq = min(4u, qn - b);
                 // stage the particles and boxes of up to 4 j-clusters
                 __syncwarp();
-                bool cand = false, sure = false;
+                bool cand = false;
                 if (grp < nq) {
                     const uint32_t Jl = S.jq[b + grp];
 #pragma unroll
@@ -323,58 +323,22 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
                         const float4 p = a.pos[Jl * MJ + jl];
                         S.jp[grp * MJ + jl] = make_float4(p.x, p.y, p.z, __fmul_rn(a.support, p.w));
                     }
-                    const float4 jlo = a.jlo[Jl], jhi = a.jhi[Jl];
-                    if ((lane & 7) == 0) {
-                        S.jb[2 * grp] = jlo;
-                        S.jb[2 * grp + 1] = jhi;
-                    }
-                    // round 1: 4 j-clusters x 8 i-cluster boxes, one per lane:
-                    // may some pair be neighbors, and are all pairs neighbors?
-                    cand = boxes_near<PER>(ilo, ihi, jlo, jhi, box);
-                    sure = cand && Jl / R != s * kSC + (lane & 7) &&
-                           boxes_all_near<PER>(ilo, ihi, jlo, jhi, box);
+                    // 4 j-clusters x 8 i-cluster boxes, one per lane: may some
+                    // pair be neighbors?
+                    cand = boxes_near<PER>(ilo, ihi, a.jlo[Jl], a.jhi[Jl], box);
                 }
                 const uint32_t bal = __ballot_sync(0xffffffffu, cand);
-                const uint32_t sbal = __ballot_sync(0xffffffffu, sure);
                 __syncwarp();
                 for (uint32_t q = 0; q < nq; ++q) {
-                    uint32_t cm = (bal >> (8 * q)) & 0xffu;
+                    const uint32_t cm = (bal >> (8 * q)) & 0xffu;
                     if (!cm) continue;
                     const uint32_t J = S.jq[b + q];
-                    const uint32_t sm = (sbal >> (8 * q)) & 0xffu;
-                    if (sm == cm) {  // every candidate tile is a sure hit
-                        if (lane == 0 && cnt < a.stage_cap) {
-                            stJ[cnt] = J;
-                            stM[cnt] = (uint8_t)sm;
-                        }
-                        ++cnt;
-                        tiles += __popc(sm);
-                        continue;
-                    }
-                    if (__popc(cm) > 1) {
-                        // round 2: every i particle against the j-cluster box
-                        const float4 jlo = S.jb[2 * q], jhi = S.jb[2 * q + 1];
-                        uint32_t pm = 0;
-#pragma unroll
-                        for (int t = 0; t < NPI; ++t) {
-                            const uint32_t bt = __ballot_sync(
-                                0xffffffffu,
-                                (!PER || ((qok >> t) & 1u)) &&
-                                    point_near<PER>(qp[t], qr[t], jlo, jhi, box));
-#pragma unroll
-                            for (int c = 0; c < CPB; ++c)
-                                if ((bt >> (c * M)) & ((M == 32) ? 0xffffffffu : ((1u << M) - 1u)))
-                                    pm |= 1u << (t * CPB + c);
-                        }
-                        cm &= pm | sm;
-                        if (!cm) continue;
-                    }
-                    // exact FP32 test of the remaining M x MJ tiles
-                    uint32_t mask = sm;
-                    ttests += __popc(cm & ~sm);
+                    // exact FP32 test of the candidate M x MJ tiles
+                    uint32_t mask = 0;
+                    ttests += __popc(cm);
 #pragma unroll
                     for (int k = 0; k < kSC; ++k) {
-                        if (!((cm >> k) & 1u) || ((mask >> k) & 1u)) continue;
+                        if (!((cm >> k) & 1u)) continue;
                         const uint32_t ii = base + k * M + II;
                         const float4 pik = S.ip[k * M + II];
 #pragma unroll
