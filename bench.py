@@ -33,10 +33,11 @@ N_FULL = 1 << 24
 ALU_OPS_PER_PAIR_SEARCH = 9      # predicate: 3 sub, 3 mul, 2 add, 1 compare (non-periodic)
 ALGO_BYTES_PER_PARTICLE = 145    # keygen 20 + sort 24 + permute 49 + octree 2 + search 19 + density 31
 # DRAM bytes (read + write) of one k_search launch per particle, from an ncu
-# capture of the half search (8x8 clusters, leaf bucket 256) on this generator
-# at 2^21 particles: 45.1 MB + 13.2 MB; scaled by the particle count (the
-# traffic grows with the particles).  Valid for that kernel version only.
-SEARCH_DRAM_BYTES_PER_PARTICLE = 58.3e6 / 2097152
+# capture of the half search (8x8 clusters, leaf bucket 256, cluster-box round
+# then exact tile tests) on this generator at 2^21 particles: 45.1 MB + 12.7 MB;
+# scaled by the particle count (the traffic grows with the particles).  Valid
+# for that kernel version only.
+SEARCH_DRAM_BYTES_PER_PARTICLE = 57.8e6 / 2097152
 
 
 def peaks():
