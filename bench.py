@@ -255,7 +255,8 @@ def run_native(args):
     dev = {k: torch.from_numpy(d[k]).cuda() for k in ("x", "y", "z", "h", "m")}
     M, MJ = (int(v) for v in args.tile.split("x"))
     params = nl.make_params(key=d["kind"], cluster=M, support=d["support"], compress=1,
-                            leaf_bucket=args.leaf_bucket, j_cluster=MJ)
+                            leaf_bucket=args.leaf_bucket, j_cluster=MJ,
+                            threads_per_block=args.threads, blocks_per_sm=args.blocks_per_sm)
     L = nl.NeighborList()
     stream = torch.cuda.current_stream()
     # smoothing lengths at 200 +- 2 neighbors from the plain start (untimed
@@ -567,6 +568,10 @@ def main():
     ap.add_argument("--reuse-h", action="store_true",
                     help="reuse converged h cached by an earlier run with the same n")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--threads", type=int, default=0, choices=[0, 128, 256],
+                    help="search / pass block size of the single-system bench (0: library default)")
+    ap.add_argument("--blocks-per-sm", type=int, default=0,
+                    help="persistent blocks per SM of the single-system bench (0: library default)")
     ap.add_argument("--leaf-bucket", type=int, default=256,
                     help="octree leaf capacity of the single-system bench")
     ap.add_argument("--tile", default="8x8", choices=["8x8", "8x4", "16x8", "16x16", "4x4"],
