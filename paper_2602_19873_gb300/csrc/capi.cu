@@ -141,8 +141,11 @@ struct nl_list {
     cudaEvent_t ev[kStages + 1] = {};
     float stage_ms[kStages] = {};
     int pass_timed = 0;   // the pass events (5..7) have been recorded
-    // device copies of host inputs for nl_density_from_host
+    // device copies of host inputs for nl_density_from_host; the masses are
+    // uploaded on a side stream while the list is built
     DevBuf hx, hy, hz, hh, hm, hrho;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_m = nullptr;
     // h iteration state (sorted order)
     DevBuf it_hq, it_hlo, it_hhi, it_hs, it_counts, it_conv, it_aflag, it_alist, it_words, it_tmp;
 
@@ -179,6 +182,11 @@ struct nl_list {
         for (DevBuf *b : all) b->release();
         for (int i = 0; i <= kStages; ++i)
             if (ev[i]) cudaEventDestroy(ev[i]);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_m) cudaEventDestroy(ev_m);
+        if (side) cudaStreamDestroy(side);
+        ev_in = ev_m = nullptr;
+        side = nullptr;
         if (hst) cudaFreeHost(hst);
         hst = nullptr;
     }
@@ -976,13 +984,24 @@ nl_status nl_density_from_host(nl_list *nl, const float *x, const float *y, cons
     const size_t b = (size_t)n * 4;
     DevBuf *bufs[] = {&nl->hx, &nl->hy, &nl->hz, &nl->hh, &nl->hm, &nl->hrho};
     for (DevBuf *d : bufs) CK(d->ensure(b));
+    if (!nl->side) {
+        CK(cudaStreamCreateWithFlags(&nl->side, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&nl->ev_in, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&nl->ev_m, cudaEventDisableTiming));
+    }
+    // the side stream starts after earlier work on `stream` (which may still
+    // read the previous masses) and uploads m while the list is built
+    CK(cudaEventRecord(nl->ev_in, s));
+    CK(cudaStreamWaitEvent(nl->side, nl->ev_in, 0));
+    CK(cudaMemcpyAsync(nl->hm.p, m, b, cudaMemcpyHostToDevice, nl->side));
+    CK(cudaEventRecord(nl->ev_m, nl->side));
     CK(cudaMemcpyAsync(nl->hx.p, x, b, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(nl->hy.p, y, b, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(nl->hz.p, z, b, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(nl->hh.p, h, b, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(nl->hm.p, m, b, cudaMemcpyHostToDevice, s));
     nl_status st = nl_rebuild(nl, nl->hx.as<float>(), nl->hy.as<float>(), nl->hz.as<float>(),
                               nl->hh.as<float>(), n, box, p, stream);
+    CK(cudaStreamWaitEvent(s, nl->ev_m, 0));  // also on failure: m stays owned by us
     if (st != NL_OK) return st;
     st = nl_density_pass(nl, nl->hm.as<float>(), nl->hrho.as<float>(), stream);
     if (st != NL_OK) return st;
@@ -1271,7 +1290,7 @@ static nl_status do_iterate_h(nl_list *nl, const float *x, const float *y, const
     unsigned int words[4] = {0, 0, 0, 0};
     for (; iters < max_iter;) {
         if (rebuild) {
-            CK(launch_hsearch(npad, hs.hq, margin, hs.hcap_sys, T, hs.hs, s));
+            CK(launch_hsearch(npad, hs.hq, hs.hhi, hs.conv, margin, hs.hcap_sys, T, hs.hs, s));
             CK(launch_pos_h(npad, hs.hs, nl->pos.as<float4>(), s));
             CK(launch_cluster_boxes(npad, M, jcl(p), nl->pos.as<float4>(), p->support,
                                     nl->clo.as<float4>(), nl->chi.as<float4>(),

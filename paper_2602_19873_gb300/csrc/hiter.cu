@@ -117,17 +117,28 @@ cudaError_t launch_plain_h0(uint32_t nsc, int M, const uint32_t *perm_pad, const
     return cudaGetLastError();
 }
 
-__global__ void k_hsearch(uint32_t npad, const float *__restrict__ hq, float margin,
-                          const float *__restrict__ hcap_sys, SysTables t, float *__restrict__ hs)
+// Search h of each particle for a rebuild: h (1 + margin), except that a
+// converged particle keeps its h (the gather count of a particle depends on
+// its own h only, so it will not change) and a particle whose bisection
+// bracket is closed above needs no more than the bracket's upper end (its
+// next h stays below it).  Every value is >= the particle's current h.
+__global__ void k_hsearch(uint32_t npad, const float *__restrict__ hq,
+                          const float *__restrict__ hhi, const uint8_t *__restrict__ conv,
+                          float margin, const float *__restrict__ hcap_sys, SysTables t,
+                          float *__restrict__ hs)
 {
     uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < npad) hs[k] = fminf(hq[k] * (1.f + margin), hcap_sys[sys_of(t.pad_off, t.nsys, k)]);
+    if (k >= npad) return;
+    const float h = hq[k], hi = hhi[k];
+    const float want = conv[k] ? h : fmaxf(fminf(hi, h * (1.f + margin)), h);
+    hs[k] = fminf(want, hcap_sys[sys_of(t.pad_off, t.nsys, k)]);
 }
 
-cudaError_t launch_hsearch(uint32_t npad, const float *hq, float margin, const float *hcap_sys,
-                           const SysTables &t, float *hs, cudaStream_t s)
+cudaError_t launch_hsearch(uint32_t npad, const float *hq, const float *hhi, const uint8_t *conv,
+                           float margin, const float *hcap_sys, const SysTables &t, float *hs,
+                           cudaStream_t s)
 {
-    k_hsearch<<<(npad + 255) / 256, 256, 0, s>>>(npad, hq, margin, hcap_sys, t, hs);
+    k_hsearch<<<(npad + 255) / 256, 256, 0, s>>>(npad, hq, hhi, conv, margin, hcap_sys, t, hs);
     return cudaGetLastError();
 }
 

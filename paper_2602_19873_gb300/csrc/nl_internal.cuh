@@ -653,8 +653,9 @@ cudaError_t launch_cluster_boxes(uint32_t npad, int M, int MJ, const float4 *pos
                                  cudaStream_t s);
 cudaError_t launch_plain_h0(uint32_t nsc, int M, const uint32_t *perm_pad, const float4 *clo,
                             const float4 *chi, float n_target, float *hq, cudaStream_t s);
-cudaError_t launch_hsearch(uint32_t npad, const float *hq, float margin, const float *hcap_sys,
-                           const SysTables &t, float *hs, cudaStream_t s);
+cudaError_t launch_hsearch(uint32_t npad, const float *hq, const float *hhi, const uint8_t *conv,
+                           float margin, const float *hcap_sys, const SysTables &t, float *hs,
+                           cudaStream_t s);
 struct HIterState {
     float *hq, *hlo, *hhi, *hs;
     uint32_t *counts;
