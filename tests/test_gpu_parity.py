@@ -386,3 +386,30 @@ def test_periodic_interior_and_boundary_super_clusters(h, per):
     assert (np.abs(rho - want) / want).max() <= DENSITY_RTOL
     assert np.array_equal(gpu_counts(L, n)[o["perm"]], np.diff(g_off))
     L.free()
+
+
+def test_density_from_host_buffers(cases):
+    """The host-buffer entry point (copies inside, masses on a second stream)
+    gives bit for bit the density of the device-resident build and pass, for
+    pageable and pinned inputs and on repeated calls with changed masses."""
+    import torch
+    d, o, (g_off, g_idx, p_off, p_idx) = cases["plummer"]
+    n = len(o["xs"])
+    L, t = gpu_build(d)
+    want = gpu_density(L, t, n)
+    L.free()
+    p = nl.make_params(key=d["kind"], cluster=8, support=d["support"])
+    E = nl.NeighborList()
+    host = {k: np.ascontiguousarray(d[k], dtype=np.float32) for k in ("x", "y", "z", "h", "m")}
+    rho = np.empty(n, np.float32)
+    E.density_from_host(host["x"], host["y"], host["z"], host["h"], host["m"], d["box"], p, rho)
+    assert np.array_equal(rho, want)
+    pin = {k: torch.from_numpy(v).pin_memory().numpy() for k, v in host.items()}
+    rho_p = torch.empty(n, dtype=torch.float32).pin_memory().numpy()
+    for scale in (1.0, 2.0, 0.5):
+        pin["m"][:] = host["m"] * np.float32(scale)
+        E.density_from_host(pin["x"], pin["y"], pin["z"], pin["h"], pin["m"], d["box"], p, rho_p)
+        ref = orc.density(o["xs"], o["ys"], o["zs"], o["hs"], o["ms"] * np.float32(scale), d["box"],
+                          g_off, g_idx, np.arange(n))
+        assert (np.abs(rho_p[o["perm"]] - ref) / ref).max() <= DENSITY_RTOL
+    E.free()
