@@ -202,29 +202,6 @@ __device__ __forceinline__ bool point_near(const float4 &p, float r, const float
     return d2 <= __fmul_rn(rr, rr);
 }
 
-// Is EVERY pair between box A and box B a symmetric neighbor?  hi.w holds
-// the smallest radius of a box.  Upper bounds of |dx| per axis are
-// round-to-nearest differences of the far corners (monotone, so never below
-// the canonical per-pair value); a periodic axis qualifies only when no pair
-// can wrap (bound <= L/2).  Empty boxes (inf corners) never qualify.
-template <bool PER>
-__device__ __forceinline__ bool boxes_all_near(const float4 &alo, const float4 &ahi,
-                                               const float4 &blo, const float4 &bhi,
-                                               const DevBox &b)
-{
-    float gx = fmaxf(__fsub_rn(bhi.x, alo.x), __fsub_rn(ahi.x, blo.x));
-    float gy = fmaxf(__fsub_rn(bhi.y, alo.y), __fsub_rn(ahi.y, blo.y));
-    float gz = fmaxf(__fsub_rn(bhi.z, alo.z), __fsub_rn(ahi.z, blo.z));
-    if (PER) {
-        if ((b.per[0] && !(gx <= b.half[0])) || (b.per[1] && !(gy <= b.half[1])) ||
-            (b.per[2] && !(gz <= b.half[2])))
-            return false;
-    }
-    float d2 = __fadd_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)), __fmul_rn(gz, gz));
-    float r = fmaxf(ahi.w, bhi.w);
-    return d2 < __fmul_rn(r, r);
-}
-
 // ---------------------------------------------------------------------------
 // The same arithmetic on a compact per-system form for the hot loops: the
 // periodic lengths L (+inf on an open axis) in three registers.  L/2 is
@@ -311,24 +288,6 @@ __device__ __forceinline__ bool point_near(const float4 &p, float r, const float
     float d2 = __fadd_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)), __fmul_rn(gz, gz));
     float rr = fmaxf(r, blo.w);
     return d2 <= __fmul_rn(rr, rr);
-}
-
-template <bool PER>
-__device__ __forceinline__ bool boxes_all_near(const float4 &alo, const float4 &ahi,
-                                               const float4 &blo, const float4 &bhi,
-                                               const PerLen &L)
-{
-    float gx = fmaxf(__fsub_rn(bhi.x, alo.x), __fsub_rn(ahi.x, blo.x));
-    float gy = fmaxf(__fsub_rn(bhi.y, alo.y), __fsub_rn(ahi.y, blo.y));
-    float gz = fmaxf(__fsub_rn(bhi.z, alo.z), __fsub_rn(ahi.z, blo.z));
-    if (PER) {
-        if (!(gx <= __fmul_rn(0.5f, L.x)) || !(gy <= __fmul_rn(0.5f, L.y)) ||
-            !(gz <= __fmul_rn(0.5f, L.z)))
-            return false;
-    }
-    float d2 = __fadd_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)), __fmul_rn(gz, gz));
-    float r = fmaxf(ahi.w, bhi.w);
-    return d2 < __fmul_rn(r, r);
 }
 
 // ---------------------------------------------------------------------------
