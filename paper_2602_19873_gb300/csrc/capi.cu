@@ -432,6 +432,14 @@ nl_status do_prep(nl_list *nl, const float *x, const float *y, const float *z, c
     return NL_OK;
 }
 
+// Warp slots the staging arrays hold at the current per-slot capacity.
+uint32_t stage_slots(const nl_list *nl)
+{
+    const size_t c = (size_t)nl->stage_cap;
+    const size_t slots = std::min(nl->stageJ.cap / (4 * c), nl->stageM.cap / c);
+    return (uint32_t)std::min<size_t>(slots, 0xffffffffu);
+}
+
 // First search round over all super-clusters.  Open systems run without
 // periodic arithmetic; so do the interior super-clusters of periodic systems
 // (classified here, on the device, from this build's boxes and radii); only
@@ -568,6 +576,7 @@ nl_status do_search_half(nl_list *nl, cudaStream_t s)
         sa.stageJ = nl->stageJ.as<uint32_t>();
         sa.stageM = nl->stageM.as<uint8_t>();
         sa.stage_cap = nl->stage_cap;
+        sa.stage_slots = stage_slots(nl);
         sa.uJ = nl->uJ.as<uint32_t>();
         sa.uM = nl->uM.as<uint8_t>();
         sa.up_cap = nl->graph_up_cap;
@@ -597,6 +606,7 @@ nl_status do_search_half(nl_list *nl, cudaStream_t s)
         sa.stageJ = nl->stageJ.as<uint32_t>();
         sa.stageM = nl->stageM.as<uint8_t>();
         sa.stage_cap = nl->stage_cap;
+        sa.stage_slots = stage_slots(nl);
         sa.uJ = nl->uJ.as<uint32_t>();
         sa.uM = nl->uM.as<uint8_t>();
         sa.up_cap = upc;
@@ -765,6 +775,7 @@ nl_status do_search(nl_list *nl, cudaStream_t s)
         sa.stageJ = nl->stageJ.as<uint32_t>();
         sa.stageM = nl->stageM.as<uint8_t>();
         sa.stage_cap = nl->stage_cap;
+        sa.stage_slots = stage_slots(nl);
         sa.list = nl->list.as<uint8_t>();
         sa.list_cap = nl->list.cap - 8;  // 8 bytes of slack behind the last record
         if (work)
@@ -1387,6 +1398,15 @@ nl_status nl_graph_create(nl_list *nl, const float *x, const float *y, const flo
         CK(bigger.ensure(want));
         nl->list.release();
         nl->list = bigger;
+    }
+    {
+        // staging for the full persistent grid (the redo rounds of the build
+        // above may have grown the per-slot capacity on a smaller grid)
+        const int tpb = p->threads_per_block ? p->threads_per_block : 256;
+        const size_t slots = (size_t)nl->num_sms *
+                             (p->blocks_per_sm ? p->blocks_per_sm : kSearchBlocksPerSM) * (tpb / 32);
+        CK(nl->stageJ.ensure(slots * nl->stage_cap * 4));
+        CK(nl->stageM.ensure(slots * nl->stage_cap));
     }
     {
         // half search buffers: slack over the sizes of this build, and sort

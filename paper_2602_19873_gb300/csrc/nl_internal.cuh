@@ -525,6 +525,7 @@ struct SearchArgs {
     uint32_t *stageJ;
     uint8_t *stageM;
     uint32_t stage_cap;
+    uint32_t stage_slots;          // warp slots the staging arrays hold (stage_cap entries each)
     uint8_t *list;
     unsigned long long list_cap;
     uint32_t *rec_off;

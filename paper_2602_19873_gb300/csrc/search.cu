@@ -259,6 +259,9 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
     SearchSmem<M, MJ> &S = reinterpret_cast<SearchSmem<M, MJ> *>(search_smem)[threadIdx.x >> 5];
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
     const uint32_t slot = blockIdx.x * (blockDim.x >> 5) + warp;
+    // a warp without staging room stays idle; the work counter hands its
+    // super-clusters to the others (warps never wait on each other here)
+    if (slot >= a.stage_slots) return;
     uint32_t *stJ = a.stageJ + (size_t)slot * a.stage_cap;
     uint8_t *stM = a.stageM + (size_t)slot * a.stage_cap;
     const uint32_t II = lane % M;

@@ -89,3 +89,30 @@ def test_autotuner_returns_a_valid_faster_choice():
         a = _normal_density(dev, offs, boxes, base, stream)
         b = _normal_density(dev, offs, boxes, best, stream)
         assert np.max(np.abs(a - b) / a) < 2e-5
+
+
+def test_graph_after_staging_growth(monkeypatch):
+    """A build whose staging overflowed grows the per-slot capacity during
+    redo rounds on a smaller grid; the captured graph then runs the full
+    grid.  Its replays must stay within the staging arrays and match a
+    normal build."""
+    import torch
+    monkeypatch.setenv("NLGB_STAGE_CAP0", "64")
+    monkeypatch.setenv("NLGB_LIST_CAP0", "100000")
+    stream = torch.cuda.Stream()
+    systems, offs, dev = _batch(521, n_systems=6)
+    boxes = [d["box"] for d in systems]
+    p = nl.make_params(key=1, cluster=8, support=2.0)
+    with torch.cuda.stream(stream):
+        rho = torch.zeros(int(offs[-1]), dtype=torch.float32, device="cuda")
+        L = nl.NeighborList()
+        G = nl.Graph(L, dev["x"], dev["y"], dev["z"], dev["h"], dev["m"], rho, offs, boxes, p,
+                     stream)
+        want = _normal_density(dev, offs, boxes, p, stream)
+        rho.zero_()
+        for _ in range(2):
+            G.launch(stream)
+        G.check(stream)
+        assert np.array_equal(rho.cpu().numpy(), want)
+        G.free()
+        L.free()
