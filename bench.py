@@ -491,6 +491,163 @@ def run_batched(args):
         dist.destroy_process_group()
 
 
+CONFIGS = {
+    "uniform_32k": ("uniform_periodic_32k", "2^15 uniform particles in a periodic unit cube, "
+                    "constant h for 100 neighbors, Morton keys; build + density"),
+    "evrard_2m": ("evrard_2m", "2^21-particle Evrard sphere (rho ~ 1/r), h iterated to 200 +- 2; "
+                  "build + density + SPH pressure force (P = 2/3 rho u, u = 0.05)"),
+    "lj_fluid_4m": ("lj_fluid_4m", "4,000,000-atom jittered lattice at 100 nm^-3, periodic, "
+                    "rc = 0.9 nm (about 305 neighbors); build + Lennard-Jones force"),
+}
+
+
+def run_config(args):
+    """The other workloads: one step = build + the workload's passes."""
+    import torch
+    from paper_2602_19873_gb300 import nl
+    from paper_2602_19873_gb300 import workloads as wl
+
+    ws, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    init_ranks("nccl")
+    gen, desc = CONFIGS[args.workload]
+    seed = {"uniform_periodic_32k": 1, "evrard_2m": 2, "lj_fluid_4m": 3}[gen] + 100 * rank
+    d = wl.cached(wl.config, "%s_%d" % (gen, seed), gen, seed=seed)
+    n = len(d["x"])
+    dev = {k: torch.from_numpy(np.ascontiguousarray(d[k], dtype=np.float32)).cuda()
+           for k in ("x", "y", "z", "h", "m")}
+    params = nl.make_params(key=d["kind"], cluster=8, support=d["support"], compress=1,
+                            leaf_bucket=args.leaf_bucket)
+    stream = torch.cuda.current_stream()
+    if gen == "evrard_2m":  # smoothing lengths at 200 +- 2 neighbors (untimed input preparation)
+        H = nl.NeighborList()
+        H.iterate_h(dev["x"], dev["y"], dev["z"], dev["h"], d["box"], params, 200.0, 2.0,
+                    max_iter=60, margin=0.15, start=nl.NL_HSTART_PLAIN, stream=stream)
+        H.free()
+    L = nl.NeighborList()
+    L.set_profiling(True)
+    out0 = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+    rho = torch.empty(n, dtype=torch.float32, device="cuda")
+    pres = None
+    if gen == "evrard_2m":  # pressure from a density pass (an input field of the force pass)
+        L.build(dev["x"], dev["y"], dev["z"], dev["h"], d["box"], params, stream)
+        L.density_pass(dev["m"], rho, stream)
+        pres = rho * (2.0 / 3.0 * 0.05)
+
+    def step():
+        L.build(dev["x"], dev["y"], dev["z"], dev["h"], d["box"], params, stream)
+        if gen == "lj_fluid_4m":
+            L.force_pass(nl.NL_FORCE_LJ, *out0, eps=1.0, sigma=0.3, stream=stream)
+        else:
+            L.density_pass(dev["m"], rho, stream)
+            if gen == "evrard_2m":
+                L.force_pass(nl.NL_FORCE_SPH_PRESSURE, *out0, m=dev["m"], rho=rho, pres=pres,
+                             stream=stream)
+
+    quiesce_host()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(t0.elapsed_time(t1) / args.steps, ws, "cuda")
+    clk = clocks.stop()
+    sizes = L.sizes()
+    cnt = torch.empty(n, dtype=torch.int32, device="cuda")
+    L.neighbor_counts(cnt, stream)
+    useful = int(cnt.sum().item())
+    pairs = sizes["n_tiles"] * params.cluster * sizes["j_cluster"]
+    out = {"metric": "build+pass Mparticles/s (%s)" % args.workload,
+           "value": job_rate(n, ws, ms), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "%s: %s" % (args.workload, desc), "n": n,
+                      "l2": "inputs larger than L2 except uniform_32k (no flush)"},
+           "stages_ms": L.stage_times(),
+           "list": {"bytes_per_particle": sizes["list_bytes"] / n, "entries": sizes["n_entries"],
+                    "computed_pairs": pairs, "gather_pairs": useful,
+                    "cluster_overhead": pairs / float(useful + n)},
+           "e2e": None, "gpu_launches": None, "clocks": clk}
+    if rank == 0 and not args.no_cpu_baseline:
+        ns = min(n, args.cpu_sample or (1 << 18))
+        samp = wl.config(gen, scale=ns / float(n), seed=seed)
+        import oracle
+        oracle.build()
+        t = time.perf_counter()
+        oracle_step(samp)
+        dt = time.perf_counter() - t
+        out["cpu_baseline"] = {"value": len(samp["x"]) / dt / 1e6, "unit": UNIT,
+                               "cores": oracle.num_threads(), "kind": "oracle",
+                               "sample": "oracle build + density of the same generator at %d "
+                                         "particles, %.1f s" % (len(samp["x"]), dt)}
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_sweep(args):
+    """List size and cluster overhead against the neighbor count on the LJ
+    fluid (100 nm^-3): 8x8 and 8x4 tiles, compressed and raw lists, build and
+    Lennard-Jones pass times."""
+    import torch
+    from paper_2602_19873_gb300 import nl
+    from paper_2602_19873_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    d = wl.cached(wl.config, "lj_fluid_4m_3", "lj_fluid_4m", seed=3)
+    n = len(d["x"])
+    dev = {k: torch.from_numpy(np.ascontiguousarray(d[k], dtype=np.float32)).cuda()
+           for k in ("x", "y", "z", "m")}
+    stream = torch.cuda.current_stream()
+    out0 = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+    cnt = torch.empty(n, dtype=torch.int32, device="cuda")
+    rows = []
+    quiesce_host()
+    for nb in (25, 50, 100, 200, 400, 800, 1600):
+        rc = (3.0 * nb / (4.0 * math.pi * 100.0)) ** (1.0 / 3.0)
+        h = torch.full((n,), rc, dtype=torch.float32, device="cuda")
+        for (M, MJ) in ((8, 8), (8, 4)):
+            for comp in (1, 0):
+                p = nl.make_params(key=1, cluster=M, j_cluster=MJ, support=1.0, compress=comp)
+                L = nl.NeighborList()
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                for r in range(4):
+                    if r == 3:
+                        e[0].record(stream)
+                    L.build(dev["x"], dev["y"], dev["z"], h, d["box"], p, stream)
+                    if r == 3:
+                        e[1].record(stream)
+                    L.force_pass(nl.NL_FORCE_LJ, *out0, eps=1.0, sigma=0.3, stream=stream)
+                    if r == 3:
+                        e[2].record(stream)
+                torch.cuda.synchronize()
+                sz = L.sizes()
+                if (M, MJ, comp) == (8, 8, 1):
+                    L.neighbor_counts(cnt, stream)
+                    useful = int(cnt.sum().item())
+                pairs = sz["n_tiles"] * M * MJ
+                rows.append({"neighbors_target": nb, "rc_nm": rc, "tile": "%dx%d" % (M, MJ),
+                             "compressed": bool(comp),
+                             "mean_neighbors": useful / n,
+                             "bytes_per_particle": sz["list_bytes"] / n,
+                             "full_list_bytes_per_particle": 4.0 * useful / n,
+                             "cluster_overhead": pairs / float(useful + n),
+                             "build_ms": e[0].elapsed_time(e[1]),
+                             "lj_pass_ms": e[1].elapsed_time(e[2])})
+                L.free()
+    print(json.dumps({"sweep": "LJ fluid 4,000,000 atoms at 100 nm^-3, periodic, Hilbert keys, "
+                               "leaf bucket 256; list radius for the target neighbor count",
+                      "rows": rows}))
+
+
 def oracle_step(d):
     """The oracle's build + density on one system: keys, stable sort, FP64
     cell-list gather sets, symmetric sets, per-super-cluster records, density."""
@@ -577,12 +734,19 @@ def main():
     ap.add_argument("--tile", default="8x8", choices=["8x8", "8x4", "16x8", "16x16", "4x4"],
                     help="i-cluster x j-cluster size of the single-system bench")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-h comparison")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched_256"])
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "batched_256"] + sorted(CONFIGS))
+    ap.add_argument("--sweep", action="store_true",
+                    help="list size / cluster overhead / times against the neighbor count (LJ fluid)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.sweep:
+        run_sweep(args)
     elif args.workload == "batched_256":
         run_batched(args)
+    elif args.workload in CONFIGS:
+        run_config(args)
     else:
         run_native(args)
 
