@@ -21,7 +21,8 @@ __all__ = [
     "build", "lib", "Box", "quantize", "morton3", "hilbert3", "hilbert3_inverse", "keys",
     "sort", "octree", "brute_neighbors", "gather_all", "symmetrize", "cluster_lists",
     "encode_block", "encode_record", "decode_record", "record_bytes", "stream_nibbles",
-    "w", "dw", "W", "density", "sph_force", "lj_force", "lj_energy", "gather_counts_brute",
+    "w", "dw", "W", "density", "sph_force", "lj_force", "lj_energy", "ljc_force", "ljc_energy",
+    "gather_counts_brute",
     "pred", "dist2", "dist2_row", "num_threads", "pipeline_lists", "mlp_nparams",
     "mlp_forward", "mlp_loss_grad",
 ]
@@ -98,6 +99,10 @@ def lib():
                 "orc_sph_force": (None, [P] * 14),
                 "orc_lj_force": (None, [P, P, P, P, C.c_double, C.c_double, P, P, P, P, P, P]),
                 "orc_lj_energy": (C.c_double, [P, P, P, P, C.c_double, C.c_double, P]),
+                "orc_ljc_force": (None, [P, P, P, P, C.c_double, C.c_double, P, C.c_double, P,
+                                         P, P, P, P, P]),
+                "orc_ljc_energy": (C.c_double, [P, P, P, P, C.c_double, C.c_double, P,
+                                                C.c_double, P]),
                 "orc_gather_counts_brute": (None, [I64, P, P, P, P, P, F32, I64, P, P]),
                 "orc_dist2_row": (None, [I64, P, P, P, P, I64, P]),
                 "orc_num_threads": (C.c_int, []),
@@ -380,6 +385,38 @@ def lj_energy(xs, ys, zs, box, eps, sigma, off, idx):
     b = _box(box)
     try:
         return lib().orc_lj_energy(_p(xs), _p(ys), _p(zs), C.byref(b), float(eps), float(sigma), h)
+    finally:
+        lib().orc_csr_free(h)
+
+
+def ljc_force(xs, ys, zs, box, eps, sigma, q, kc, off, idx, rows):
+    """FP64 Lennard-Jones + cutoff Coulomb force of particles rows over the
+    interaction sets (off, idx); q None: no Coulomb term.  Also sum_j |f_ij|."""
+    xs, ys, zs = (_f32(a) for a in (xs, ys, zs))
+    qq = None if q is None else _f32(q)
+    h, keep = _csr_make(off, idx)
+    rows = _i64(rows)
+    if len(rows) != len(off) - 1:
+        raise ValueError("one row index per CSR row")
+    fx, fy, fz, fa = (np.zeros(len(rows)) for _ in range(4))
+    b = _box(box)
+    try:
+        lib().orc_ljc_force(_p(xs), _p(ys), _p(zs), C.byref(b), float(eps), float(sigma),
+                            None if qq is None else _p(qq), float(kc), h, _p(rows), _p(fx),
+                            _p(fy), _p(fz), _p(fa))
+    finally:
+        lib().orc_csr_free(h)
+    return fx, fy, fz, fa
+
+
+def ljc_energy(xs, ys, zs, box, eps, sigma, q, kc, off, idx):
+    xs, ys, zs = (_f32(a) for a in (xs, ys, zs))
+    qq = None if q is None else _f32(q)
+    h, keep = _csr_make(off, idx)
+    b = _box(box)
+    try:
+        return lib().orc_ljc_energy(_p(xs), _p(ys), _p(zs), C.byref(b), float(eps), float(sigma),
+                                    None if qq is None else _p(qq), float(kc), h)
     finally:
         lib().orc_csr_free(h)
 

@@ -46,6 +46,10 @@
  *        a_i = -sum_j m_j [P_i/rho_i^2 grad_i W(r_ij,h_i) + P_j/rho_j^2 grad_i W(r_ij,h_j)]
  *    over the symmetric neighbor set.
  *  - LJ: F_i = sum_j 24 eps (2 s^12/r^14 - s^6/r^8) (x_i - x_j), no shift.
+ *  - LJ + Coulomb (Sec. III-B): the LJ term plus kc q_i q_j (x_i - x_j)/r^3
+ *    over the pairs within the interaction cutoff rc, plain cutoff (no shift,
+ *    no reaction field); the list is built at a larger radius (Verlet buffer)
+ *    and the interaction set is the gather set at rc.
  *
  * Parity unpinned: orc_cluster_overhead's normalisation (the paper's Fig. 2
  * values are not printed); it is reported, never compared.
@@ -1042,6 +1046,63 @@ double orc_lj_energy(const float *xs, const float *ys, const float *zs, const or
             double sr2 = sigma * sigma / (dx * dx + dy * dy + dz * dz);
             double sr6 = sr2 * sr2 * sr2;
             e += 4.0 * eps * (sr6 * sr6 - sr6);
+        }
+    }
+    return e;
+}
+
+/* Lennard-Jones 12/6 plus Coulomb with a plain cutoff (Sec. III-B names the
+ * two interactions; the cutoff form is our reading): over the pairs of P (the
+ * interaction set, i.e. the gather set at the interaction radius rc),
+ *   F_i = sum_j [24 eps (2 s^12/r^14 - s^6/r^8) + kc q_i q_j / r^3] (x_i - x_j),
+ * the negative gradient of
+ *   E = sum_{i<j} [4 eps ((s/r)^12 - (s/r)^6) + kc q_i q_j / r].
+ * q may be NULL (no Coulomb term).  fabs_sum[k] = sum_j |f_ij|. */
+void orc_ljc_force(const float *xs, const float *ys, const float *zs, const orc_box *b,
+                   double eps, double sigma, const float *q, double kc, const orc_csr *P,
+                   const int64_t *rows, double *fx, double *fy, double *fz, double *fabs_sum)
+{
+    double s6 = pow(sigma, 6.0), s12 = s6 * s6;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < P->n; ++k) {
+        int64_t i = rows[k];
+        double ax = 0, ay = 0, az = 0, fa = 0;
+        for (int64_t t = P->off[k]; t < P->off[k + 1]; ++t) {
+            int64_t j = P->idx[t];
+            double dx = dx64(xs, i, j, b, 0), dy = dx64(ys, i, j, b, 1), dz = dx64(zs, i, j, b, 2);
+            double r2 = dx * dx + dy * dy + dz * dz;
+            double r = sqrt(r2);
+            double r4 = r2 * r2, r8 = r4 * r4, r14 = r8 * r4 * r2;
+            double c = 24.0 * eps * (2.0 * s12 / r14 - s6 / r8);
+            if (q) c += kc * (double)q[i] * (double)q[j] / (r2 * r);
+            /* x_i - x_j = -(dx, dy, dz) */
+            ax += c * (-dx);
+            ay += c * (-dy);
+            az += c * (-dz);
+            fa += fabs(c) * r;
+        }
+        fx[k] = ax;
+        fy[k] = ay;
+        fz[k] = az;
+        if (fabs_sum) fabs_sum[k] = fa;
+    }
+}
+
+double orc_ljc_energy(const float *xs, const float *ys, const float *zs, const orc_box *b,
+                      double eps, double sigma, const float *q, double kc, const orc_csr *P)
+{
+    double e = 0.0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : e)
+    for (int64_t i = 0; i < P->n; ++i) {
+        for (int64_t t = P->off[i]; t < P->off[i + 1]; ++t) {
+            int64_t j = P->idx[t];
+            if (j <= i) continue;
+            double dx = dx64(xs, i, j, b, 0), dy = dx64(ys, i, j, b, 1), dz = dx64(zs, i, j, b, 2);
+            double r2 = dx * dx + dy * dy + dz * dz;
+            double sr2 = sigma * sigma / r2;
+            double sr6 = sr2 * sr2 * sr2;
+            e += 4.0 * eps * (sr6 * sr6 - sr6);
+            if (q) e += kc * (double)q[i] * (double)q[j] / sqrt(r2);
         }
     }
     return e;

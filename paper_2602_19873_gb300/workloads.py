@@ -15,6 +15,9 @@ Evrard sphere of Sec. IV; none of the paper's data ships):
                  (radius r = u^(1/2)), non-periodic.
   lj_fluid    -- cubic lattice at 100 particles/nm^3 in a periodic cube,
                  Gaussian jitter 0.05 nm, single cutoff.
+  lj_coulomb  -- the same fluid with charges +-1 (neutral) and two radii:
+                 the list radius (about 200 neighbors) and the shorter
+                 interaction cutoff (about 150), the Verlet-buffer shape.
   plummer     -- several Plummer spheres with log-uniform scale radii,
                  centres uniform in the unit box, non-periodic, bbox box.
   batched     -- many independent systems of log-uniform size, alternating
@@ -102,6 +105,25 @@ def lj_fluid(n=4_000_000, seed=3, density=100.0, rc=0.9, jitter=0.05):
             "m": np.ones(n, np.float32), "h": np.full(n, np.float32(rc), np.float32),
             "box": _box([0, 0, 0], [Lf, Lf, Lf], [1, 1, 1]), "kind": KIND_HILBERT,
             "support": 1.0, "rc": rc, "eps": 1.0, "sigma": 0.3, "L": float(Lf)}
+
+
+def lj_coulomb(n=4_000_000, seed=6, density=100.0, n_list=200.0, n_int=150.0, jitter=0.05):
+    """lj_fluid with charges and a Verlet buffer: h = r_list holds n_list
+    expected neighbors, rc = r_int holds n_int (spheres at `density`); charges
+    +1 on a random half and -1 on the rest (zero for an odd one out).  kc is
+    the Coulomb constant in kJ mol^-1 nm e^-2."""
+    r_list = (3.0 * n_list / (4.0 * math.pi * density)) ** (1.0 / 3.0)
+    r_int = (3.0 * n_int / (4.0 * math.pi * density)) ** (1.0 / 3.0)
+    d = lj_fluid(n, seed=seed, density=density, rc=r_list, jitter=jitter)
+    rng = np.random.default_rng(seed + 1000)
+    q = np.zeros(n, np.float32)
+    order = rng.permutation(n)
+    half = n // 2
+    q[order[:half]] = 1.0
+    q[order[half:2 * half]] = -1.0
+    d.update({"name": "lj_coulomb", "q": q, "rc": float(np.float32(r_int)),
+              "r_list": float(np.float32(r_list)), "kc": 138.935458})
+    return d
 
 
 def _plummer_radii(rng, n, a):
@@ -197,13 +219,15 @@ def cached(fn, key, *args, **kw):
 
 
 def config(name, scale=1.0, seed=None):
-    """The five named workloads at full size (scale=1) or shrunk for tests."""
+    """The six named workloads at full size (scale=1) or shrunk for tests."""
     if name == "uniform_periodic_32k":
         return uniform(max(8, int(32768 * scale)), seed=1 if seed is None else seed)
     if name == "evrard_2m":
         return evrard(max(8, int((1 << 21) * scale)), seed=2 if seed is None else seed)
     if name == "lj_fluid_4m":
         return lj_fluid(max(8, int(4_000_000 * scale)), seed=3 if seed is None else seed)
+    if name == "lj_coulomb_4m":
+        return lj_coulomb(max(8, int(4_000_000 * scale)), seed=6 if seed is None else seed)
     if name == "plummer64_16m":
         n = max(64, int((1 << 24) * scale))
         return plummer(n, n_spheres=64 if n >= 64 * 64 else max(1, n // 64),

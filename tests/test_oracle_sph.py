@@ -153,3 +153,101 @@ def test_lj_force_energy_and_newton3(orc):
             if abs(grad) > 1e3 * abs(F[k, a]) + 1e3:
                 continue  # a pair crossed rc inside the step (energy jump)
             assert F[k, a] == pytest.approx(-grad, rel=1e-3, abs=1e-3)
+
+
+def _pair_system(p1, p2, box=None):
+    xs, ys, zs = (np.array([p1[a], p2[a]], np.float32) for a in range(3))
+    if box is None:
+        box = {"lo": np.full(3, -10, np.float32), "hi": np.full(3, 10, np.float32),
+               "periodic": np.zeros(3, np.int32)}
+    off = np.array([0, 1, 2], np.int64)
+    idx = np.array([1, 0], np.int64)
+    return xs, ys, zs, box, off, idx
+
+
+def test_ljc_two_particles_closed_forms(orc):
+    """Coulomb's law and the LJ minimum for one pair (Sec. III-B interactions)."""
+    xs, ys, zs, box, off, idx = _pair_system((0.1, -0.2, 0.3), (0.5, 0.1, -0.3))
+    P = np.stack([xs, ys, zs], 1).astype(np.float64)
+    u = P[0] - P[1]
+    r = float(np.linalg.norm(u))
+    q = np.array([2.0, -0.5], np.float32)
+    kc = 1.5
+    # Coulomb only: |F| = kc q1 q2 / r^2 along the unit vector from 2 to 1
+    fx, fy, fz, fa = orc.ljc_force(xs, ys, zs, box, 0.0, 0.3, q, kc, off, idx, [0, 1])
+    want = kc * 2.0 * -0.5 / r ** 2 * (u / r)
+    assert np.allclose([fx[0], fy[0], fz[0]], want, rtol=1e-12, atol=0)
+    assert np.allclose([fx[1], fy[1], fz[1]], -want, rtol=1e-12, atol=0)
+    assert fa[0] == pytest.approx(abs(kc * 2.0 * -0.5) / r ** 2, rel=1e-12)
+    assert orc.ljc_energy(xs, ys, zs, box, 0.0, 0.3, q, kc, off, idx) == pytest.approx(
+        kc * 2.0 * -0.5 / r, rel=1e-12)
+    # LJ only at the potential minimum r = 2^(1/6) sigma: zero force, E = -eps
+    sig = r / 2 ** (1 / 6)
+    fx, fy, fz, _ = orc.ljc_force(xs, ys, zs, box, 0.8, sig, None, kc, off, idx, [0, 1])
+    assert max(abs(fx[0]), abs(fy[0]), abs(fz[0])) < 1e-12
+    assert orc.ljc_energy(xs, ys, zs, box, 0.8, sig, None, kc, off, idx) == pytest.approx(-0.8, rel=1e-12)
+    # repulsive inside the minimum: the force on 1 points away from 2
+    fx, fy, fz, _ = orc.ljc_force(xs, ys, zs, box, 0.8, 1.1 * sig, None, kc, off, idx, [0, 1])
+    assert float(np.dot([fx[0], fy[0], fz[0]], u)) > 0
+
+
+def test_ljc_periodic_minimum_image(orc):
+    """A pair straddling a periodic face interacts across it (distance 0.2,
+    not 0.8)."""
+    box = {"lo": np.zeros(3, np.float32), "hi": np.ones(3, np.float32),
+           "periodic": np.ones(3, np.int32)}
+    xs, ys, zs, box, off, idx = _pair_system((0.05, 0.5, 0.5), (0.85, 0.5, 0.5), box)
+    q = np.array([1.0, 1.0], np.float32)
+    fx, fy, fz, _ = orc.ljc_force(xs, ys, zs, box, 0.0, 0.3, q, 1.0, off, idx, [0, 1])
+    r = float(np.float32(1.0) - (np.float32(0.85) - np.float32(0.05)))
+    # like charges repel: particle 0 is pushed in +x (away from its image at -0.15)
+    assert fx[0] == pytest.approx(1.0 / r ** 2, rel=1e-6)
+    assert abs(fy[0]) < 1e-12 and abs(fz[0]) < 1e-12
+
+
+def test_ljc_reduces_to_lj_without_charges(orc):
+    d = wl.lj_fluid(800, seed=36)
+    xs, ys, zs, hs, ms = _sorted(orc, d)
+    g_off, g_idx = orc.gather_all(xs, ys, zs, hs, d["box"], 1.0)
+    rows = np.arange(len(xs))
+    a = orc.lj_force(xs, ys, zs, d["box"], 1.0, 0.3, g_off, g_idx, rows)
+    b = orc.ljc_force(xs, ys, zs, d["box"], 1.0, 0.3, None, 138.9, g_off, g_idx, rows)
+    c = orc.ljc_force(xs, ys, zs, d["box"], 1.0, 0.3, np.zeros(len(xs), np.float32), 138.9,
+                      g_off, g_idx, rows)
+    for u, v, w in zip(a, b, c):
+        assert np.array_equal(u, v) and np.array_equal(u, w)
+
+
+def test_ljc_force_is_minus_energy_gradient(orc):
+    """Newton III and F = -dE/dx for LJ + Coulomb at the interaction cutoff of
+    the Verlet-buffer workload (pairs that cross rc inside the step skipped)."""
+    d = wl.lj_coulomb(1500, seed=37)
+    k_ = orc.keys(d["x"], d["y"], d["z"], d["box"], d["kind"])
+    p = orc.sort(k_)
+    xs, ys, zs, q = (np.asarray(d[a])[p] for a in ("x", "y", "z", "q"))
+    box, rc, kc = d["box"], d["rc"], d["kc"]
+    hr = np.full(len(xs), np.float32(rc))
+    g_off, g_idx = orc.gather_all(xs, ys, zs, hr, box, 1.0)
+    n = len(xs)
+    fx, fy, fz, fa = orc.ljc_force(xs, ys, zs, box, 1.0, 0.3, q, kc, g_off, g_idx, np.arange(n))
+    F = np.stack([fx, fy, fz], 1)
+    assert np.abs(F.sum(0)).max() < 1e-10 * np.abs(F).sum()
+    assert abs(float(q.astype(np.float64).sum())) <= 1.0
+    checked = 0
+    for k in (5, n // 3, n - 7):
+        for a, arr in enumerate((xs, ys, zs)):
+            vals = []
+            for sgn in (+1, -1):
+                pert = [xs.copy(), ys.copy(), zs.copy()]
+                pert[a][k] = np.float32(float(arr[k]) + sgn * 1e-4)
+                go, gi = orc.gather_all(*pert, hr, box, 1.0)
+                if not (np.array_equal(go, g_off) and np.array_equal(gi, g_idx)):
+                    vals = None  # the pair set changed inside the step (energy jump)
+                    break
+                vals.append((orc.ljc_energy(*pert, box, 1.0, 0.3, q, kc, go, gi), float(pert[a][k])))
+            if vals is None:
+                continue
+            grad = (vals[0][0] - vals[1][0]) / (vals[0][1] - vals[1][1])
+            assert F[k, a] == pytest.approx(-grad, rel=1e-3, abs=1e-6 * np.abs(F).max())
+            checked += 1
+    assert checked >= 6
