@@ -498,7 +498,50 @@ CONFIGS = {
                   "build + density + SPH pressure force (P = 2/3 rho u, u = 0.05)"),
     "lj_fluid_4m": ("lj_fluid_4m", "4,000,000-atom jittered lattice at 100 nm^-3, periodic, "
                     "rc = 0.9 nm (about 305 neighbors); build + Lennard-Jones force"),
+    "lj_coulomb_4m": ("lj_coulomb_4m", "4,000,000-atom jittered lattice at 100 nm^-3, periodic, "
+                      "charges +-1; list radius 0.7816 nm (about 200 neighbors), interaction "
+                      "cutoff 0.7102 nm (about 150); build + Lennard-Jones + Coulomb force, the "
+                      "list rebuilt every step; 'reuse' times refresh + force on a kept list"),
 }
+
+
+def reuse_timing(L, d, dev, out0, args, stream, ws):
+    """Steps on a kept list (Verlet buffer): positions moved by up to 0.45 of
+    the skin r_list - rc, then per step nl_refresh_positions + the LJ +
+    Coulomb force, timed like the rebuild steps."""
+    import torch
+    from paper_2602_19873_gb300 import nl
+    rng = np.random.default_rng(17)
+    n = len(d["x"])
+    v = rng.normal(size=(n, 3))
+    v *= (0.45 * (d["r_list"] - d["rc"]) * rng.random(n) / np.linalg.norm(v, axis=1))[:, None]
+    Lf = np.float32(d["L"])
+    moved = {}
+    for a, k in enumerate(("x", "y", "z")):
+        p = (np.asarray(d[k], np.float64) + v[:, a]).astype(np.float32)
+        p = np.where(p < 0, p + Lf, p)
+        p = np.where(p >= Lf, p - Lf, p).astype(np.float32)
+        moved[k] = torch.from_numpy(np.ascontiguousarray(p)).cuda()
+    md = torch.zeros(1, dtype=torch.float32, device="cuda")
+
+    def step():
+        L.refresh_positions(moved["x"], moved["y"], moved["z"], md, stream)
+        L.force_pass(nl.NL_FORCE_LJ_COULOMB, *out0, m=dev["q"], eps=d["eps"], sigma=d["sigma"],
+                     rc=d["rc"], kc=d["kc"], stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(t0.elapsed_time(t1) / args.steps, ws, "cuda")
+    return {"ms_per_step": ms, "value": job_rate(n, ws, ms), "unit": UNIT,
+            "max_disp_nm": float(md.item()), "skin_nm": d["r_list"] - d["rc"]}
 
 
 def run_config(args):
@@ -511,11 +554,12 @@ def run_config(args):
     torch.cuda.set_device(local)
     init_ranks("nccl")
     gen, desc = CONFIGS[args.workload]
-    seed = {"uniform_periodic_32k": 1, "evrard_2m": 2, "lj_fluid_4m": 3}[gen] + 100 * rank
+    seed = {"uniform_periodic_32k": 1, "evrard_2m": 2, "lj_fluid_4m": 3,
+            "lj_coulomb_4m": 6}[gen] + 100 * rank
     d = wl.cached(wl.config, "%s_%d" % (gen, seed), gen, seed=seed)
     n = len(d["x"])
     dev = {k: torch.from_numpy(np.ascontiguousarray(d[k], dtype=np.float32)).cuda()
-           for k in ("x", "y", "z", "h", "m")}
+           for k in ("x", "y", "z", "h", "m") + (("q",) if "q" in d else ())}
     params = nl.make_params(key=d["kind"], cluster=8, support=d["support"], compress=1,
                             leaf_bucket=args.leaf_bucket)
     stream = torch.cuda.current_stream()
@@ -538,6 +582,9 @@ def run_config(args):
         L.build(dev["x"], dev["y"], dev["z"], dev["h"], d["box"], params, stream)
         if gen == "lj_fluid_4m":
             L.force_pass(nl.NL_FORCE_LJ, *out0, eps=1.0, sigma=0.3, stream=stream)
+        elif gen == "lj_coulomb_4m":
+            L.force_pass(nl.NL_FORCE_LJ_COULOMB, *out0, m=dev["q"], eps=d["eps"],
+                         sigma=d["sigma"], rc=d["rc"], kc=d["kc"], stream=stream)
         else:
             L.density_pass(dev["m"], rho, stream)
             if gen == "evrard_2m":
@@ -575,6 +622,8 @@ def run_config(args):
                     "computed_pairs": pairs, "gather_pairs": useful,
                     "cluster_overhead": pairs / float(useful + n)},
            "e2e": None, "gpu_launches": None, "clocks": clk}
+    if gen == "lj_coulomb_4m":
+        out["reuse"] = reuse_timing(L, d, dev, out0, args, stream, ws)
     if rank == 0 and not args.no_cpu_baseline:
         ns = min(n, args.cpu_sample or (1 << 18))
         samp = wl.config(gen, scale=ns / float(n), seed=seed)
@@ -585,8 +634,10 @@ def run_config(args):
         dt = time.perf_counter() - t
         out["cpu_baseline"] = {"value": len(samp["x"]) / dt / 1e6, "unit": UNIT,
                                "cores": oracle.num_threads(), "kind": "oracle",
-                               "sample": "oracle build + density of the same generator at %d "
-                                         "particles, %.1f s" % (len(samp["x"]), dt)}
+                               "sample": "oracle build + %s of the same generator at %d "
+                                         "particles, %.1f s" % (
+                                             "LJ + Coulomb force" if "q" in samp else "density",
+                                             len(samp["x"]), dt)}
     if rank == 0:
         print(json.dumps(out))
     if ws > 1:
@@ -663,6 +714,12 @@ def oracle_step(d):
     nbytes = 0
     for t in range(nsc):
         nbytes += len(oracle.encode_record(J[so[t]:so[t + 1]], m[so[t]:so[t + 1]], 32, True))
+    if "q" in d:  # LJ + Coulomb over the pairs within the interaction cutoff
+        hr = np.full(n, np.float32(d["rc"]), np.float32)
+        i_off, i_idx = oracle.gather_all(*s[:3], hr, d["box"], 1.0)
+        f = oracle.ljc_force(*s[:3], d["box"], d["eps"], d["sigma"], d["q"][perm], d["kc"],
+                             i_off, i_idx, np.arange(n))
+        return f, nbytes
     rho = oracle.density(*s, d["box"], g_off, g_idx, np.arange(n))
     return rho, nbytes
 

@@ -131,9 +131,20 @@ nl_status nl_density_pass(const nl_list *nl, const float *m, float *rho, void *s
  *  NL_FORCE_LJ: over gather pairs (i != j, d2 < ri^2),
  *    F_i = sum_j 24 eps (2 sigma^12 / r^14 - sigma^6 / r^8) (x_i - x_j);
  *    params = host {eps, sigma}; m, rho, pres unused (may be NULL).
+ *  NL_FORCE_LJ_COULOMB (Sec. III-B: 12/6 Lennard-Jones and Coulomb, the list
+ *    built at a larger radius than the interaction cutoff): over the listed
+ *    gather pairs inside the cutoff (i != j, d2 < ri^2 and d2 < rc^2, rc^2
+ *    rounded once in FP32),
+ *    F_i = sum_j [24 eps (2 sigma^12 / r^14 - sigma^6 / r^8) + kc q_i q_j / r^3] (x_i - x_j),
+ *    plain cutoff (no shift).  params = host {eps, sigma, rc, kc}, rc = 0 for
+ *    the list radius alone; m = the charges q (n device floats, caller order;
+ *    NULL: all zero); rho, pres unused.  NL_ERR_ARG for non-finite eps, kc or
+ *    rc, sigma <= 0 or rc < 0.  With rc below every list radius the result is
+ *    the force over all pairs within rc, also after nl_refresh_positions as
+ *    long as twice its max_disp stays below min(ri) - rc.
  * ax, ay, az: n device floats written in caller order.  FP32 arithmetic with
  * block-partial sums.  Does not synchronise. */
-enum { NL_FORCE_SPH_PRESSURE = 0, NL_FORCE_LJ = 1 };
+enum { NL_FORCE_SPH_PRESSURE = 0, NL_FORCE_LJ = 1, NL_FORCE_LJ_COULOMB = 2 };
 nl_status nl_force_pass(const nl_list *nl, int32_t kind, const float *params, const float *m,
                         const float *rho, const float *pres, float *ax, float *ay, float *az,
                         void *stream);
@@ -141,6 +152,23 @@ nl_status nl_force_pass(const nl_list *nl, int32_t kind, const float *params, co
 /* Gather-neighbor count of every particle (j != i with d2 < ri^2), caller
  * order, n device uint32.  Does not synchronise. */
 nl_status nl_neighbor_counts(const nl_list *nl, uint32_t *counts, void *stream);
+
+/* List reuse across steps (the Verlet buffer of Sec. III-B and its
+ * production remark: a list built at radius r_list serves an interaction
+ * cutoff rc < r_list while particles move less than (r_list - rc)/2).
+ * x, y, z: n device floats in caller order, the new positions, on periodic
+ * axes inside [lo, hi) as for nl_build; h and the list are kept.  The passes
+ * that follow read these positions and the listed pairs; on periodic systems
+ * the super-clusters that may hold a wrapped pair are found again for the new
+ * positions (two small kernels), so the others keep the kernel without
+ * periodic arithmetic.  max_disp: one
+ * device float or NULL; set to the largest displacement of any particle from
+ * the positions the list was built on (minimum image on periodic axes, FP32),
+ * so that the caller rebuilds once 2 * max_disp reaches r_list - rc.  The
+ * next build or rebuild drops the reference positions.  NL_ERR_ARG for an
+ * empty list or a NULL array.  Does not synchronise. */
+nl_status nl_refresh_positions(nl_list *nl, const float *x, const float *y, const float *z,
+                               float *max_disp, void *stream);
 
 /* Releases the list and its device memory (after the stream work using it
  * has completed; nl_free synchronises the device).  nl_free(NULL) = NL_OK. */

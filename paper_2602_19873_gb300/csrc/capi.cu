@@ -118,6 +118,10 @@ struct nl_list {
     DevBuf sc_int, sc_bnd;
     DevBuf perm_pad, sys_off, sys_pad, sys_box, sys_root, sys_hcap;
     int32_t nsys = 1;
+    // positions replaced since the search (nl_refresh_positions); pos_ref
+    // keeps the positions the list was built on
+    int moved = 0;
+    DevBuf pos_ref;
     uint32_t node_cap = 0;
     const struct nl_mlp *mlp = nullptr;
     DevBuf ml_X, ml_e64, ml_pred, ml_slo, ml_shi;
@@ -178,7 +182,8 @@ struct nl_list {
                          &it_hlo, &it_hhi, &it_hs, &it_counts, &it_conv, &it_aflag, &it_alist,
                          &it_words, &it_tmp, &ml_X, &ml_e64, &ml_pred, &ml_slo, &ml_shi,
                          &uJ, &uM, &up_off, &up_cnt, &lower_cnt, &seg_off, &tkey, &tkey_alt,
-                         &tval, &tval_alt, &thist, &sc_open, &sc_per, &sc_int, &sc_bnd};
+                         &tval, &tval_alt, &thist, &sc_open, &sc_per, &sc_int, &sc_bnd,
+                         &pos_ref};
         for (DevBuf *b : all) b->release();
         for (int i = 0; i <= kStages; ++i)
             if (ev[i]) cudaEventDestroy(ev[i]);
@@ -718,6 +723,7 @@ nl_status do_search_half(nl_list *nl, cudaStream_t s)
 // rounds for overflows.  Sets nl->n on success.
 nl_status do_search(nl_list *nl, cudaStream_t s)
 {
+    nl->moved = 0;  // the list is built on the positions it holds
     {
         // the half search needs j-clusters = i-clusters; NLGB_SEARCH=full
         // forces the full search (tests run both)
@@ -1626,8 +1632,67 @@ nl_status nl_force_pass(const nl_list *cnl, int32_t kind, const float *params, c
         CK(nl->mark(7, s));
         CK(run_pass(nl, a, PASS_LJ, s));
         CK(nl->mark(8, s));
+    } else if (kind == NL_FORCE_LJ_COULOMB) {
+        if (!params) return fail(NL_ERR_ARG, "LJ + Coulomb needs params {eps, sigma, rc, kc}");
+        if (!std::isfinite(params[0]) || !(params[1] > 0.f) || !(params[2] >= 0.f) ||
+            !std::isfinite(params[2]) || !std::isfinite(params[3]))
+            return fail(NL_ERR_ARG, "LJ + Coulomb needs finite eps, kc, sigma > 0 and rc >= 0");
+        CK(nl->aux.ensure((size_t)nl->npad * 8));
+        a = pass_args(nl);
+        a.out0 = ax;
+        a.out1 = ay;
+        a.out2 = az;
+        a.p0 = params[0];
+        a.p1 = params[1];
+        a.p2 = params[2] > 0.f ? params[2] * params[2] : INFINITY;  // rounded once, as the predicate's r^2
+        a.p3 = params[3];
+        CK(nl->mark(6, s));
+        if (m)
+            CK(launch_gather_aux(nl->npad, nl->perm_pad.as<uint32_t>(), m, nullptr, nullptr, 0,
+                                 nl->aux.as<float2>(), s));
+        else
+            CK(cudaMemsetAsync(nl->aux.p, 0, (size_t)nl->npad * 8, s));
+        CK(nl->mark(7, s));
+        CK(run_pass(nl, a, PASS_LJC, s));
+        CK(nl->mark(8, s));
     } else {
         return fail(NL_ERR_ARG, "unknown force kind %d", kind);
+    }
+    return NL_OK;
+}
+
+nl_status nl_refresh_positions(nl_list *nl, const float *x, const float *y, const float *z,
+                               float *max_disp, void *stream)
+{
+    nl_status st = check_list(nl);
+    if (st != NL_OK) return st;
+    if (!x || !y || !z) return fail(NL_ERR_ARG, "NULL position array");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!nl->moved) {
+        CK(nl->pos_ref.ensure((size_t)nl->npad * sizeof(float4)));
+        CK(cudaMemcpyAsync(nl->pos_ref.p, nl->pos.p, (size_t)nl->npad * sizeof(float4),
+                           cudaMemcpyDeviceToDevice, s));
+    }
+    CK(launch_refresh(nl->npad, nl->perm_pad.as<uint32_t>(), nl->tables(), x, y, z,
+                      nl->pos.as<float4>(), nl->pos_ref.as<float4>(), max_disp, s));
+    nl->moved = 1;
+    if (nl->any_per) {
+        // the passes split periodic super-clusters into interior ones (no
+        // wrapped pair within the largest radius R of the system: the box of
+        // their particles stays more than R from every periodic face) and
+        // boundary ones; the split is redone for the new positions, from the
+        // cluster boxes of those positions
+        const int M = nl->p.cluster;
+        CK(launch_cluster_boxes(nl->npad, M, jcl(&nl->p), nl->pos.as<float4>(), nl->p.support,
+                                nl->clo.as<float4>(), nl->chi.as<float4>(),
+                                nl->jlo.as<float4>(), nl->jhi.as<float4>(), s));
+        Status *dst = nl->status.as<Status>();
+        CK(cudaMemsetAsync(&dst->n_int, 0, 2 * sizeof(unsigned int), s));
+        const bool mixed = nl->n_open && nl->n_per;
+        CK(launch_classify(mixed ? nl->sc_per.as<uint32_t>() : nullptr, mixed ? nl->n_per : nl->nsc,
+                           M, nl->tables(), nl->clo.as<float4>(), nl->chi.as<float4>(),
+                           nl->nlo.as<float4>(), nl->node_cap, nl->sc_int.as<uint32_t>(),
+                           nl->sc_bnd.as<uint32_t>(), dst, s));
     }
     return NL_OK;
 }

@@ -570,19 +570,20 @@ cudaError_t launch_fill_keys(uint64_t *keys, uint32_t cap, const unsigned long l
 cudaError_t exclusive_scan_u32(const uint32_t *cnt, uint32_t *seg_off, uint32_t n, uint32_t *bsum,
                                uint32_t *total, cudaStream_t s);
 
-enum PassKind { PASS_DENSITY = 0, PASS_COUNT = 1, PASS_SPH = 2, PASS_LJ = 3 };
+enum PassKind { PASS_DENSITY = 0, PASS_COUNT = 1, PASS_SPH = 2, PASS_LJ = 3, PASS_LJC = 4 };
 struct PassArgs {
     const float4 *pos;
     const uint8_t *list;
     const uint32_t *rec_off;
     const uint32_t *perm;  // caller index of every padded slot, ~0 for dummies
-    const float2 *aux;     // per padded particle: density m; SPH (m, P/rho^2)
+    const float2 *aux;     // per padded particle: density m; SPH (m, P/rho^2); LJ + Coulomb (q, 0)
     uint32_t n, nsc;
     SysTables sys;
     float support;
     int compress;
     int mj;                // j-cluster size MJ (units of the stored indices)
     float p0, p1;          // LJ: eps, sigma
+    float p2, p3;          // LJ + Coulomb: rc^2 (interaction cutoff, +inf: the list radius), kc
     float *out0, *out1, *out2;
     uint32_t *outc;
     Status *st;
@@ -599,6 +600,12 @@ cudaError_t launch_pass(const PassArgs &a, int kind, int M, int any_periodic, in
 cudaError_t launch_gather_aux(uint32_t npad, const uint32_t *perm_pad, const float *a,
                               const float *b, const float *c, int mode, float2 *aux,
                               cudaStream_t s);
+
+// pos[k].xyz = caller position perm_pad[k] (h kept); *max_disp (device, may be
+// NULL) = largest |x_new - pos_ref| over real slots, minimum image per system.
+cudaError_t launch_refresh(uint32_t npad, const uint32_t *perm_pad, const SysTables &t,
+                           const float *x, const float *y, const float *z, float4 *pos,
+                           const float4 *pos_ref, float *max_disp, cudaStream_t s);
 
 // Octree node boxes only (topology unchanged), e.g. after new radii.
 cudaError_t octree_boxes(uint32_t node_cap, const float4 *pos, float support, const OctreeOut &o,

@@ -13,6 +13,8 @@ cudaError_t launch_pass_sph(const PassArgs &a, int M, int per, int grid, int thr
                           cudaStream_t s);
 cudaError_t launch_pass_lj(const PassArgs &a, int M, int per, int grid, int threads,
                           cudaStream_t s);
+cudaError_t launch_pass_ljc(const PassArgs &a, int M, int per, int grid, int threads,
+                          cudaStream_t s);
 
 cudaError_t launch_pass(const PassArgs &a, int kind, int M, int any_periodic, int num_sms,
                         cudaStream_t s, int threads, int blocks_per_sm)
@@ -26,6 +28,7 @@ cudaError_t launch_pass(const PassArgs &a, int kind, int M, int any_periodic, in
     case PASS_COUNT: return launch_pass_count(a, M, any_periodic, grid, tpb, s);
     case PASS_SPH: return launch_pass_sph(a, M, any_periodic, grid, tpb, s);
     case PASS_LJ: return launch_pass_lj(a, M, any_periodic, grid, tpb, s);
+    case PASS_LJC: return launch_pass_ljc(a, M, any_periodic, grid, tpb, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -48,6 +51,52 @@ __global__ void k_gather_aux(uint32_t npad, const uint32_t *__restrict__ perm_pa
         }
     }
     aux[k] = v;
+}
+
+// New positions for a list kept across steps (Verlet buffer): every real
+// padded slot takes its particle's caller-order position and keeps its h;
+// optionally the largest displacement from the positions the list was built
+// on (minimum image on periodic axes), as a float held in an unsigned word
+// (non-negative floats order like their bit patterns).
+__global__ void __launch_bounds__(256) k_refresh(uint32_t npad, const uint32_t *__restrict__ perm_pad,
+                                                 SysTables t, const float *__restrict__ x,
+                                                 const float *__restrict__ y,
+                                                 const float *__restrict__ z, float4 *__restrict__ pos,
+                                                 const float4 *__restrict__ pos_ref,
+                                                 unsigned *__restrict__ max_disp)
+{
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    float d = 0.f;
+    if (k < npad) {
+        const uint32_t o = perm_pad[k];
+        if (o != 0xffffffffu) {
+            const float4 old = pos[k];
+            const float4 p = make_float4(x[o], y[o], z[o], old.w);
+            pos[k] = p;
+            if (max_disp) {
+                const PerLen L = per_len(t.box[sys_of(t.pad_off, t.nsys, k)]);
+                const float3 dv = pair_dx_acc<true>(pos_ref[k], p, L);
+                d = sqrtf(dv.x * dv.x + dv.y * dv.y + dv.z * dv.z);
+            }
+        }
+    }
+    if (!max_disp) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, o));
+    if ((threadIdx.x & 31) == 0 && d > 0.f) atomicMax(max_disp, __float_as_uint(d));
+}
+
+cudaError_t launch_refresh(uint32_t npad, const uint32_t *perm_pad, const SysTables &t,
+                           const float *x, const float *y, const float *z, float4 *pos,
+                           const float4 *pos_ref, float *max_disp, cudaStream_t s)
+{
+    if (max_disp) {
+        cudaError_t e = cudaMemsetAsync(max_disp, 0, sizeof(float), s);
+        if (e != cudaSuccess) return e;
+    }
+    k_refresh<<<(npad + 255) / 256, 256, 0, s>>>(npad, perm_pad, t, x, y, z, pos, pos_ref,
+                                                reinterpret_cast<unsigned *>(max_disp));
+    return cudaGetLastError();
 }
 
 cudaError_t launch_gather_aux(uint32_t npad, const uint32_t *perm_pad, const float *a,

@@ -76,6 +76,8 @@ template <>
 struct Acc<PASS_SPH> { float x[kSC], y[kSC], z[kSC], bx[kSC], by[kSC], bz[kSC]; };
 template <>
 struct Acc<PASS_LJ> { float x[kSC], y[kSC], z[kSC], bx[kSC], by[kSC], bz[kSC]; };
+template <>
+struct Acc<PASS_LJC> { float x[kSC], y[kSC], z[kSC], bx[kSC], by[kSC], bz[kSC]; };
 
 template <int KIND>
 __device__ __forceinline__ void acc_begin_block(Acc<KIND> &acc)
@@ -83,7 +85,7 @@ __device__ __forceinline__ void acc_begin_block(Acc<KIND> &acc)
     if constexpr (KIND == PASS_DENSITY) {
 #pragma unroll
         for (int k = 0; k < kSC; ++k) acc.b[k] = 0.f;
-    } else if constexpr (KIND == PASS_SPH || KIND == PASS_LJ) {
+    } else if constexpr (KIND == PASS_SPH || KIND == PASS_LJ || KIND == PASS_LJC) {
 #pragma unroll
         for (int k = 0; k < kSC; ++k) { acc.bx[k] = 0.f; acc.by[k] = 0.f; acc.bz[k] = 0.f; }
     }
@@ -100,7 +102,7 @@ __device__ __forceinline__ void acc_end_block(Acc<KIND> &acc)
             acc.c[k] = __fsub_rn(__fsub_rn(t, acc.v[k]), y);
             acc.v[k] = t;
         }
-    } else if constexpr (KIND == PASS_SPH || KIND == PASS_LJ) {
+    } else if constexpr (KIND == PASS_SPH || KIND == PASS_LJ || KIND == PASS_LJC) {
 #pragma unroll
         for (int k = 0; k < kSC; ++k) {
             acc.x[k] += acc.bx[k]; acc.y[k] += acc.by[k]; acc.z[k] += acc.bz[k];
@@ -113,7 +115,7 @@ __device__ __forceinline__ void acc_end_block(Acc<KIND> &acc)
 template <int MJ, int KIND>
 constexpr size_t pass_smem_per_warp()
 {
-    return (size_t)32 * MJ * (sizeof(float4) + ((KIND == PASS_DENSITY || KIND == PASS_SPH) ? sizeof(float2) : 0));
+    return (size_t)32 * MJ * (sizeof(float4) + ((KIND == PASS_DENSITY || KIND == PASS_SPH || KIND == PASS_LJC) ? sizeof(float2) : 0));
 }
 
 // Resident blocks per SM the register budget is cut for: the scalar passes
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(PS_THREADS, ps_min_blocks<KIND>()) k_pass(Pass
 {
     constexpr int NP = (M * MJ) / 32 > 0 ? (M * MJ) / 32 : 1;
     constexpr int JSTEP = 32 / M;
-    constexpr bool AUX = (KIND == PASS_DENSITY || KIND == PASS_SPH);
+    constexpr bool AUX = (KIND == PASS_DENSITY || KIND == PASS_SPH || KIND == PASS_LJC);
     extern __shared__ __align__(16) unsigned char pass_smem[];
     float4 *sp = reinterpret_cast<float4 *>(pass_smem + (threadIdx.x >> 5) * pass_smem_per_warp<MJ, KIND>());
     float2 *sa = reinterpret_cast<float2 *>(sp + 32 * MJ);
@@ -156,8 +158,10 @@ __global__ void __launch_bounds__(PS_THREADS, ps_min_blocks<KIND>()) k_pass(Pass
             float r = __fmul_rn(a.support, (KIND == PASS_COUNT && a.hq) ? a.hq[i] : pi[k].w);
             ri[k] = r;
             ri2[k] = __fmul_rn(r, r);
+            // LJ + Coulomb: pairs inside the list radius and the interaction cutoff
+            if constexpr (KIND == PASS_LJC) ri2[k] = fminf(ri2[k], a.p2);
             hinv[k] = 1.f / pi[k].w;
-            ci[k] = (KIND == PASS_SPH) ? a.aux[i].y : 0.f;
+            ci[k] = (KIND == PASS_SPH) ? a.aux[i].y : (KIND == PASS_LJC) ? a.p3 * a.aux[i].x : 0.f;
         }
         Acc<KIND> acc;
         // density and counts take the self pair i = j inside the loop when the
@@ -259,13 +263,25 @@ __global__ void __launch_bounds__(PS_THREADS, ps_min_blocks<KIND>()) k_pass(Pass
                         acc.by[k] += sc * dv.y;
                         acc.bz[k] += sc * dv.z;
                     }
-                } else {  // LJ: F_i += 24 eps (2 s^12/r^14 - s^6/r^8)(x_i - x_j)
+                } else if constexpr (KIND == PASS_LJ) {  // F_i += 24 eps (2 s^12/r^14 - s^6/r^8)(x_i - x_j)
                     if (owner && ii != jj && d2 < ri2[k]) {
                         const float3 dv = pair_dx_acc<PER>(pi[k], pj, box);
                         const float ir2 = 1.f / d2_of(dv);
                         const float s2 = a.p1 * a.p1 * ir2;
                         const float s6 = s2 * s2 * s2;
                         const float c = 24.f * a.p0 * ir2 * s6 * (2.f * s6 - 1.f);
+                        acc.bx[k] -= c * dv.x;
+                        acc.by[k] -= c * dv.y;
+                        acc.bz[k] -= c * dv.z;
+                    }
+                } else {  // LJ + Coulomb: the LJ term plus kc q_i q_j (x_i - x_j) / r^3
+                    if (owner && ii != jj && d2 < ri2[k]) {
+                        const float3 dv = pair_dx_acc<PER>(pi[k], pj, box);
+                        const float ir = rsqrtf(d2_of(dv));
+                        const float ir2 = ir * ir;
+                        const float s2 = a.p1 * a.p1 * ir2;
+                        const float s6 = s2 * s2 * s2;
+                        const float c = ir2 * (24.f * a.p0 * s6 * (2.f * s6 - 1.f) + ci[k] * aj.x * ir);
                         acc.bx[k] -= c * dv.x;
                         acc.by[k] -= c * dv.y;
                         acc.bz[k] -= c * dv.z;
@@ -352,7 +368,7 @@ __global__ void __launch_bounds__(PS_THREADS, ps_min_blocks<KIND>()) k_pass(Pass
                 a.out0[o] = acc.x[k];
                 a.out1[o] = acc.y[k];
                 a.out2[o] = acc.z[k];
-            } else {
+            } else {  // LJ, LJ + Coulomb
                 a.out0[o] = acc.x[k];
                 a.out1[o] = acc.y[k];
                 a.out2[o] = acc.z[k];

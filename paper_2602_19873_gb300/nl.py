@@ -59,6 +59,7 @@ _SIGS = {
     "nl_density_pass": (C.c_int, [P, P, P, P]),
     "nl_neighbor_counts": (C.c_int, [P, P, P]),
     "nl_force_pass": (C.c_int, [P, C.c_int32, P, P, P, P, P, P, P, P]),
+    "nl_refresh_positions": (C.c_int, [P, P, P, P, P, P]),
     "nl_free": (C.c_int, [P]),
     "nl_get_sizes": (C.c_int, [P, P]),
     "nl_copy_sorted": (C.c_int, [P, P, P]),
@@ -96,7 +97,7 @@ _SIGS = {
 }
 
 NL_HSTART_GIVEN, NL_HSTART_PLAIN, NL_HSTART_LEARNED = 0, 1, 2
-NL_FORCE_SPH_PRESSURE, NL_FORCE_LJ = 0, 1
+NL_FORCE_SPH_PRESSURE, NL_FORCE_LJ, NL_FORCE_LJ_COULOMB = 0, 1, 2
 
 
 class nl_hiter_info(C.Structure):
@@ -399,13 +400,18 @@ class NeighborList:
         _check(load().nl_density_pass(self.handle, _ptr(m), _ptr(rho), _stream(stream)))
 
     def force_pass(self, kind, ax, ay, az, m=None, rho=None, pres=None, eps=1.0, sigma=1.0,
-                   stream=None):
-        prm = (C.c_float * 2)(float(eps), float(sigma))
+                   rc=0.0, kc=0.0, stream=None):
+        """nl_force_pass; for NL_FORCE_LJ_COULOMB `m` carries the charges q."""
+        prm = (C.c_float * 4)(float(eps), float(sigma), float(rc), float(kc))
         _check(load().nl_force_pass(self.handle, int(kind), prm, _ptr(m), _ptr(rho), _ptr(pres),
                                     _ptr(ax), _ptr(ay), _ptr(az), _stream(stream)))
 
     def neighbor_counts(self, counts, stream=None):
         _check(load().nl_neighbor_counts(self.handle, _ptr(counts), _stream(stream)))
+
+    def refresh_positions(self, x, y, z, max_disp=None, stream=None):
+        _check(load().nl_refresh_positions(self.handle, _ptr(x), _ptr(y), _ptr(z), _ptr(max_disp),
+                                           _stream(stream)))
 
     def sizes(self):
         s = nl_sizes()
