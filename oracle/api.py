@@ -19,7 +19,7 @@ _lib = None
 
 __all__ = [
     "build", "lib", "Box", "quantize", "morton3", "hilbert3", "hilbert3_inverse", "keys",
-    "sort", "octree", "brute_neighbors", "gather_all", "symmetrize", "cluster_lists",
+    "sort", "octree", "brute_neighbors", "gather_all", "symmetrize", "cluster_lists", "half_lists",
     "encode_block", "encode_record", "decode_record", "record_bytes", "stream_nibbles",
     "w", "dw", "W", "density", "sph_force", "lj_force", "lj_energy", "ljc_force", "ljc_energy",
     "gather_counts_brute",
@@ -257,6 +257,23 @@ def cluster_lists(n, cluster, off, idx, rows, sc_ids, jcluster=None):
     L.orc_clist_copy(c, _p(o), _p(J), _p(m))
     L.orc_clist_free(c)
     return o, J[:nnz], m[:nnz]
+
+
+def half_lists(o, J, m, sc_ids):
+    """Half list of the super-clusters sc_ids (j-clusters = i-clusters): each
+    record keeps the entries J >= 8 s of the full canonical record of s, with
+    their masks, so every pair of clusters of different super-clusters is
+    stored once, by the lower super-cluster (Sec. II-D's symmetric lists)."""
+    o2 = [0]
+    J2, m2 = [], []
+    for t, s in enumerate(np.asarray(sc_ids, np.int64)):
+        Js, ms = J[o[t]:o[t + 1]], m[o[t]:o[t + 1]]
+        keep = Js >= 8 * s
+        J2.append(Js[keep])
+        m2.append(ms[keep])
+        o2.append(o2[-1] + int(keep.sum()))
+    cat = (lambda a, dt: np.concatenate(a).astype(dt) if a else np.zeros(0, dt))
+    return np.asarray(o2, np.int64), cat(J2, np.int32), cat(m2, np.uint8)
 
 
 def pipeline_lists(x, y, z, h, box, support, kind, cluster):

@@ -177,3 +177,44 @@ def test_cluster_lists_with_half_j_clusters(orc, M, MJ):
         Js = sorted(want)
         assert J[o[s]:o[s + 1]].tolist() == Js
         assert m[o[s]:o[s + 1]].tolist() == [want[x] for x in Js]
+
+
+def _tiles(o, J, m, sc_ids):
+    out = set()
+    for t, s in enumerate(sc_ids):
+        for J_, mk in zip(J[o[t]:o[t + 1]], m[o[t]:o[t + 1]]):
+            for k in range(8):
+                if (int(mk) >> k) & 1:
+                    out.add((8 * int(s) + k, int(J_)))
+    return out
+
+
+@pytest.mark.parametrize("M", [4, 8])
+@pytest.mark.parametrize("name", ["plummer", "uniform"])
+def test_half_lists_store_every_cluster_pair_once(orc, name, M):
+    """The half list with its transposes is the full list; a pair of clusters
+    of different super-clusters is stored exactly once, by the lower one; the
+    super-cluster's own clusters keep both orders."""
+    d = _small(name, 1900)
+    xs, ys, zs, hs, ms = _sorted(orc, d)
+    g_off, g_idx = orc.gather_all(xs, ys, zs, hs, d["box"], 2.0)
+    p_off, p_idx = orc.symmetrize(g_off, g_idx)
+    n = len(xs)
+    nsc = (n + 8 * M - 1) // (8 * M)
+    sc = np.arange(nsc)
+    full = _tiles(*orc.cluster_lists(n, M, p_off, p_idx, np.arange(n), sc), sc)
+    o, J, m = orc.half_lists(*orc.cluster_lists(n, M, p_off, p_idx, np.arange(n), sc), sc)
+    half = _tiles(o, J, m, sc)
+    assert half | {(b, a) for a, b in half} == full
+    for (a, b) in full:
+        if a // 8 != b // 8:
+            assert ((a, b) in half) != ((b, a) in half)
+            assert ((a, b) in half) == (b // 8 > a // 8)
+        else:
+            assert (a, b) in half
+    # records stay ascending and carry no empty masks
+    for s in sc:
+        Js = J[o[s]:o[s + 1]]
+        assert np.all(np.diff(Js) > 0) and np.all(Js >= 8 * s)
+        assert np.all(m[o[s]:o[s + 1]] != 0)
+    assert len(J) < len(orc.cluster_lists(n, M, p_off, p_idx, np.arange(n), sc)[1])
