@@ -32,12 +32,14 @@ WORKLOAD = "plummer64_16m"
 N_FULL = 1 << 24
 ALU_OPS_PER_PAIR_SEARCH = 9      # predicate: 3 sub, 3 mul, 2 add, 1 compare (non-periodic)
 ALGO_BYTES_PER_PARTICLE = 145    # keygen 20 + sort 24 + permute 49 + octree 2 + search 19 + density 31
-# DRAM bytes (read + write) of one k_search launch per particle, from an ncu
-# capture of the half search (8x8 clusters, leaf bucket 256, cluster-box round
-# then exact tile tests) on this generator at 2^21 particles: 45.1 MB + 12.7 MB;
-# scaled by the particle count (the traffic grows with the particles).  Valid
-# for that kernel version only.
-SEARCH_DRAM_BYTES_PER_PARTICLE = 57.8e6 / 2097152
+# DRAM bytes (read + write) of one k_search launch per particle, from ncu
+# captures on this generator at 2^21 particles (8x8 clusters, leaf bucket 256,
+# cluster-box round then exact tile tests), scaled by the particle count (the
+# traffic grows with the particles).  "full": the half search with transposed
+# tuples for full lists, 45.1 MB + 12.7 MB; "half": the same walk storing half
+# lists, 44.9 MB + 0.9 MB.  Valid for those kernel versions only; a list kind
+# without a capture reports no traffic.
+SEARCH_DRAM_BYTES_PER_PARTICLE = {"full": 57.8e6 / 2097152, "half": 45.8e6 / 2097152}
 
 
 def peaks():
@@ -161,18 +163,22 @@ def reference_sample(steps, warmup, requested=None):
     return int(min(1 << 20, max(1 << 16, 0.11e6 * 100.0 / max(1, steps + warmup))))
 
 
-def launches_per_step(sizes, batched, mixed=False):
+def launches_per_step(sizes, batched, mixed=False, half_list=False):
     """Kernels of one build + density step (graph replay when batched): keys,
     radix sort (8 passes x 3, a 9th by system in batches), permute, octree
     (10), search (open, interior and boundary launches plus a classification
     when a batch mixes open and periodic systems),
     and for the half search the tuple sort (3 per 8 key bits, plus the fill of
     unused slots in a graph), the lower-entry scan (3) and the record
-    assembly; then the pass input gather and the pass (three when mixed)."""
+    assembly; then the pass input gather and the pass (three when mixed);
+    a half list stores the search's records directly and adds the pass's
+    finishing kernel."""
     sort_passes = 9 if batched else 8
     # mixed batches: open, interior and boundary launches of the search and
     # the pass, plus the interior classification
     n = 1 + 3 * sort_passes + 1 + 10 + (3 + 1 if mixed else 1) + (2 if mixed else 0)
+    if half_list:
+        return n + 3
     if sizes["j_cluster"] == sizes["cluster"]:
         nsc = sizes["n_superclusters"]
         bits = 1
@@ -256,7 +262,8 @@ def run_native(args):
     M, MJ = (int(v) for v in args.tile.split("x"))
     params = nl.make_params(key=d["kind"], cluster=M, support=d["support"], compress=1,
                             leaf_bucket=args.leaf_bucket, j_cluster=MJ,
-                            threads_per_block=args.threads, blocks_per_sm=args.blocks_per_sm)
+                            threads_per_block=args.threads, blocks_per_sm=args.blocks_per_sm,
+                            half_list=int(args.list == "half"))
     L = nl.NeighborList()
     stream = torch.cuda.current_stream()
     # smoothing lengths at 200 +- 2 neighbors from the plain start (untimed
@@ -321,6 +328,43 @@ def run_native(args):
     stages = {k: v / args.steps for k, v in stage_acc.items()}
     sizes = L.sizes()
 
+    # the other storage of the same list (full <-> half), timed the same way
+    alt_kind = "full" if args.list == "half" else "half"
+    alt_params = nl.make_params(key=d["kind"], cluster=M, support=d["support"], compress=1,
+                                leaf_bucket=args.leaf_bucket, j_cluster=MJ,
+                                threads_per_block=args.threads, blocks_per_sm=args.blocks_per_sm,
+                                half_list=int(alt_kind == "half"))
+    alt = None
+    if alt_kind == "full" or MJ == M:
+        A = nl.NeighborList()
+        A.set_profiling(True)
+
+        def alt_step():
+            A.build(dev["x"], dev["y"], dev["z"], dev["h"], d["box"], alt_params, stream)
+            A.density_pass(dev["m"], rho, stream)
+
+        quiesce_host()
+        for _ in range(args.warmup):
+            alt_step()
+        torch.cuda.synchronize()
+        a_acc = {}
+        t0.record(stream)
+        for _ in range(args.steps):
+            alt_step()
+            for k, v in A.stage_times().items():
+                a_acc[k] = a_acc.get(k, 0.0) + v
+        t1.record(stream)
+        torch.cuda.synchronize()
+        a_ms = max_over_ranks(t0.elapsed_time(t1) / args.steps, ws, "cuda")
+        asz = A.sizes()
+        alt = {"list": alt_kind, "ms_per_step": a_ms, "value": job_rate(n, ws, a_ms),
+               "unit": UNIT, "stages_ms": {k: v / args.steps for k, v in a_acc.items()},
+               "bytes_per_particle": asz["list_bytes"] / n, "entries": asz["n_entries"]}
+        A.free()
+    # pair slots of the symmetric relation the search decides: the full
+    # list's tiles (a half list stores each pair of super-clusters once)
+    full_tiles = sizes["n_tiles"] if args.list == "full" else (asz["n_tiles"] if alt else None)
+
     # end to end through the host-buffer entry point (pinned memory)
     pin = {k: torch.from_numpy(d[k]).pin_memory().numpy() for k in ("x", "y", "z", "h", "m")}
     rho_h = torch.empty(n, dtype=torch.float32).pin_memory().numpy()
@@ -341,7 +385,7 @@ def run_native(args):
     hbm, hbm_kind, sm_max = peaks()
     alu_peak = 152 * 128 * sm_max * 1e6 / 1e12  # FP32 instructions per second, Tops
     search_ms = stages.get("search", float("nan"))
-    pairs = sizes["n_tiles"] * params.cluster * sizes["j_cluster"]
+    pairs = (full_tiles if full_tiles is not None else sizes["n_tiles"]) * params.cluster * sizes["j_cluster"]
     achieved = pairs * ALU_OPS_PER_PAIR_SEARCH / (search_ms * 1e-3) / 1e12
     step_bytes = ALGO_BYTES_PER_PARTICLE * n
     out = {
@@ -351,7 +395,7 @@ def run_native(args):
         "data": "synthetic",
         "config": {"workload": "%s: 2^24 particles in 64 Plummer spheres (scale radii "
                                "log-uniform 1e-3..1e-1), Hilbert keys, %dx%d clusters, "
-                               "compressed list" % (WORKLOAD, M, MJ),
+                               "compressed %s list" % (WORKLOAD, M, MJ, args.list),
                    "n": n, "cluster": params.cluster, "j_cluster": sizes["j_cluster"],
                    "leaf_bucket": params.leaf_bucket,
                    "h": "iterated on the GPU to 200 +- 2 gather neighbors (plain start)",
@@ -362,16 +406,19 @@ def run_native(args):
                      "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                      "peak_kind": "FP32 lanes x max SM clock (152 SMs x 128 x %.0f MHz)" % sm_max,
                      "frac": achieved / alu_peak,
-                     "traffic": (SEARCH_DRAM_BYTES_PER_PARTICLE * n
-                                 if (M, MJ) == (8, 8) and params.leaf_bucket == 256 else None),
-                     "algorithmic": "%d FP32 ops per computed pair, %d computed pairs" % (
-                         ALU_OPS_PER_PAIR_SEARCH, pairs)},
+                     "traffic": (SEARCH_DRAM_BYTES_PER_PARTICLE[args.list] * n
+                                 if (M, MJ) == (8, 8) and params.leaf_bucket == 256
+                                 and SEARCH_DRAM_BYTES_PER_PARTICLE.get(args.list) else None),
+                     "algorithmic": "%d FP32 ops per computed pair, %d computed pairs (tiles of "
+                                    "the full list x M x MJ)" % (ALU_OPS_PER_PAIR_SEARCH, pairs)},
         "hbm_step": {"achieved_gbs": step_bytes / (ms * 1e-3) / 1e9, "peak_gbs": hbm,
                      "peak_kind": hbm_kind,
                      "frac": step_bytes / (ms * 1e-3) / 1e9 / hbm,
                      "bytes_per_particle": ALGO_BYTES_PER_PARTICLE},
-        "list": {"bytes_per_particle": sizes["list_bytes"] / n, "entries": sizes["n_entries"],
-                 "computed_pairs": pairs, "nodes": sizes["n_nodes"], "leaves": sizes["n_leaves"],
+        "list": {"kind": args.list, "bytes_per_particle": sizes["list_bytes"] / n,
+                 "entries": sizes["n_entries"],
+                 "computed_pairs": sizes["n_tiles"] * params.cluster * sizes["j_cluster"],
+                 "nodes": sizes["n_nodes"], "leaves": sizes["n_leaves"],
                  "search_node_visits": sizes["node_visits"],
                  "search_leaf_visits": sizes["leaf_visits"],
                  "search_j_examined": sizes["j_examined"],
@@ -388,8 +435,10 @@ def run_native(args):
                             "learned": None if learned is None else learned["ms"] + ms}},
         "gpu_launches": None,
         "clocks": clk,
+        "other_list": alt,
     }
-    out["gpu_launches"] = args.steps * launches_per_step(sizes, False)
+    out["gpu_launches"] = args.steps * launches_per_step(sizes, False,
+                                                         half_list=args.list == "half")
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_sample or (1 << 20))
     if rank == 0:
@@ -418,7 +467,7 @@ def run_batched(args):
     dev = {k: torch.from_numpy(np.concatenate([d[k] for d in systems]).astype(np.float32)).cuda()
            for k in "xyzhm"}
     stream = torch.cuda.Stream()
-    base = nl.make_params(key=1, cluster=8, support=2.0)
+    base = nl.make_params(key=1, cluster=8, support=2.0, half_list=int(args.list == "half"))
     with torch.cuda.stream(stream):
         H = nl.NeighborList()
         t = time.perf_counter()
@@ -482,7 +531,8 @@ def run_batched(args):
            "per_system_max_rel_density_err": worst,
            "per_system_error_sample": [int(len(systems[k]["x"])) for k in sample],
            "gpu_launches": args.steps * launches_per_step(
-               sizes, True, mixed=len({bool(np.any(b["periodic"])) for b in boxes}) > 1),
+               sizes, True, mixed=len({bool(np.any(b["periodic"])) for b in boxes}) > 1,
+               half_list=args.list == "half"),
            "clocks": clk}
     if rank == 0:
         print(json.dumps(out))
@@ -791,6 +841,8 @@ def main():
     ap.add_argument("--tile", default="8x8", choices=["8x8", "8x4", "16x8", "16x16", "4x4"],
                     help="i-cluster x j-cluster size of the single-system bench")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-h comparison")
+    ap.add_argument("--list", default="half", choices=["full", "half"],
+                    help="full lists, or half lists (every cluster pair once; density workloads)")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "batched_256"] + sorted(CONFIGS))
     ap.add_argument("--sweep", action="store_true",

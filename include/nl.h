@@ -76,9 +76,16 @@ typedef struct {
     int32_t j_cluster;    /* particles per j-cluster MJ: 0 (= M), M, or M / 2 when M >= 8;
                              the M x MJ tiles of Sec. II-A / III-A (8 x 4 is the paper's
                              NVIDIA choice).  Stored list indices count j-clusters. */
+    int32_t half_list;    /* 1: store every cluster pair once (the symmetric list of
+                             Sec. II-D): the record of super-cluster s holds only the
+                             j-clusters J >= 8s of its full record, with the same masks,
+                             and the density and count passes add each pair to both of
+                             its particles.  Needs MJ = M.  The force passes need a full
+                             list (0, the default); the h iteration always builds full
+                             lists. */
 } nl_params;
 
-/* Fills p with {NL_KEY_HILBERT, 8, 2.0f, 1, 256, 0, 0, 0}. */
+/* Fills p with {NL_KEY_HILBERT, 8, 2.0f, 1, 256, 0, 0, 0, 0}. */
 void nl_default_params(nl_params *p);
 
 typedef struct nl_list nl_list; /* opaque; owns all of its device memory */

@@ -122,6 +122,8 @@ struct nl_list {
     // keeps the positions the list was built on
     int moved = 0;
     DevBuf pos_ref;
+    // half-list passes: per sorted particle fixed-point density sums, counts
+    DevBuf hsum, hcnt;
     uint32_t node_cap = 0;
     const struct nl_mlp *mlp = nullptr;
     DevBuf ml_X, ml_e64, ml_pred, ml_slo, ml_shi;
@@ -183,7 +185,7 @@ struct nl_list {
                          &it_words, &it_tmp, &ml_X, &ml_e64, &ml_pred, &ml_slo, &ml_shi,
                          &uJ, &uM, &up_off, &up_cnt, &lower_cnt, &seg_off, &tkey, &tkey_alt,
                          &tval, &tval_alt, &thist, &sc_open, &sc_per, &sc_int, &sc_bnd,
-                         &pos_ref};
+                         &pos_ref, &hsum, &hcnt};
         for (DevBuf *b : all) b->release();
         for (int i = 0; i <= kStages; ++i)
             if (ev[i]) cudaEventDestroy(ev[i]);
@@ -213,6 +215,9 @@ nl_status check_params(const nl_params *p, const nl_box *box)
         !(p->cluster >= 8 && p->j_cluster * 2 == p->cluster))
         return fail(NL_ERR_ARG, "j_cluster must be 0, cluster or cluster / 2 >= 4 (got %d for cluster %d)",
                     p->j_cluster, p->cluster);
+    if (p->half_list != 0 && p->half_list != 1) return fail(NL_ERR_ARG, "half_list must be 0 or 1");
+    if (p->half_list && p->j_cluster != 0 && p->j_cluster != p->cluster)
+        return fail(NL_ERR_ARG, "a half list needs j-clusters of the i-cluster size");
     if (!(p->support > 0.f) || !std::isfinite(p->support))
         return fail(NL_ERR_ARG, "support must be finite and > 0");
     if (p->compress != 0 && p->compress != 1) return fail(NL_ERR_ARG, "compress must be 0 or 1");
@@ -729,7 +734,7 @@ nl_status do_search(nl_list *nl, cudaStream_t s)
         // forces the full search (tests run both)
         const char *e = std::getenv("NLGB_SEARCH");
         const bool full = e && std::strcmp(e, "full") == 0;
-        if (!full && jcl(&nl->p) == nl->p.cluster) return do_search_half(nl, s);
+        if (!nl->p.half_list && !full && jcl(&nl->p) == nl->p.cluster) return do_search_half(nl, s);
     }
     nl_status st;
     const nl_params *p = &nl->p;
@@ -773,6 +778,7 @@ nl_status do_search(nl_list *nl, cudaStream_t s)
     sa.compress = p->compress;
     sa.st = dst;
     sa.rec_off = nl->rec_off.as<uint32_t>();
+    sa.half = p->half_list ? 2 : 0;  // the half list: the half search's own entries as records
 
     unsigned long long entries = 0, tiles = 0, used = 0, nv = 0, lv = 0, jx = 0, tt = 0;
     const uint32_t *work = nullptr;
@@ -879,6 +885,9 @@ PassArgs pass_args(const nl_list *nl)
     a.compress = nl->p.compress;
     a.mj = jcl(&nl->p);
     a.st = nl->status.as<Status>();
+    a.half = nl->p.half_list;
+    a.hsum = nl->hsum.as<unsigned long long>();
+    a.hcnt = nl->hcnt.as<uint32_t>();
     return a;
 }
 
@@ -897,6 +906,7 @@ void nl_default_params(nl_params *p)
     p->threads_per_block = 0;
     p->blocks_per_sm = 0;
     p->j_cluster = 0;
+    p->half_list = 0;
 }
 
 const char *nl_last_error(void) { return g_err.c_str(); }
@@ -1269,7 +1279,10 @@ static nl_status do_iterate_h(nl_list *nl, const float *x, const float *y, const
         CK(launch_fill(nl->it_tmp.as<float>(), N, 1e-30f, s));
         hin = nl->it_tmp.as<float>();
     }
-    nl_status st = do_prep(nl, x, y, z, hin, n, nsys, offs, boxes, p, s);
+    // the iteration re-runs single super-clusters on full lists
+    nl_params pf = p ? *p : nl_params{};
+    pf.half_list = 0;
+    nl_status st = do_prep(nl, x, y, z, hin, n, nsys, offs, boxes, p ? &pf : nullptr, s);
     if (st != NL_OK) return st;
     const int M = p->cluster;
     const uint32_t nsc = nl->nsc, npad = nl->npad;
@@ -1538,6 +1551,7 @@ nl_status nl_autotune_batch(const float *x, const float *y, const float *z, cons
     for (int mi = 0; mi < 5 && st == NL_OK; ++mi)
         for (int ti = 0; ti < 2 && st == NL_OK; ++ti)
             for (int bi = 0; bi < 3 && st == NL_OK; ++bi) {
+                if (base->half_list && MJs[mi] != Ms[mi]) continue;  // half lists need MJ = M
                 nl_params c = *base;
                 c.cluster = Ms[mi];
                 c.j_cluster = MJs[mi];
@@ -1586,14 +1600,20 @@ nl_status nl_density_pass(const nl_list *cnl, const float *m, float *rho, void *
     if (!m || !rho) return fail(NL_ERR_ARG, "NULL m or rho");
     nl_list *nl = const_cast<nl_list *>(cnl);
     cudaStream_t s = (cudaStream_t)stream;
+    const bool half = nl->p.half_list != 0;
     CK(nl->aux.ensure((size_t)nl->npad * 8));
+    if (half) CK(nl->hsum.ensure((size_t)nl->npad * 8));
+    Status *dst = nl->status.as<Status>();
     CK(nl->mark(6, s));
+    if (half) CK(cudaMemsetAsync(&dst->m_absmax, 0, sizeof(unsigned int), s));
     CK(launch_gather_aux(nl->npad, nl->perm_pad.as<uint32_t>(), m, nullptr, nullptr, 0,
-                         nl->aux.as<float2>(), s));
+                         nl->aux.as<float2>(), s, half ? &dst->m_absmax : nullptr));
+    if (half) CK(cudaMemsetAsync(nl->hsum.p, 0, (size_t)nl->npad * 8, s));
     CK(nl->mark(7, s));
     PassArgs a = pass_args(nl);
     a.out0 = rho;
     CK(run_pass(nl, a, PASS_DENSITY, s));
+    if (half) CK(launch_half_finish(a, PASS_DENSITY, nl->npad, s));
     CK(nl->mark(8, s));
     return NL_OK;
 }
@@ -1605,6 +1625,7 @@ nl_status nl_force_pass(const nl_list *cnl, int32_t kind, const float *params, c
     nl_status st = check_list(cnl);
     if (st != NL_OK) return st;
     if (!ax || !ay || !az) return fail(NL_ERR_ARG, "NULL force output");
+    if (cnl->p.half_list) return fail(NL_ERR_ARG, "the force passes need a full list (half_list = 0)");
     nl_list *nl = const_cast<nl_list *>(cnl);
     cudaStream_t s = (cudaStream_t)stream;
     if (kind == NL_FORCE_SPH_PRESSURE) {
@@ -1703,9 +1724,16 @@ nl_status nl_neighbor_counts(const nl_list *cnl, uint32_t *counts, void *stream)
     if (st != NL_OK) return st;
     if (!counts) return fail(NL_ERR_ARG, "NULL counts");
     nl_list *nl = const_cast<nl_list *>(cnl);
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool half = nl->p.half_list != 0;
+    if (half) {
+        CK(nl->hcnt.ensure((size_t)nl->npad * 4));
+        CK(cudaMemsetAsync(nl->hcnt.p, 0, (size_t)nl->npad * 4, s));
+    }
     PassArgs a = pass_args(nl);
     a.outc = counts;
-    CK(run_pass(nl, a, PASS_COUNT, (cudaStream_t)stream));
+    CK(run_pass(nl, a, PASS_COUNT, s));
+    if (half) CK(launch_half_finish(a, PASS_COUNT, nl->npad, s));
     return NL_OK;
 }
 

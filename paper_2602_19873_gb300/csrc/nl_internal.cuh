@@ -81,6 +81,8 @@ struct Status {
     unsigned int pad2;
     // periodic super-clusters whose neighbors cannot wrap (interior) and the rest
     unsigned int n_int, n_bnd;
+    // half-list density: bits of the largest |m| (sets the fixed-point scale)
+    unsigned int m_absmax, pad3;
 };
 
 // ---------------------------------------------------------------------------
@@ -535,6 +537,8 @@ struct SearchArgs {
     // keeps them as its upper entries and sends every tile (8s+k, J) with J
     // beyond its own clusters to super-cluster J/8 as a transposed tuple
     // (key = (J/8) * ncl + 8s+k, value = bit J%8 of the rows, merged per key)
+    // half = 1; half = 2 stores the entries J >= 8s themselves as the record
+    // (half list, every cluster pair once) and emits no tuples
     int half;
     uint32_t ncl;                  // clusters in total (padded)
     uint32_t *uJ;                  // upper entries (j-cluster, mask)
@@ -592,14 +596,33 @@ struct PassArgs {
     const uint32_t *work;    // optional list of super-clusters to process
     uint32_t nwork;
     const uint32_t *nwork_dev;  // optional device count of work (at most nwork)
+    // half list (every cluster pair once): both particles of a pair take
+    // their share.  Density sums are added as 64-bit fixed point (integer
+    // additions in any order give the same bits), counts as integers; a
+    // finishing kernel turns them into the outputs.
+    int half;
+    unsigned long long *hsum;   // density: per sorted particle, sum m_j w in units of 2^-scale
+    uint32_t *hcnt;             // counts: per sorted particle
 };
+
+// Fixed-point scale of the half-list density: 2^(40 - e) with |m| < 2^e for
+// the largest mass, so one neighbor adds at most 2^40 units (w <= 1) and 2^23
+// neighbors fit in 63 bits; clamped to the FP32 range.
+__device__ __forceinline__ int half_scale_exp(unsigned int mbits)
+{
+    const int e = (int)((mbits >> 23) & 0xffu) - 126;
+    return max(-126, min(127, 40 - e));
+}
 // threads 0 = 256; blocks_per_sm 0 = default
 cudaError_t launch_pass(const PassArgs &a, int kind, int M, int any_periodic, int num_sms,
                         cudaStream_t s, int threads = 0, int blocks_per_sm = 0);
-// aux[k] = (a[perm[k]], ...) for real padded slots, zero for dummies.
+// aux[k] = (a[perm[k]], ...) for real padded slots, zero for dummies;
+// amax (optional): atomic max of the bits of |aux.x| (zero it first).
 cudaError_t launch_gather_aux(uint32_t npad, const uint32_t *perm_pad, const float *a,
                               const float *b, const float *c, int mode, float2 *aux,
-                              cudaStream_t s);
+                              cudaStream_t s, unsigned int *amax = nullptr);
+// Outputs of a half-list pass (PASS_DENSITY or PASS_COUNT) from its sums.
+cudaError_t launch_half_finish(const PassArgs &a, int kind, uint32_t npad, cudaStream_t s);
 
 // pos[k].xyz = caller position perm_pad[k] (h kept); *max_disp (device, may be
 // NULL) = largest |x_new - pos_ref| over real slots, minimum image per system.

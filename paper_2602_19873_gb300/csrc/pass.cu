@@ -35,22 +35,64 @@ cudaError_t launch_pass(const PassArgs &a, int kind, int M, int any_periodic, in
 
 // Gather per-particle pass inputs into SFC order.
 // mode 0: aux = (a, 0); mode 1: aux = (a, b / (c*c)) (SPH: m, P / rho^2).
-__global__ void k_gather_aux(uint32_t npad, const uint32_t *__restrict__ perm_pad,
-                             const float *__restrict__ a, const float *__restrict__ b,
-                             const float *__restrict__ c, int mode, float2 *__restrict__ aux)
+__global__ void __launch_bounds__(256) k_gather_aux(uint32_t npad, const uint32_t *__restrict__ perm_pad,
+                                                    const float *__restrict__ a, const float *__restrict__ b,
+                                                    const float *__restrict__ c, int mode,
+                                                    float2 *__restrict__ aux, unsigned int *amax)
 {
+    __shared__ unsigned int wmax[8];
     uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= npad) return;
     float2 v = make_float2(0.f, 0.f);
-    const uint32_t o = perm_pad[k];
-    if (o != 0xffffffffu) {
-        v.x = a[o];
-        if (mode == 1) {
-            float rho = c[o];
-            v.y = b[o] / (rho * rho);
+    if (k < npad) {
+        const uint32_t o = perm_pad[k];
+        if (o != 0xffffffffu) {
+            v.x = a[o];
+            if (mode == 1) {
+                float rho = c[o];
+                v.y = b[o] / (rho * rho);
+            }
         }
+        aux[k] = v;
     }
-    aux[k] = v;
+    if (!amax) return;  // uniform over the grid
+    // largest |a| of the block, one atomic per block (non-negative floats
+    // order like their bit patterns)
+    unsigned int m = __reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(v.x)));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : 0u;
+        m = __reduce_max_sync(0xffffffffu, m);
+        if (threadIdx.x == 0 && m) atomicMax(amax, m);
+    }
+}
+
+// Outputs of a half-list pass: density = (sum in fixed point) * 2^-scale *
+// W's normalisation 1/(pi h^3), in the same FP32 form as the full-list pass;
+// counts as summed.  Real slots only, written at perm[k] (or k).
+__global__ void __launch_bounds__(256) k_half_finish(PassArgs a, int kind, uint32_t npad)
+{
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npad) return;
+    const uint32_t pc = a.perm[k];
+    if (pc == 0xffffffffu) return;
+    const uint32_t o = a.sorted_out ? k : pc;
+    if (kind == PASS_COUNT) {
+        a.outc[o] = a.hcnt[k];
+        return;
+    }
+    const int ex = half_scale_exp(a.st->m_absmax);
+    const double unit = __longlong_as_double((long long)(1023 - ex) << 52);  // 2^-ex
+    const float v = (float)((double)(long long)a.hsum[k] * unit);
+    const float hinv = 1.f / a.pos[k].w;
+    a.out0[o] = v * (0.318309886183790672f * hinv * hinv * hinv);
+}
+
+cudaError_t launch_half_finish(const PassArgs &a, int kind, uint32_t npad, cudaStream_t s)
+{
+    if (kind != PASS_DENSITY && kind != PASS_COUNT) return cudaErrorInvalidValue;
+    k_half_finish<<<(npad + 255) / 256, 256, 0, s>>>(a, kind, npad);
+    return cudaGetLastError();
 }
 
 // New positions for a list kept across steps (Verlet buffer): every real
@@ -101,9 +143,9 @@ cudaError_t launch_refresh(uint32_t npad, const uint32_t *perm_pad, const SysTab
 
 cudaError_t launch_gather_aux(uint32_t npad, const uint32_t *perm_pad, const float *a,
                               const float *b, const float *c, int mode, float2 *aux,
-                              cudaStream_t s)
+                              cudaStream_t s, unsigned int *amax)
 {
-    k_gather_aux<<<(npad + 255) / 256, 256, 0, s>>>(npad, perm_pad, a, b, c, mode, aux);
+    k_gather_aux<<<(npad + 255) / 256, 256, 0, s>>>(npad, perm_pad, a, b, c, mode, aux, amax);
     return cudaGetLastError();
 }
 

@@ -111,28 +111,63 @@ __device__ __forceinline__ void acc_end_block(Acc<KIND> &acc)
 }
 
 // Shared memory per warp: the j particles (and pass inputs) of one block
-// of 32 list entries, loaded in bulk before the block is computed.
-template <int MJ, int KIND>
+// of 32 list entries, loaded in bulk before the block is computed; on a
+// half list also the masses of the super-cluster's own particles.
+template <int MJ, int KIND, bool HL = false>
 constexpr size_t pass_smem_per_warp()
 {
-    return (size_t)32 * MJ * (sizeof(float4) + ((KIND == PASS_DENSITY || KIND == PASS_SPH || KIND == PASS_LJC) ? sizeof(float2) : 0));
+    return (size_t)32 * MJ * (sizeof(float4) + ((KIND == PASS_DENSITY || KIND == PASS_SPH || KIND == PASS_LJC) ? sizeof(float2) : 0)) +
+           (HL ? (size_t)kSC * MJ * sizeof(float) : 0);
 }
 
 // Resident blocks per SM the register budget is cut for: the scalar passes
 // run at 64 registers (4 blocks of 256, some spills; measured faster than 3
-// blocks at 80), the vector passes keep 128.
-template <int KIND>
-constexpr int ps_min_blocks() { return (KIND == PASS_DENSITY || KIND == PASS_COUNT) ? 4 : 2; }
+// blocks at 80), the vector passes keep 128; the half-list density pass
+// holds more per lane and runs 3 blocks at 80.
+template <int KIND, bool HL>
+constexpr int ps_min_blocks()
+{
+    return (HL && KIND == PASS_DENSITY) ? 3 : (KIND == PASS_DENSITY || KIND == PASS_COUNT) ? 4 : 2;
+}
 
-template <int M, int MJ, bool PER, int KIND>
-__global__ void __launch_bounds__(PS_THREADS, ps_min_blocks<KIND>()) k_pass(PassArgs a)
+// Nearest integer of x (ties away from zero) as a 64-bit two's complement
+// word, with integer operations only; |x| < 2^62.  Subnormal x give 0.
+__device__ __forceinline__ unsigned long long fixed_of(float x)
+{
+    const uint32_t b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 0xffu) - 150;  // |x| = mant * 2^e
+    const unsigned long long m = (unsigned long long)((b & 0x7fffffu) | 0x800000u);
+    unsigned long long q;
+    if (e >= 0)
+        q = m << e;
+    else if (e > -25)
+        q = (m + (1ull << (-e - 1))) >> (-e);
+    else
+        q = 0ull;
+    if (((b >> 23) & 0xffu) == 0u) q = 0ull;
+    return (b >> 31) ? (0ull - q) : q;
+}
+
+// HL: the list holds every cluster pair once (half list, MJ = M).  Entries
+// of the super-cluster's own clusters are complete as they are (both orders
+// of every pair are listed); an entry J beyond them is a pair of clusters
+// listed only here, so its pairs also add to the j particles: d2 < rj^2 gives
+// particle j the term with its own h.  Those j shares are summed over the
+// entry's i particles in a fixed shuffle order and added as integers (fixed
+// point for density), so the result does not depend on the order of the adds.
+template <int M, int MJ, bool PER, int KIND, bool HL>
+__global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pass(PassArgs a)
 {
     constexpr int NP = (M * MJ) / 32 > 0 ? (M * MJ) / 32 : 1;
     constexpr int JSTEP = 32 / M;
     constexpr bool AUX = (KIND == PASS_DENSITY || KIND == PASS_SPH || KIND == PASS_LJC);
+    static_assert(!HL || ((KIND == PASS_DENSITY || KIND == PASS_COUNT) && M == MJ), "half-list pass");
     extern __shared__ __align__(16) unsigned char pass_smem[];
-    float4 *sp = reinterpret_cast<float4 *>(pass_smem + (threadIdx.x >> 5) * pass_smem_per_warp<MJ, KIND>());
+    float4 *sp = reinterpret_cast<float4 *>(pass_smem + (threadIdx.x >> 5) * pass_smem_per_warp<MJ, KIND, HL>());
     float2 *sa = reinterpret_cast<float2 *>(sp + 32 * MJ);
+    float *smi = AUX ? reinterpret_cast<float *>(sa + 32 * MJ) : reinterpret_cast<float *>(sp + 32 * MJ);
+    // fixed-point scale of the half-list density (2^ex)
+    const float hscale = (HL && KIND == PASS_DENSITY) ? __int_as_float((half_scale_exp(a.st->m_absmax) + 127) << 23) : 0.f;
     const unsigned lane = lane_id();
     const unsigned lt = lanemask_lt();
     const uint32_t II = lane % M;
@@ -162,6 +197,15 @@ __global__ void __launch_bounds__(PS_THREADS, ps_min_blocks<KIND>()) k_pass(Pass
             if constexpr (KIND == PASS_LJC) ri2[k] = fminf(ri2[k], a.p2);
             hinv[k] = 1.f / pi[k].w;
             ci[k] = (KIND == PASS_SPH) ? a.aux[i].y : (KIND == PASS_LJC) ? a.p3 * a.aux[i].x : 0.f;
+        }
+        if constexpr (HL && KIND == PASS_DENSITY) {
+            // masses of the own particles, for the j shares
+            __syncwarp();
+            if (lane < (uint32_t)M) {
+#pragma unroll
+                for (int k = 0; k < kSC; ++k) smi[k * M + II] = a.aux[(s * kSC + k) * M + II].x;
+            }
+            __syncwarp();
         }
         Acc<KIND> acc;
         // density and counts take the self pair i = j inside the loop when the
@@ -227,18 +271,46 @@ __global__ void __launch_bounds__(PS_THREADS, ps_min_blocks<KIND>()) k_pass(Pass
                 const uint32_t e = min(q / MJ, 31u);
                 const uint32_t src = __shfl_sync(0xffffffffu, J, e) * MJ + (q % MJ);
                 if (q < nb * MJ) {
-                    sp[q] = a.pos[src];
-                    if constexpr (AUX) sa[q] = a.aux[src];
+                    if constexpr (HL) {
+                        // half list: w holds rj^2, and the density input's
+                        // second word 1/h_j (dummies: rj = 0, never a pair)
+                        const float4 p = a.pos[src];
+                        const float rj = __fmul_rn(a.support, p.w);
+                        sp[q] = make_float4(p.x, p.y, p.z, __fmul_rn(rj, rj));
+                        if constexpr (AUX) sa[q] = make_float2(a.aux[src].x, 1.f / p.w);
+                    } else {
+                        sp[q] = a.pos[src];
+                        if constexpr (AUX) sa[q] = a.aux[src];
+                    }
                 }
             }
             __syncwarp();
+            // half list: the current entry feeds its j particles too (js), with
+            // the shares of this lane's j particles in jsh / jcn
+            bool js = false;
+            float jsh[NP] = {};
+            uint32_t jcn[NP] = {};
             // one (i-cluster k, j particle) term per lane
-            auto term = [&](int k, const float4 &pj, const float2 &aj, uint32_t jj) {
+            auto term = [&](int k, const float4 &pj, const float2 &aj, uint32_t jj, int tt) {
                 const uint32_t ii = (s * kSC + k) * M + II;
                 // canonical distance decides the pair; the sums use the
                 // accurate vector (identical unless wrapped)
                 const float d2 = pair_d2<PER>(pi[k], pj, box);
-                if constexpr (KIND == PASS_DENSITY) {
+                if constexpr (HL && KIND == PASS_DENSITY) {
+                    const bool ini = d2 < ri2[k];        // i = j included (see selfseen)
+                    const bool inj = js && d2 < pj.w;    // the j share (entries beyond the own clusters)
+                    if (owner && (ini || inj)) {
+                        const float e2 = PER ? d2_of(pair_dx_acc<PER>(pi[k], pj, box)) : d2;
+                        const float r = sqrt_approx(e2);
+                        if (ini) acc.b[k] += aj.x * spline_w_inside(r * hinv[k]);
+                        if (inj) jsh[tt] += smi[k * M + II] * spline_w_inside(r * aj.y);
+                    }
+                } else if constexpr (HL && KIND == PASS_COUNT) {
+                    if (owner) {
+                        if (d2 < ri2[k]) acc.v[k] += 1u;  // i = j included (see selfseen)
+                        if (js && d2 < pj.w) jcn[tt] += 1u;
+                    }
+                } else if constexpr (KIND == PASS_DENSITY) {
                     if (owner && d2 < ri2[k]) {  // i = j included (see selfseen)
                         const float e2 = PER ? d2_of(pair_dx_acc<PER>(pi[k], pj, box)) : d2;
                         acc.b[k] += aj.x * spline_w_inside(sqrt_approx(e2) * hinv[k]);
@@ -291,6 +363,10 @@ __global__ void __launch_bounds__(PS_THREADS, ps_min_blocks<KIND>()) k_pass(Pass
             for (uint32_t e = 0; e < nb; ++e) {
                 const uint32_t Je = __shfl_sync(0xffffffffu, J, e);
                 const uint32_t me = __shfl_sync(0xffffffffu, mk, e);
+                // half list: an entry beyond the own clusters also feeds its j particles
+                js = HL && Je >= (s + 1) * kSC * RJ;
+#pragma unroll
+                for (int tt = 0; tt < NP; ++tt) { jsh[tt] = 0.f; jcn[tt] = 0u; }
                 if constexpr (SELF_IN_LOOP) {
                     const uint32_t rel = Je - s * kSC * RJ;  // j-cluster within the own ones
                     if (rel < (uint32_t)(kSC * RJ)) {
@@ -313,7 +389,7 @@ __global__ void __launch_bounds__(PS_THREADS, ps_min_blocks<KIND>()) k_pass(Pass
                     for (int k = 0; k < kSC; ++k) {
                         if (!((me >> k) & 1u)) continue;
 #pragma unroll
-                        for (int tt = 0; tt < NP; ++tt) term(k, pj[tt], aj[tt], Je * MJ + JJ0 + tt * JSTEP);
+                        for (int tt = 0; tt < NP; ++tt) term(k, pj[tt], aj[tt], Je * MJ + JJ0 + tt * JSTEP, tt);
                     }
                 } else {
 #pragma unroll
@@ -322,7 +398,29 @@ __global__ void __launch_bounds__(PS_THREADS, ps_min_blocks<KIND>()) k_pass(Pass
                         const float2 aj = AUX ? sa[e * MJ + JJ0 + tt * JSTEP] : make_float2(0.f, 0.f);
 #pragma unroll
                         for (int k = 0; k < kSC; ++k)
-                            if ((me >> k) & 1u) term(k, pj, aj, Je * MJ + JJ0 + tt * JSTEP);
+                            if ((me >> k) & 1u) term(k, pj, aj, Je * MJ + JJ0 + tt * JSTEP, tt);
+                    }
+                }
+                if constexpr (HL) {
+                    if (js) {
+                        // sum each j particle's share over the M lanes of its i
+                        // particles (fixed order), one integer add per j particle
+#pragma unroll
+                        for (int tt = 0; tt < NP; ++tt) {
+                            const uint32_t jj = Je * MJ + JJ0 + tt * JSTEP;
+                            if constexpr (KIND == PASS_DENSITY) {
+                                float v = jsh[tt];
+#pragma unroll
+                                for (int o = 1; o < M; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                                if (owner && II == 0 && v != 0.f)
+                                    atomicAdd(&a.hsum[jj], fixed_of(v * hscale));
+                            } else {
+                                uint32_t v = jcn[tt];
+#pragma unroll
+                                for (int o = 1; o < M; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                                if (owner && II == 0 && v != 0u) atomicAdd(&a.hcnt[jj], v);
+                            }
+                        }
                     }
                 }
             }
@@ -359,7 +457,12 @@ __global__ void __launch_bounds__(PS_THREADS, ps_min_blocks<KIND>()) k_pass(Pass
             // the loop took i = j iff its entry was listed and the radius is
             // nonzero (d2 = 0 < r^2)
             const bool took_self = ((selfseen >> k) & 1u) && ri2[k] > 0.f;
-            if constexpr (KIND == PASS_DENSITY) {
+            if constexpr (HL && KIND == PASS_DENSITY) {
+                const float self = took_self ? 0.f : a.aux[i].x;  // m_i w(0) = m_i
+                atomicAdd(&a.hsum[i], fixed_of((acc.v[k] + self) * hscale));
+            } else if constexpr (HL && KIND == PASS_COUNT) {
+                atomicAdd(&a.hcnt[i], acc.v[k] - (took_self ? 1u : 0u));
+            } else if constexpr (KIND == PASS_DENSITY) {
                 const float self = took_self ? 0.f : a.aux[i].x;  // m_i w(0) = m_i
                 a.out0[o] = (acc.v[k] + self) * (0.318309886183790672f * hinv[k] * hinv[k] * hinv[k]);
             } else if constexpr (KIND == PASS_COUNT) {
@@ -377,30 +480,43 @@ __global__ void __launch_bounds__(PS_THREADS, ps_min_blocks<KIND>()) k_pass(Pass
     }
 }
 
-template <int M, int MJ, int KIND>
+template <int M, int MJ, int KIND, bool HL = false>
 static void launch_mk(const PassArgs &a, int per, int grid, int threads, cudaStream_t s)
 {
     // the attribute is set for the largest block so that any shape fits
-    const size_t smax = (size_t)(PS_THREADS / 32) * pass_smem_per_warp<MJ, KIND>();
-    const size_t smem = (size_t)(threads / 32) * pass_smem_per_warp<MJ, KIND>();
+    const size_t smax = (size_t)(PS_THREADS / 32) * pass_smem_per_warp<MJ, KIND, HL>();
+    const size_t smem = (size_t)(threads / 32) * pass_smem_per_warp<MJ, KIND, HL>();
     static bool attr[2] = {false, false};
     if (!attr[per ? 1 : 0]) {
         if (per)
-            cudaFuncSetAttribute(k_pass<M, MJ, true, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+            cudaFuncSetAttribute(k_pass<M, MJ, true, KIND, HL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
         else
-            cudaFuncSetAttribute(k_pass<M, MJ, false, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+            cudaFuncSetAttribute(k_pass<M, MJ, false, KIND, HL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
         attr[per ? 1 : 0] = true;
     }
     if (per)
-        k_pass<M, MJ, true, KIND><<<grid, threads, smem, s>>>(a);
+        k_pass<M, MJ, true, KIND, HL><<<grid, threads, smem, s>>>(a);
     else
-        k_pass<M, MJ, false, KIND><<<grid, threads, smem, s>>>(a);
+        k_pass<M, MJ, false, KIND, HL><<<grid, threads, smem, s>>>(a);
 }
 
 template <int KIND>
 static cudaError_t launch_k(const PassArgs &a, int M, int per, int grid, int threads, cudaStream_t s)
 {
     if (threads != 128 && threads != PS_THREADS) return cudaErrorInvalidValue;
+    if (a.half) {
+        if constexpr (KIND == PASS_DENSITY || KIND == PASS_COUNT) {
+            switch (M * 100 + a.mj) {
+            case 404: launch_mk<4, 4, KIND, true>(a, per, grid, threads, s); break;
+            case 808: launch_mk<8, 8, KIND, true>(a, per, grid, threads, s); break;
+            case 1616: launch_mk<16, 16, KIND, true>(a, per, grid, threads, s); break;
+            default: return cudaErrorInvalidValue;
+            }
+            return cudaGetLastError();
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
     switch (M * 100 + a.mj) {
     case 404: launch_mk<4, 4, KIND>(a, per, grid, threads, s); break;
     case 808: launch_mk<8, 8, KIND>(a, per, grid, threads, s); break;

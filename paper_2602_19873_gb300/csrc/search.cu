@@ -248,9 +248,13 @@ struct SearchSmem {
     uint32_t win[WIN_WORDS];
 };
 
-template <int M, int MJ, bool PER, bool HALF>
+// MODE 0: full list.  MODE 1: half search, upper entries and transposed
+// tuples for the record assembly.  MODE 2: half list (each pair stored once,
+// Sec. II-D): the half search's upper entries encoded as the record.
+template <int M, int MJ, bool PER, int MODE>
 __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCtl ctl)
 {
+    constexpr bool HALF = MODE != 0;  // only j-clusters from the own first one on
     constexpr int NP = (M * MJ) / 32 > 0 ? (M * MJ) / 32 : 1;  // pairs per lane per tile
     constexpr int JSTEP = 32 / M;
     constexpr uint32_t R = M / MJ;        // j-clusters per i-cluster
@@ -432,7 +436,7 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
         bool ok = staged;
         if (!staged) {
             if (lane == 0) atomicMax(&a.st->max_count, cnt);
-        } else if constexpr (HALF) {
+        } else if constexpr (MODE == 1) {
             // a buffer overflow here makes the host re-run every super-cluster
             ok = half_output(cnt, stJ, stM, a, s);
         } else {
@@ -443,12 +447,12 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
         }
         if (lane == 0) {
             if (!ok) {
-                if (!HALF || !staged) {
+                if (MODE != 1 || !staged) {
                     uint32_t r = atomicAdd(&a.st->stage_overflow, 1u);
                     ctl.redo[r] = s;
                 }
                 a.rec_off[s] = kBadRecord;
-            } else if (!HALF) {
+            } else if (MODE != 1) {
                 atomicAdd(&a.st->n_entries, (unsigned long long)cnt);
                 atomicAdd(&a.st->n_tiles, (unsigned long long)tiles);
             }
@@ -460,7 +464,7 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
     }
 }
 
-template <int M, int MJ, bool HALF>
+template <int M, int MJ, int MODE>
 static void launch_m(const SearchArgs &a, const SearchCtl &c, int per, int grid, int threads,
                      cudaStream_t s)
 {
@@ -469,15 +473,15 @@ static void launch_m(const SearchArgs &a, const SearchCtl &c, int per, int grid,
     static bool attr[2] = {false, false};
     if (!attr[per ? 1 : 0]) {
         if (per)
-            cudaFuncSetAttribute(k_search<M, MJ, true, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+            cudaFuncSetAttribute(k_search<M, MJ, true, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
         else
-            cudaFuncSetAttribute(k_search<M, MJ, false, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+            cudaFuncSetAttribute(k_search<M, MJ, false, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
         attr[per ? 1 : 0] = true;
     }
     if (per)
-        k_search<M, MJ, true, HALF><<<grid, threads, smem, s>>>(a, c);
+        k_search<M, MJ, true, MODE><<<grid, threads, smem, s>>>(a, c);
     else
-        k_search<M, MJ, false, HALF><<<grid, threads, smem, s>>>(a, c);
+        k_search<M, MJ, false, MODE><<<grid, threads, smem, s>>>(a, c);
 }
 
 cudaError_t launch_search_ctl(const SearchArgs &a, const uint32_t *work, uint32_t count,
@@ -487,21 +491,25 @@ cudaError_t launch_search_ctl(const SearchArgs &a, const uint32_t *work, uint32_
     SearchCtl c{work, count, redo, count_dev};
     if (threads != 128 && threads != SR_THREADS) return cudaErrorInvalidValue;
     if (a.half && a.mj != M) return cudaErrorInvalidValue;  // needs j-clusters = i-clusters
+    if (a.half < 0 || a.half > 2) return cudaErrorInvalidValue;
     switch (M * 100 + a.mj) {
     case 404:
-        if (a.half) launch_m<4, 4, true>(a, c, any_periodic, grid, threads, s);
-        else launch_m<4, 4, false>(a, c, any_periodic, grid, threads, s);
+        if (a.half == 1) launch_m<4, 4, 1>(a, c, any_periodic, grid, threads, s);
+        else if (a.half == 2) launch_m<4, 4, 2>(a, c, any_periodic, grid, threads, s);
+        else launch_m<4, 4, 0>(a, c, any_periodic, grid, threads, s);
         break;
     case 808:
-        if (a.half) launch_m<8, 8, true>(a, c, any_periodic, grid, threads, s);
-        else launch_m<8, 8, false>(a, c, any_periodic, grid, threads, s);
+        if (a.half == 1) launch_m<8, 8, 1>(a, c, any_periodic, grid, threads, s);
+        else if (a.half == 2) launch_m<8, 8, 2>(a, c, any_periodic, grid, threads, s);
+        else launch_m<8, 8, 0>(a, c, any_periodic, grid, threads, s);
         break;
-    case 804: launch_m<8, 4, false>(a, c, any_periodic, grid, threads, s); break;
+    case 804: launch_m<8, 4, 0>(a, c, any_periodic, grid, threads, s); break;
     case 1616:
-        if (a.half) launch_m<16, 16, true>(a, c, any_periodic, grid, threads, s);
-        else launch_m<16, 16, false>(a, c, any_periodic, grid, threads, s);
+        if (a.half == 1) launch_m<16, 16, 1>(a, c, any_periodic, grid, threads, s);
+        else if (a.half == 2) launch_m<16, 16, 2>(a, c, any_periodic, grid, threads, s);
+        else launch_m<16, 16, 0>(a, c, any_periodic, grid, threads, s);
         break;
-    case 1608: launch_m<16, 8, false>(a, c, any_periodic, grid, threads, s); break;
+    case 1608: launch_m<16, 8, 0>(a, c, any_periodic, grid, threads, s); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

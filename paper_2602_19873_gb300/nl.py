@@ -38,7 +38,7 @@ class nl_params(C.Structure):
     _fields_ = [("key", C.c_int32), ("cluster", C.c_int32), ("support", C.c_float),
                 ("compress", C.c_int32), ("leaf_bucket", C.c_int32),
                 ("threads_per_block", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("j_cluster", C.c_int32)]
+                ("j_cluster", C.c_int32), ("half_list", C.c_int32)]
 
 
 class nl_sizes(C.Structure):
@@ -164,14 +164,15 @@ def make_box(box):
 
 
 def make_params(key=NL_KEY_HILBERT, cluster=8, support=2.0, compress=1, leaf_bucket=256,
-                threads_per_block=0, blocks_per_sm=0, j_cluster=0):
-    """Build options; j_cluster 0 means j-clusters of `cluster` particles."""
+                threads_per_block=0, blocks_per_sm=0, j_cluster=0, half_list=0):
+    """Build options; j_cluster 0 means j-clusters of `cluster` particles;
+    half_list 1 stores every cluster pair once."""
     p = nl_params()
     load().nl_default_params(C.byref(p))
     p.key, p.cluster, p.support = int(key), int(cluster), float(support)
     p.compress, p.leaf_bucket = int(compress), int(leaf_bucket)
     p.threads_per_block, p.blocks_per_sm = int(threads_per_block), int(blocks_per_sm)
-    p.j_cluster = int(j_cluster)
+    p.j_cluster, p.half_list = int(j_cluster), int(half_list)
     return p
 
 

@@ -16,12 +16,13 @@ def to_dev(d, keys=("x", "y", "z", "h", "m")):
     return {k: torch.from_numpy(np.ascontiguousarray(d[k], dtype=np.float32)).cuda() for k in keys}
 
 
-def gpu_build(d, cluster=8, compress=1, bucket=256, kind=None, support=None, j_cluster=0):
+def gpu_build(d, cluster=8, compress=1, bucket=256, kind=None, support=None, j_cluster=0,
+              half_list=0):
     import torch
     t = to_dev(d)
     p = nl.make_params(key=d["kind"] if kind is None else kind, cluster=cluster,
                        support=d["support"] if support is None else support, compress=compress,
-                       leaf_bucket=bucket, j_cluster=j_cluster)
+                       leaf_bucket=bucket, j_cluster=j_cluster, half_list=half_list)
     L = nl.NeighborList().build(t["x"], t["y"], t["z"], t["h"], d["box"], p)
     torch.cuda.synchronize()
     return L, t
@@ -47,12 +48,16 @@ def gpu_records(L, sc_ids):
     return out
 
 
-def compare_records(L, o, d, cluster, compress, sc_ids, rows, p_off, p_idx, jcluster=None):
+def compare_records(L, o, d, cluster, compress, sc_ids, rows, p_off, p_idx, jcluster=None,
+                    half=False):
     """Byte-exact comparison of the GPU records of sc_ids with the oracle's
-    independent encoding of the canonical lists built from (rows, P)."""
+    independent encoding of the canonical lists built from (rows, P); half:
+    the oracle's half lists."""
     n = len(o["xs"])
     so, J, m = orc.cluster_lists(n, cluster, p_off, p_idx, rows, sc_ids,
                                  jcluster=jcluster or cluster)
+    if half:
+        so, J, m = orc.half_lists(so, J, m, sc_ids)
     off, data = L.records()
     total = 0
     for t, s in enumerate(sc_ids):

@@ -1,0 +1,166 @@
+"""Half lists (every pair of clusters of two super-clusters stored once, the
+symmetric lists of Sec. II-D): records byte-exact against the oracle's half
+lists, densities within 1e-5 and counts exact against the oracle, repeatable
+bit for bit (the j shares are added as integers), in batches and CUDA graphs
+too; the force passes refuse them."""
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_2602_19873_gb300 import nl
+from paper_2602_19873_gb300 import workloads as wl
+
+from nlcheck import (DENSITY_RTOL, compare_records, full_reference, gpu_build, gpu_counts,
+                     gpu_density, oracle_sorted)
+
+pytestmark = pytest.mark.gpu
+
+
+def _cases():
+    return {
+        "uniform": lambda: wl.uniform(20037, seed=131, n_target=60.0),
+        "evrard": lambda: wl.evrard(20011, seed=132, n_target=60.0),
+        "plummer": lambda: wl.plummer(24001, n_spheres=3, seed=133, n_target=60.0),
+        "lj_fluid": lambda: wl.lj_fluid(12000, seed=134),
+    }
+
+
+@pytest.fixture(scope="module")
+def cases():
+    out = {}
+    for k, f in _cases().items():
+        d = f()
+        o = oracle_sorted(d)
+        out[k] = (d, o, full_reference(o, d))
+    return out
+
+
+@pytest.mark.parametrize("cluster", [4, 8, 16])
+@pytest.mark.parametrize("name", ["uniform", "evrard", "plummer", "lj_fluid"])
+def test_half_list_records_density_counts(cases, name, cluster):
+    d, o, (g_off, g_idx, p_off, p_idx) = cases[name]
+    n = len(o["xs"])
+    L, t = gpu_build(d, cluster=cluster, half_list=1)
+    nsc = L.sizes()["n_superclusters"]
+    total, so, J, m = compare_records(L, o, d, cluster, 1, np.arange(nsc), np.arange(n), p_off,
+                                      p_idx, half=True)
+    assert L.sizes()["list_bytes"] == total
+    assert L.sizes()["n_entries"] == len(J)
+    rho = gpu_density(L, t, n)
+    want = orc.density(o["xs"], o["ys"], o["zs"], o["hs"], o["ms"], d["box"], g_off, g_idx,
+                       np.arange(n))
+    rel = np.abs(rho[o["perm"]] - want) / want
+    assert rel.max() <= DENSITY_RTOL, rel.max()
+    assert np.array_equal(gpu_counts(L, n)[o["perm"]], np.diff(g_off))
+    # the same bits on a second pass
+    assert np.array_equal(gpu_density(L, t, n), rho)
+    # about half of the full list's entries
+    F, _ = gpu_build(d, cluster=cluster)
+    assert L.sizes()["list_bytes"] < 0.75 * F.sizes()["list_bytes"]
+    F.free()
+    L.free()
+
+
+def test_half_list_uncompressed(cases):
+    d, o, (g_off, g_idx, p_off, p_idx) = cases["plummer"]
+    n = len(o["xs"])
+    L, t = gpu_build(d, cluster=8, compress=0, half_list=1)
+    nsc = L.sizes()["n_superclusters"]
+    compare_records(L, o, d, 8, 0, np.arange(nsc), np.arange(n), p_off, p_idx, half=True)
+    assert np.array_equal(gpu_counts(L, n)[o["perm"]], np.diff(g_off))
+    L.free()
+
+
+def test_half_list_refuses_forces_and_split_tiles(cases):
+    import torch
+    d, o, _ = cases["lj_fluid"]
+    n = len(o["xs"])
+    L, t = gpu_build(d, half_list=1)
+    out = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+    with pytest.raises(nl.NLError):
+        L.force_pass(nl.NL_FORCE_LJ, *out, eps=1.0, sigma=0.3)
+    L.free()
+    with pytest.raises(nl.NLError):
+        gpu_build(d, cluster=8, j_cluster=4, half_list=1)
+
+
+def test_half_list_batch_of_open_and_periodic_systems():
+    import torch
+    systems = wl.batched(n_systems=10, seed=135, log_n=(2.7, 3.6))
+    offs = np.zeros(len(systems) + 1, np.int64)
+    offs[1:] = np.cumsum([len(d["x"]) for d in systems])
+    dev = {k: torch.from_numpy(np.concatenate([d[k] for d in systems]).astype(np.float32)).cuda()
+           for k in "xyzhm"}
+    p = nl.make_params(key=1, cluster=8, support=2.0, half_list=1)
+    L = nl.NeighborList().build_batch(dev["x"], dev["y"], dev["z"], dev["h"], offs,
+                                      [d["box"] for d in systems], p)
+    n = int(offs[-1])
+    rho = torch.empty(n, dtype=torch.float32, device="cuda")
+    L.density_pass(dev["m"], rho)
+    cnt = torch.empty(n, dtype=torch.int32, device="cuda")
+    L.neighbor_counts(cnt)
+    torch.cuda.synchronize()
+    rho, cnt = rho.cpu().numpy(), cnt.cpu().numpy()
+    for k, d in enumerate(systems):
+        o = oracle_sorted(d, kind=1)
+        g_off, g_idx = orc.gather_all(o["xs"], o["ys"], o["zs"], o["hs"], d["box"], 2.0)
+        want = orc.density(o["xs"], o["ys"], o["zs"], o["hs"], o["ms"], d["box"], g_off, g_idx,
+                           np.arange(len(o["xs"])))
+        got = rho[offs[k]:offs[k + 1]][o["perm"]]
+        assert (np.abs(got - want) / want).max() <= DENSITY_RTOL, k
+        assert np.array_equal(cnt[offs[k]:offs[k + 1]][o["perm"]], np.diff(g_off)), k
+    L.free()
+
+
+def test_half_list_graph_replay_matches_normal_build():
+    import torch
+    stream = torch.cuda.Stream()
+    systems = wl.batched(n_systems=8, seed=136, log_n=(2.7, 3.5))
+    offs = np.zeros(len(systems) + 1, np.int64)
+    offs[1:] = np.cumsum([len(d["x"]) for d in systems])
+    dev = {k: torch.from_numpy(np.concatenate([d[k] for d in systems]).astype(np.float32)).cuda()
+           for k in "xyzhm"}
+    boxes = [d["box"] for d in systems]
+    p = nl.make_params(key=1, cluster=8, support=2.0, half_list=1)
+    with torch.cuda.stream(stream):
+        A = nl.NeighborList().build_batch(dev["x"], dev["y"], dev["z"], dev["h"], offs, boxes, p,
+                                          stream)
+        want = torch.empty(int(offs[-1]), dtype=torch.float32, device="cuda")
+        A.density_pass(dev["m"], want, stream)
+        stream.synchronize()
+        rho = torch.zeros(int(offs[-1]), dtype=torch.float32, device="cuda")
+        L = nl.NeighborList()
+        G = nl.Graph(L, dev["x"], dev["y"], dev["z"], dev["h"], dev["m"], rho, offs, boxes, p,
+                     stream)
+        rho.zero_()
+        for _ in range(2):
+            G.launch(stream)
+        G.check(stream)
+        stream.synchronize()
+        assert np.array_equal(rho.cpu().numpy(), want.cpu().numpy())
+        assert L.sizes()["list_bytes"] == A.sizes()["list_bytes"]
+    A.free()
+    G.free()
+    L.free()
+
+
+def test_half_list_evrard_2m_sampled():
+    """Full size (2^21 particles, 8x8, compressed, leaf bucket 256): sampled
+    super-clusters byte-exact against the oracle's half lists, their
+    particles' densities within 1e-5."""
+    d = wl.cached(wl.evrard, "evrard_%d_2" % (1 << 21), 1 << 21, seed=2)
+    o = oracle_sorted(d)
+    n = len(o["xs"])
+    L, t = gpu_build(d, cluster=8, compress=1, bucket=256, half_list=1)
+    nsc = L.sizes()["n_superclusters"]
+    rng = np.random.default_rng(137)
+    sc = np.unique(np.concatenate([[0, nsc // 2, nsc - 1], rng.integers(0, nsc, 5)]))
+    rows = np.concatenate([np.arange(s * 64, min(n, (s + 1) * 64)) for s in sc])
+    p_off, p_idx = orc.brute_neighbors(o["xs"], o["ys"], o["zs"], o["hs"], d["box"], 2.0, 1, rows)
+    compare_records(L, o, d, 8, 1, sc, rows, p_off, p_idx, half=True)
+    g_off, g_idx = orc.brute_neighbors(o["xs"], o["ys"], o["zs"], o["hs"], d["box"], 2.0, 0, rows)
+    rho = gpu_density(L, t, n)[o["perm"]]
+    want = orc.density(o["xs"], o["ys"], o["zs"], o["hs"], o["ms"], d["box"], g_off, g_idx, rows)
+    assert (np.abs(rho[rows] - want) / want).max() <= DENSITY_RTOL
+    assert np.array_equal(gpu_counts(L, n)[o["perm"]][rows], np.diff(g_off))
+    L.free()
