@@ -697,8 +697,9 @@ def run_config(args):
 
 def run_sweep(args):
     """List size and cluster overhead against the neighbor count on the LJ
-    fluid (100 nm^-3): 8x8 and 8x4 tiles, compressed and raw lists, build and
-    Lennard-Jones pass times."""
+    fluid (100 nm^-3): 8x8 and 8x4 tiles, compressed and raw lists, full and
+    (8x8) half lists, build and pass times (Lennard-Jones on full lists,
+    density on half lists)."""
     import torch
     from paper_2602_19873_gb300 import nl
     from paper_2602_19873_gb300 import workloads as wl
@@ -715,9 +716,10 @@ def run_sweep(args):
     for nb in (25, 50, 100, 200, 400, 800, 1600):
         rc = (3.0 * nb / (4.0 * math.pi * 100.0)) ** (1.0 / 3.0)
         h = torch.full((n,), rc, dtype=torch.float32, device="cuda")
-        for (M, MJ) in ((8, 8), (8, 4)):
+        for (M, MJ, half) in ((8, 8, 0), (8, 4, 0), (8, 8, 1)):
             for comp in (1, 0):
-                p = nl.make_params(key=1, cluster=M, j_cluster=MJ, support=1.0, compress=comp)
+                p = nl.make_params(key=1, cluster=M, j_cluster=MJ, support=1.0, compress=comp,
+                                   half_list=half)
                 L = nl.NeighborList()
                 e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
                 for r in range(4):
@@ -726,23 +728,27 @@ def run_sweep(args):
                     L.build(dev["x"], dev["y"], dev["z"], h, d["box"], p, stream)
                     if r == 3:
                         e[1].record(stream)
-                    L.force_pass(nl.NL_FORCE_LJ, *out0, eps=1.0, sigma=0.3, stream=stream)
+                    if half:  # half lists serve the density and count passes
+                        L.density_pass(dev["m"], out0[0], stream)
+                    else:
+                        L.force_pass(nl.NL_FORCE_LJ, *out0, eps=1.0, sigma=0.3, stream=stream)
                     if r == 3:
                         e[2].record(stream)
                 torch.cuda.synchronize()
                 sz = L.sizes()
-                if (M, MJ, comp) == (8, 8, 1):
+                if (M, MJ, comp, half) == (8, 8, 1, 0):
                     L.neighbor_counts(cnt, stream)
                     useful = int(cnt.sum().item())
                 pairs = sz["n_tiles"] * M * MJ
                 rows.append({"neighbors_target": nb, "rc_nm": rc, "tile": "%dx%d" % (M, MJ),
+                             "list": "half" if half else "full",
                              "compressed": bool(comp),
                              "mean_neighbors": useful / n,
                              "bytes_per_particle": sz["list_bytes"] / n,
                              "full_list_bytes_per_particle": 4.0 * useful / n,
-                             "cluster_overhead": pairs / float(useful + n),
+                             "cluster_overhead": pairs / float(useful + n) * (2 if half else 1),
                              "build_ms": e[0].elapsed_time(e[1]),
-                             "lj_pass_ms": e[1].elapsed_time(e[2])})
+                             ("density_pass_ms" if half else "lj_pass_ms"): e[1].elapsed_time(e[2])})
                 L.free()
     print(json.dumps({"sweep": "LJ fluid 4,000,000 atoms at 100 nm^-3, periodic, Hilbert keys, "
                                "leaf bucket 256; list radius for the target neighbor count",

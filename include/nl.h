@@ -329,7 +329,8 @@ nl_status nl_graph_free(nl_graph *g);
 /* Autotuner: times build + density of the given batch for every candidate
  * tile shape M x MJ in {4x4, 8x8, 8x4, 16x16, 16x8}, block shape in {128, 256} threads and
  * persistent-grid occupancy in {2, 3, 4} blocks per SM (reps timed runs
- * each after one warm-up, CUDA events on `stream`) and writes the fastest
+ * each after one warm-up, CUDA events on `stream`; with base->half_list only
+ * the shapes with MJ = M) and writes the fastest
  * parameters (other fields copied from *base) to *best and its mean time
  * to *best_ms.  Synchronises `stream`. */
 nl_status nl_autotune_batch(const float *x, const float *y, const float *z, const float *h,
