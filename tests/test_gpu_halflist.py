@@ -164,3 +164,48 @@ def test_half_list_evrard_2m_sampled():
     assert (np.abs(rho[rows] - want) / want).max() <= DENSITY_RTOL
     assert np.array_equal(gpu_counts(L, n)[o["perm"]][rows], np.diff(g_off))
     L.free()
+
+
+def test_half_list_from_host_buffers_and_mass_scaling(cases):
+    """The host-buffer entry point on half lists: the same bits as the device
+    build and pass, and the oracle's density for masses scaled by 2^+-k and by
+    3 (the fixed-point unit follows the largest mass)."""
+    import torch
+    d, o, (g_off, g_idx, p_off, p_idx) = cases["plummer"]
+    n = len(o["xs"])
+    L, t = gpu_build(d, half_list=1)
+    want = gpu_density(L, t, n)
+    L.free()
+    p = nl.make_params(key=d["kind"], cluster=8, support=d["support"], half_list=1)
+    E = nl.NeighborList()
+    host = {k: np.ascontiguousarray(d[k], dtype=np.float32) for k in ("x", "y", "z", "h", "m")}
+    rho = np.empty(n, np.float32)
+    E.density_from_host(host["x"], host["y"], host["z"], host["h"], host["m"], d["box"], p, rho)
+    assert np.array_equal(rho, want)
+    for scale in (1024.0, 1.0 / 4096.0, 3.0, 1e-20, 1e20):
+        m = host["m"] * np.float32(scale)
+        E.density_from_host(host["x"], host["y"], host["z"], host["h"], m, d["box"], p, rho)
+        ref = orc.density(o["xs"], o["ys"], o["zs"], o["hs"], o["ms"] * np.float32(scale),
+                          d["box"], g_off, g_idx, np.arange(n))
+        assert (np.abs(rho[o["perm"]] - ref) / ref).max() <= DENSITY_RTOL, scale
+    E.free()
+
+
+def test_h_iteration_with_half_list_params_builds_full_lists(cases):
+    """The h iteration re-runs single super-clusters, so it works on full lists
+    whatever half_list says: the same h as with full-list parameters."""
+    import torch
+    d, o, _ = cases["evrard"]
+    t = {k: torch.from_numpy(np.ascontiguousarray(d[k], np.float32)).cuda() for k in "xyzh"}
+    out = []
+    for half in (0, 1):
+        h = t["h"].clone()
+        H = nl.NeighborList()
+        p = nl.make_params(key=d["kind"], cluster=8, support=2.0, half_list=half)
+        H.iterate_h(t["x"], t["y"], t["z"], h, d["box"], p, 60.0, 2.0, max_iter=60,
+                    start=nl.NL_HSTART_PLAIN)
+        assert H.sizes()["list_bytes"] > 0
+        out.append((h.cpu().numpy(), H.sizes()["list_bytes"]))
+        H.free()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]  # both left a full list
