@@ -611,7 +611,7 @@ def run_config(args):
     dev = {k: torch.from_numpy(np.ascontiguousarray(d[k], dtype=np.float32)).cuda()
            for k in ("x", "y", "z", "h", "m") + (("q",) if "q" in d else ())}
     params = nl.make_params(key=d["kind"], cluster=8, support=d["support"], compress=1,
-                            leaf_bucket=args.leaf_bucket)
+                            leaf_bucket=args.leaf_bucket, half_list=int(args.list == "half"))
     stream = torch.cuda.current_stream()
     if gen == "evrard_2m":  # smoothing lengths at 200 +- 2 neighbors (untimed input preparation)
         H = nl.NeighborList()
@@ -665,7 +665,7 @@ def run_config(args):
            "value": job_rate(n, ws, ms), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "%s: %s" % (args.workload, desc), "n": n,
+           "config": {"workload": "%s: %s" % (args.workload, desc), "n": n, "list": args.list,
                       "l2": "inputs larger than L2 except uniform_32k (no flush)"},
            "stages_ms": L.stage_times(),
            "list": {"bytes_per_particle": sizes["list_bytes"] / n, "entries": sizes["n_entries"],

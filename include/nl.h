@@ -79,10 +79,11 @@ typedef struct {
     int32_t half_list;    /* 1: store every cluster pair once (the symmetric list of
                              Sec. II-D): the record of super-cluster s holds only the
                              j-clusters J >= 8s of its full record, with the same masks,
-                             and the density and count passes add each pair to both of
-                             its particles.  Needs MJ = M.  The force passes need a full
-                             list (0, the default); the h iteration always builds full
-                             lists. */
+                             and every pass adds each pair to both of its particles
+                             (density and counts as integers: the same bits on every
+                             run; forces as FP64 sums rounded once to FP32, where the
+                             order of the adds can move the last bit in rare ties).
+                             Needs MJ = M.  The h iteration always builds full lists. */
 } nl_params;
 
 /* Fills p with {NL_KEY_HILBERT, 8, 2.0f, 1, 256, 0, 0, 0, 0}. */
@@ -150,7 +151,9 @@ nl_status nl_density_pass(const nl_list *nl, const float *m, float *rho, void *s
  *    the force over all pairs within rc, also after nl_refresh_positions as
  *    long as twice its max_disp stays below min(ri) - rc.
  * ax, ay, az: n device floats written in caller order.  FP32 arithmetic with
- * block-partial sums.  Does not synchronise. */
+ * block-partial sums; on a half list each pair also gives particle j its
+ * force (SPH: -m_i/m_j times i's pair term; LJ, LJ + Coulomb: -F_ij when
+ * d2 < rj^2), the shares summed in FP64.  Does not synchronise. */
 enum { NL_FORCE_SPH_PRESSURE = 0, NL_FORCE_LJ = 1, NL_FORCE_LJ_COULOMB = 2 };
 nl_status nl_force_pass(const nl_list *nl, int32_t kind, const float *params, const float *m,
                         const float *rho, const float *pres, float *ax, float *ay, float *az,

@@ -122,8 +122,9 @@ struct nl_list {
     // keeps the positions the list was built on
     int moved = 0;
     DevBuf pos_ref;
-    // half-list passes: per sorted particle fixed-point density sums, counts
-    DevBuf hsum, hcnt;
+    // half-list passes: per sorted particle fixed-point density sums, counts,
+    // FP64 force sums
+    DevBuf hsum, hcnt, hf;
     uint32_t node_cap = 0;
     const struct nl_mlp *mlp = nullptr;
     DevBuf ml_X, ml_e64, ml_pred, ml_slo, ml_shi;
@@ -185,7 +186,7 @@ struct nl_list {
                          &it_words, &it_tmp, &ml_X, &ml_e64, &ml_pred, &ml_slo, &ml_shi,
                          &uJ, &uM, &up_off, &up_cnt, &lower_cnt, &seg_off, &tkey, &tkey_alt,
                          &tval, &tval_alt, &thist, &sc_open, &sc_per, &sc_int, &sc_bnd,
-                         &pos_ref, &hsum, &hcnt};
+                         &pos_ref, &hsum, &hcnt, &hf};
         for (DevBuf *b : all) b->release();
         for (int i = 0; i <= kStages; ++i)
             if (ev[i]) cudaEventDestroy(ev[i]);
@@ -888,6 +889,7 @@ PassArgs pass_args(const nl_list *nl)
     a.half = nl->p.half_list;
     a.hsum = nl->hsum.as<unsigned long long>();
     a.hcnt = nl->hcnt.as<uint32_t>();
+    a.hf = nl->hf.as<double>();
     return a;
 }
 
@@ -1625,9 +1627,10 @@ nl_status nl_force_pass(const nl_list *cnl, int32_t kind, const float *params, c
     nl_status st = check_list(cnl);
     if (st != NL_OK) return st;
     if (!ax || !ay || !az) return fail(NL_ERR_ARG, "NULL force output");
-    if (cnl->p.half_list) return fail(NL_ERR_ARG, "the force passes need a full list (half_list = 0)");
     nl_list *nl = const_cast<nl_list *>(cnl);
     cudaStream_t s = (cudaStream_t)stream;
+    const bool half = nl->p.half_list != 0;
+    if (half) CK(nl->hf.ensure((size_t)nl->npad * 24));
     if (kind == NL_FORCE_SPH_PRESSURE) {
         if (!m || !rho || !pres) return fail(NL_ERR_ARG, "SPH force needs m, rho and pres");
         CK(nl->aux.ensure((size_t)nl->npad * 8));
@@ -1641,7 +1644,9 @@ nl_status nl_force_pass(const nl_list *cnl, int32_t kind, const float *params, c
         CK(launch_gather_aux(nl->npad, nl->perm_pad.as<uint32_t>(), m, pres, rho, 1,
                              nl->aux.as<float2>(), s));
         CK(nl->mark(7, s));
+        if (half) CK(cudaMemsetAsync(nl->hf.p, 0, (size_t)nl->npad * 24, s));
         CK(run_pass(nl, a, PASS_SPH, s));
+        if (half) CK(launch_half_finish(a, PASS_SPH, nl->npad, s));
         CK(nl->mark(8, s));
     } else if (kind == NL_FORCE_LJ) {
         if (!params) return fail(NL_ERR_ARG, "LJ force needs params {eps, sigma}");
@@ -1651,7 +1656,9 @@ nl_status nl_force_pass(const nl_list *cnl, int32_t kind, const float *params, c
         a.p1 = params[1];
         CK(nl->mark(6, s));
         CK(nl->mark(7, s));
+        if (half) CK(cudaMemsetAsync(nl->hf.p, 0, (size_t)nl->npad * 24, s));
         CK(run_pass(nl, a, PASS_LJ, s));
+        if (half) CK(launch_half_finish(a, PASS_LJ, nl->npad, s));
         CK(nl->mark(8, s));
     } else if (kind == NL_FORCE_LJ_COULOMB) {
         if (!params) return fail(NL_ERR_ARG, "LJ + Coulomb needs params {eps, sigma, rc, kc}");
@@ -1674,7 +1681,9 @@ nl_status nl_force_pass(const nl_list *cnl, int32_t kind, const float *params, c
         else
             CK(cudaMemsetAsync(nl->aux.p, 0, (size_t)nl->npad * 8, s));
         CK(nl->mark(7, s));
+        if (half) CK(cudaMemsetAsync(nl->hf.p, 0, (size_t)nl->npad * 24, s));
         CK(run_pass(nl, a, PASS_LJC, s));
+        if (half) CK(launch_half_finish(a, PASS_LJC, nl->npad, s));
         CK(nl->mark(8, s));
     } else {
         return fail(NL_ERR_ARG, "unknown force kind %d", kind);

@@ -603,6 +603,7 @@ struct PassArgs {
     int half;
     unsigned long long *hsum;   // density: per sorted particle, sum m_j w in units of 2^-scale
     uint32_t *hcnt;             // counts: per sorted particle
+    double *hf;                 // forces: per sorted particle, 3 FP64 sums
 };
 
 // Fixed-point scale of the half-list density: 2^(40 - e) with |m| < 2^e for
@@ -621,7 +622,7 @@ cudaError_t launch_pass(const PassArgs &a, int kind, int M, int any_periodic, in
 cudaError_t launch_gather_aux(uint32_t npad, const uint32_t *perm_pad, const float *a,
                               const float *b, const float *c, int mode, float2 *aux,
                               cudaStream_t s, unsigned int *amax = nullptr);
-// Outputs of a half-list pass (PASS_DENSITY or PASS_COUNT) from its sums.
+// Outputs of a half-list pass from its sums (any pass kind).
 cudaError_t launch_half_finish(const PassArgs &a, int kind, uint32_t npad, cudaStream_t s);
 
 // pos[k].xyz = caller position perm_pad[k] (h kept); *max_disp (device, may be

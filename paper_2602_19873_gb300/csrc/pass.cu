@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(256) k_gather_aux(uint32_t npad, const uint32_
 
 // Outputs of a half-list pass: density = (sum in fixed point) * 2^-scale *
 // W's normalisation 1/(pi h^3), in the same FP32 form as the full-list pass;
-// counts as summed.  Real slots only, written at perm[k] (or k).
+// counts as summed; forces rounded from their FP64 sums.  Real slots only,
+// written at perm[k] (or k).
 __global__ void __launch_bounds__(256) k_half_finish(PassArgs a, int kind, uint32_t npad)
 {
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -81,6 +82,12 @@ __global__ void __launch_bounds__(256) k_half_finish(PassArgs a, int kind, uint3
         a.outc[o] = a.hcnt[k];
         return;
     }
+    if (kind != PASS_DENSITY) {  // forces: the FP64 sums rounded once to FP32
+        a.out0[o] = (float)a.hf[3 * (size_t)k + 0];
+        a.out1[o] = (float)a.hf[3 * (size_t)k + 1];
+        a.out2[o] = (float)a.hf[3 * (size_t)k + 2];
+        return;
+    }
     const int ex = half_scale_exp(a.st->m_absmax);
     const double unit = __longlong_as_double((long long)(1023 - ex) << 52);  // 2^-ex
     const float v = (float)((double)(long long)a.hsum[k] * unit);
@@ -90,7 +97,7 @@ __global__ void __launch_bounds__(256) k_half_finish(PassArgs a, int kind, uint3
 
 cudaError_t launch_half_finish(const PassArgs &a, int kind, uint32_t npad, cudaStream_t s)
 {
-    if (kind != PASS_DENSITY && kind != PASS_COUNT) return cudaErrorInvalidValue;
+    if (kind < PASS_DENSITY || kind > PASS_LJC) return cudaErrorInvalidValue;
     k_half_finish<<<(npad + 255) / 256, 256, 0, s>>>(a, kind, npad);
     return cudaGetLastError();
 }

@@ -148,6 +148,19 @@ __device__ __forceinline__ unsigned long long fixed_of(float x)
     return (b >> 31) ? (0ull - q) : q;
 }
 
+// The FP64 value of x with integer operations only (exact for normal x;
+// zero and subnormals, below 1.2e-38, give 0; inf and NaN stay so).
+__device__ __forceinline__ double f64_of(float x)
+{
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t e = (b >> 23) & 0xffu;
+    if (e == 0u) return 0.0;
+    const unsigned long long d = ((unsigned long long)(b >> 31) << 63) |
+                                 ((unsigned long long)(e == 255u ? 2047u : e + 896u) << 52) |
+                                 ((unsigned long long)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)d);
+}
+
 // HL: the list holds every cluster pair once (half list, MJ = M).  Entries
 // of the super-cluster's own clusters are complete as they are (both orders
 // of every pair are listed); an entry J beyond them is a pair of clusters
@@ -161,7 +174,8 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
     constexpr int NP = (M * MJ) / 32 > 0 ? (M * MJ) / 32 : 1;
     constexpr int JSTEP = 32 / M;
     constexpr bool AUX = (KIND == PASS_DENSITY || KIND == PASS_SPH || KIND == PASS_LJC);
-    static_assert(!HL || ((KIND == PASS_DENSITY || KIND == PASS_COUNT) && M == MJ), "half-list pass");
+    static_assert(!HL || M == MJ, "half lists have j-clusters of the i-cluster size");
+    constexpr bool FORCE = (KIND == PASS_SPH || KIND == PASS_LJ || KIND == PASS_LJC);
     extern __shared__ __align__(16) unsigned char pass_smem[];
     float4 *sp = reinterpret_cast<float4 *>(pass_smem + (threadIdx.x >> 5) * pass_smem_per_warp<MJ, KIND, HL>());
     float2 *sa = reinterpret_cast<float2 *>(sp + 32 * MJ);
@@ -198,7 +212,7 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
             hinv[k] = 1.f / pi[k].w;
             ci[k] = (KIND == PASS_SPH) ? a.aux[i].y : (KIND == PASS_LJC) ? a.p3 * a.aux[i].x : 0.f;
         }
-        if constexpr (HL && KIND == PASS_DENSITY) {
+        if constexpr (HL && (KIND == PASS_DENSITY || KIND == PASS_SPH)) {
             // masses of the own particles, for the j shares
             __syncwarp();
             if (lane < (uint32_t)M) {
@@ -271,13 +285,21 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                 const uint32_t e = min(q / MJ, 31u);
                 const uint32_t src = __shfl_sync(0xffffffffu, J, e) * MJ + (q % MJ);
                 if (q < nb * MJ) {
-                    if constexpr (HL) {
+                    if constexpr (HL && (KIND == PASS_DENSITY || KIND == PASS_COUNT)) {
                         // half list: w holds rj^2, and the density input's
                         // second word 1/h_j (dummies: rj = 0, never a pair)
                         const float4 p = a.pos[src];
                         const float rj = __fmul_rn(a.support, p.w);
                         sp[q] = make_float4(p.x, p.y, p.z, __fmul_rn(rj, rj));
                         if constexpr (AUX) sa[q] = make_float2(a.aux[src].x, 1.f / p.w);
+                    } else if constexpr (HL && (KIND == PASS_LJ || KIND == PASS_LJC)) {
+                        // half list: w holds particle j's own squared cutoff
+                        const float4 p = a.pos[src];
+                        const float rj = __fmul_rn(a.support, p.w);
+                        float rj2 = __fmul_rn(rj, rj);
+                        if constexpr (KIND == PASS_LJC) rj2 = fminf(rj2, a.p2);
+                        sp[q] = make_float4(p.x, p.y, p.z, rj2);
+                        if constexpr (AUX) sa[q] = a.aux[src];
                     } else {
                         sp[q] = a.pos[src];
                         if constexpr (AUX) sa[q] = a.aux[src];
@@ -290,6 +312,7 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
             bool js = false;
             float jsh[NP] = {};
             uint32_t jcn[NP] = {};
+            float jfx[NP] = {}, jfy[NP] = {}, jfz[NP] = {};
             // one (i-cluster k, j particle) term per lane
             auto term = [&](int k, const float4 &pj, const float2 &aj, uint32_t jj, int tt) {
                 const uint32_t ii = (s * kSC + k) * M + II;
@@ -329,11 +352,45 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                         const float hji = 1.f / pj.w;
                         const float gi = spline_dw(r * hinv[k]) * hinv[k] * hinv[k] * hinv[k] * hinv[k];
                         const float gj = spline_dw(r * hji) * hji * hji * hji * hji;
-                        const float sc = aj.x * (ci[k] * gi + aj.y * gj) * 0.318309886183790672f * ir;
+                        const float bsym = (ci[k] * gi + aj.y * gj) * 0.318309886183790672f * ir;
+                        const float sc = aj.x * bsym;
                         // x_i - x_j = -dv
                         acc.bx[k] += sc * dv.x;
                         acc.by[k] += sc * dv.y;
                         acc.bz[k] += sc * dv.z;
+                        if constexpr (HL) {
+                            if (js) {  // a_j -= m_i (same bracket) (x_j - x_i) / r
+                                const float sj = smi[k * M + II] * bsym;
+                                jfx[tt] -= sj * dv.x;
+                                jfy[tt] -= sj * dv.y;
+                                jfz[tt] -= sj * dv.z;
+                            }
+                        }
+                    }
+                } else if constexpr (HL && KIND == PASS_LJ) {  // both particles, F_j = -F_ij
+                    const bool ini = d2 < ri2[k];
+                    const bool inj = js && d2 < pj.w;
+                    if (owner && ii != jj && (ini || inj)) {
+                        const float3 dv = pair_dx_acc<PER>(pi[k], pj, box);
+                        const float ir2 = 1.f / d2_of(dv);
+                        const float s2 = a.p1 * a.p1 * ir2;
+                        const float s6 = s2 * s2 * s2;
+                        const float c = 24.f * a.p0 * ir2 * s6 * (2.f * s6 - 1.f);
+                        if (ini) { acc.bx[k] -= c * dv.x; acc.by[k] -= c * dv.y; acc.bz[k] -= c * dv.z; }
+                        if (inj) { jfx[tt] += c * dv.x; jfy[tt] += c * dv.y; jfz[tt] += c * dv.z; }
+                    }
+                } else if constexpr (HL && KIND == PASS_LJC) {  // both particles, F_j = -F_ij
+                    const bool ini = d2 < ri2[k];
+                    const bool inj = js && d2 < pj.w;
+                    if (owner && ii != jj && (ini || inj)) {
+                        const float3 dv = pair_dx_acc<PER>(pi[k], pj, box);
+                        const float ir = rsqrtf(d2_of(dv));
+                        const float ir2 = ir * ir;
+                        const float s2 = a.p1 * a.p1 * ir2;
+                        const float s6 = s2 * s2 * s2;
+                        const float c = ir2 * (24.f * a.p0 * s6 * (2.f * s6 - 1.f) + ci[k] * aj.x * ir);
+                        if (ini) { acc.bx[k] -= c * dv.x; acc.by[k] -= c * dv.y; acc.bz[k] -= c * dv.z; }
+                        if (inj) { jfx[tt] += c * dv.x; jfy[tt] += c * dv.y; jfz[tt] += c * dv.z; }
                     }
                 } else if constexpr (KIND == PASS_LJ) {  // F_i += 24 eps (2 s^12/r^14 - s^6/r^8)(x_i - x_j)
                     if (owner && ii != jj && d2 < ri2[k]) {
@@ -366,7 +423,10 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                 // half list: an entry beyond the own clusters also feeds its j particles
                 js = HL && Je >= (s + 1) * kSC * RJ;
 #pragma unroll
-                for (int tt = 0; tt < NP; ++tt) { jsh[tt] = 0.f; jcn[tt] = 0u; }
+                for (int tt = 0; tt < NP; ++tt) {
+                    jsh[tt] = 0.f; jcn[tt] = 0u;
+                    jfx[tt] = 0.f; jfy[tt] = 0.f; jfz[tt] = 0.f;
+                }
                 if constexpr (SELF_IN_LOOP) {
                     const uint32_t rel = Je - s * kSC * RJ;  // j-cluster within the own ones
                     if (rel < (uint32_t)(kSC * RJ)) {
@@ -414,6 +474,21 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                                 for (int o = 1; o < M; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                                 if (owner && II == 0 && v != 0.f)
                                     atomicAdd(&a.hsum[jj], fixed_of(v * hscale));
+                            } else if constexpr (FORCE) {
+                                // FP64 adds: their order changes the sum by about
+                                // 1e-16 of it, below the FP32 rounding of the output
+                                float vx = jfx[tt], vy = jfy[tt], vz = jfz[tt];
+#pragma unroll
+                                for (int o = 1; o < M; o <<= 1) {
+                                    vx += __shfl_xor_sync(0xffffffffu, vx, o);
+                                    vy += __shfl_xor_sync(0xffffffffu, vy, o);
+                                    vz += __shfl_xor_sync(0xffffffffu, vz, o);
+                                }
+                                if (owner && II == 0 && (vx != 0.f || vy != 0.f || vz != 0.f)) {
+                                    atomicAdd(&a.hf[3 * (size_t)jj + 0], f64_of(vx));
+                                    atomicAdd(&a.hf[3 * (size_t)jj + 1], f64_of(vy));
+                                    atomicAdd(&a.hf[3 * (size_t)jj + 2], f64_of(vz));
+                                }
                             } else {
                                 uint32_t v = jcn[tt];
 #pragma unroll
@@ -462,6 +537,10 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                 atomicAdd(&a.hsum[i], fixed_of((acc.v[k] + self) * hscale));
             } else if constexpr (HL && KIND == PASS_COUNT) {
                 atomicAdd(&a.hcnt[i], acc.v[k] - (took_self ? 1u : 0u));
+            } else if constexpr (HL && FORCE) {
+                atomicAdd(&a.hf[3 * (size_t)i + 0], f64_of(acc.x[k]));
+                atomicAdd(&a.hf[3 * (size_t)i + 1], f64_of(acc.y[k]));
+                atomicAdd(&a.hf[3 * (size_t)i + 2], f64_of(acc.z[k]));
             } else if constexpr (KIND == PASS_DENSITY) {
                 const float self = took_self ? 0.f : a.aux[i].x;  // m_i w(0) = m_i
                 a.out0[o] = (acc.v[k] + self) * (0.318309886183790672f * hinv[k] * hinv[k] * hinv[k]);
@@ -505,17 +584,13 @@ static cudaError_t launch_k(const PassArgs &a, int M, int per, int grid, int thr
 {
     if (threads != 128 && threads != PS_THREADS) return cudaErrorInvalidValue;
     if (a.half) {
-        if constexpr (KIND == PASS_DENSITY || KIND == PASS_COUNT) {
-            switch (M * 100 + a.mj) {
-            case 404: launch_mk<4, 4, KIND, true>(a, per, grid, threads, s); break;
-            case 808: launch_mk<8, 8, KIND, true>(a, per, grid, threads, s); break;
-            case 1616: launch_mk<16, 16, KIND, true>(a, per, grid, threads, s); break;
-            default: return cudaErrorInvalidValue;
-            }
-            return cudaGetLastError();
-        } else {
-            return cudaErrorInvalidValue;
+        switch (M * 100 + a.mj) {
+        case 404: launch_mk<4, 4, KIND, true>(a, per, grid, threads, s); break;
+        case 808: launch_mk<8, 8, KIND, true>(a, per, grid, threads, s); break;
+        case 1616: launch_mk<16, 16, KIND, true>(a, per, grid, threads, s); break;
+        default: return cudaErrorInvalidValue;
         }
+        return cudaGetLastError();
     }
     switch (M * 100 + a.mj) {
     case 404: launch_mk<4, 4, KIND>(a, per, grid, threads, s); break;

@@ -2,7 +2,8 @@
 symmetric lists of Sec. II-D): records byte-exact against the oracle's half
 lists, densities within 1e-5 and counts exact against the oracle, repeatable
 bit for bit (the j shares are added as integers), in batches and CUDA graphs
-too; the force passes refuse them."""
+too; SPH pressure, LJ and LJ + Coulomb forces on both particles of a pair
+within 1e-5 (FP64 sums of the shares)."""
 import numpy as np
 import pytest
 
@@ -71,15 +72,110 @@ def test_half_list_uncompressed(cases):
     L.free()
 
 
-def test_half_list_refuses_forces_and_split_tiles(cases):
+FORCE_RTOL = 1e-5   # |a_gpu - a_64| / sum_j |f_ij|_64, per particle
+
+
+def _forces(out, o):
+    return np.stack([a.cpu().numpy()[o["perm"]] for a in out], 1)
+
+
+@pytest.mark.parametrize("cluster", [4, 8, 16])
+@pytest.mark.parametrize("name", ["evrard", "uniform"])
+def test_half_list_sph_pressure_force(cases, name, cluster):
+    """Both particles of a stored pair take the symmetric pressure force
+    (a_j gets -m_i/m_j of a_i's pair term); inputs as in the full-list test."""
     import torch
-    d, o, _ = cases["lj_fluid"]
+    d, o, (g_off, g_idx, p_off, p_idx) = cases[name]
+    n = len(o["xs"])
+    rho64 = orc.density(o["xs"], o["ys"], o["zs"], o["hs"], o["ms"], d["box"], g_off, g_idx,
+                        np.arange(n))
+    rho32 = rho64.astype(np.float32)
+    pres32 = (np.float32(2.0 / 3.0) * rho32 * np.float32(0.05)).astype(np.float32)
+    ax, ay, az, fa = orc.sph_force(o["xs"], o["ys"], o["zs"], o["hs"], o["ms"],
+                                   rho32.astype(np.float64), pres32.astype(np.float64), d["box"],
+                                   p_off, p_idx, np.arange(n))
+    L, t = gpu_build(d, cluster=cluster, half_list=1)
+    inv = np.empty(n, np.int64)
+    inv[o["perm"]] = np.arange(n)
+    rho_c = torch.from_numpy(rho32[inv]).cuda()
+    pres_c = torch.from_numpy(pres32[inv]).cuda()
+    out = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+    L.force_pass(nl.NL_FORCE_SPH_PRESSURE, *out, m=t["m"], rho=rho_c, pres=pres_c)
+    torch.cuda.synchronize()
+    got = _forces(out, o)
+    err = np.linalg.norm(got - np.stack([ax, ay, az], 1), axis=1) / np.maximum(fa, 1e-300)
+    assert err.max() <= FORCE_RTOL, err.max()
+    mom = (o["ms"][:, None].astype(np.float64) * got).sum(0)
+    assert np.abs(mom).max() <= 1e-5 * (o["ms"][:, None] * fa[:, None]).sum()
+    L.free()
+
+
+@pytest.mark.parametrize("cluster", [4, 8, 16])
+def test_half_list_lj_force(cases, cluster):
+    import torch
+    d, o, (g_off, g_idx, p_off, p_idx) = cases["lj_fluid"]
+    n = len(o["xs"])
+    fx, fy, fz, fa = orc.lj_force(o["xs"], o["ys"], o["zs"], d["box"], 1.0, 0.3, g_off, g_idx,
+                                  np.arange(n))
+    L, t = gpu_build(d, cluster=cluster, half_list=1)
+    out = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+    L.force_pass(nl.NL_FORCE_LJ, *out, eps=1.0, sigma=0.3)
+    torch.cuda.synchronize()
+    got = _forces(out, o)
+    err = np.linalg.norm(got - np.stack([fx, fy, fz], 1), axis=1) / fa
+    assert err.max() <= FORCE_RTOL, err.max()
+    assert np.abs(got.sum(0)).max() <= 1e-5 * fa.sum()
+    # a second pass: the FP64 sums round to the same FP32 values (up to rare
+    # ties of the rounding)
+    L.force_pass(nl.NL_FORCE_LJ, *out, eps=1.0, sigma=0.3)
+    torch.cuda.synchronize()
+    again = _forces(out, o)
+    assert np.mean(again != got) < 1e-3
+    assert (np.abs(again - got).max(1) / fa).max() <= 1e-6
+    L.free()
+
+
+def test_half_list_lj_coulomb_force_and_refresh():
+    """The Verlet-buffer workload on a half list: the pairs within rc before
+    and after a refresh of the positions, against the oracle."""
+    import torch
+    d = wl.lj_coulomb(12000, seed=138)
+    o = oracle_sorted(d)
+    q = np.asarray(d["q"], np.float32)[o["perm"]]
     n = len(o["xs"])
     L, t = gpu_build(d, half_list=1)
+    qd = torch.from_numpy(np.asarray(d["q"], np.float32)).cuda()
     out = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
-    with pytest.raises(nl.NLError):
-        L.force_pass(nl.NL_FORCE_LJ, *out, eps=1.0, sigma=0.3)
+    rng = np.random.default_rng(139)
+    pos = [o["xs"], o["ys"], o["zs"]]
+    for step in range(2):
+        if step:
+            v = rng.normal(size=(n, 3))
+            v *= (0.45 * (d["r_list"] - d["rc"]) * rng.random(n) / np.linalg.norm(v, axis=1))[:, None]
+            Lf = np.float32(d["L"])
+            new = {}
+            for a, k in enumerate("xyz"):
+                p = (np.asarray(d[k], np.float64) + v[:, a]).astype(np.float32)
+                p = np.where(p < 0, p + Lf, p)
+                new[k] = np.where(p >= Lf, p - Lf, p).astype(np.float32)
+            nd = {k: torch.from_numpy(new[k]).cuda() for k in "xyz"}
+            L.refresh_positions(nd["x"], nd["y"], nd["z"])
+            pos = [new[k][o["perm"]] for k in "xyz"]
+        L.force_pass(nl.NL_FORCE_LJ_COULOMB, *out, m=qd, eps=d["eps"], sigma=d["sigma"],
+                     rc=d["rc"], kc=d["kc"])
+        torch.cuda.synchronize()
+        got = _forces(out, o)
+        hr = np.full(n, np.float32(d["rc"]), np.float32)
+        g_off, g_idx = orc.gather_all(*pos, hr, d["box"], 1.0)
+        fx, fy, fz, fa = orc.ljc_force(*pos, d["box"], d["eps"], d["sigma"], q, d["kc"], g_off,
+                                       g_idx, np.arange(n))
+        err = np.linalg.norm(got - np.stack([fx, fy, fz], 1), axis=1) / fa
+        assert err.max() <= FORCE_RTOL, (step, err.max())
     L.free()
+
+
+def test_half_list_needs_whole_j_clusters(cases):
+    d, o, _ = cases["lj_fluid"]
     with pytest.raises(nl.NLError):
         gpu_build(d, cluster=8, j_cluster=4, half_list=1)
 
