@@ -211,7 +211,8 @@ nl_status nl_copy_records(const nl_list *nl, uint64_t *rec_off, uint8_t *bytes);
 
 /* End-to-end convenience call on HOST buffers: copies x, y, z, h, m (n
  * floats each, pageable or pinned host memory) into device buffers owned by
- * the list (m on a second stream of the list while the list is built),
+ * the list (z and h on a second stream of the list beside x and y, m on a
+ * third while the list is built),
  * rebuilds the list (as nl_rebuild), runs nl_density_pass and copies rho
  * (n floats) back to host memory.  Synchronises `stream`. */
 nl_status nl_density_from_host(nl_list *nl, const float *x, const float *y, const float *z,

@@ -151,8 +151,8 @@ struct nl_list {
     // device copies of host inputs for nl_density_from_host; the masses are
     // uploaded on a side stream while the list is built
     DevBuf hx, hy, hz, hh, hm, hrho;
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev_in = nullptr, ev_m = nullptr;
+    cudaStream_t side = nullptr, side2 = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_m = nullptr, ev_zh = nullptr;
     // h iteration state (sorted order)
     DevBuf it_hq, it_hlo, it_hhi, it_hs, it_counts, it_conv, it_aflag, it_alist, it_words, it_tmp;
 
@@ -192,9 +192,11 @@ struct nl_list {
             if (ev[i]) cudaEventDestroy(ev[i]);
         if (ev_in) cudaEventDestroy(ev_in);
         if (ev_m) cudaEventDestroy(ev_m);
+        if (ev_zh) cudaEventDestroy(ev_zh);
         if (side) cudaStreamDestroy(side);
-        ev_in = ev_m = nullptr;
-        side = nullptr;
+        if (side2) cudaStreamDestroy(side2);
+        ev_in = ev_m = ev_zh = nullptr;
+        side = side2 = nullptr;
         if (hst) cudaFreeHost(hst);
         hst = nullptr;
     }
@@ -1015,19 +1017,25 @@ nl_status nl_density_from_host(nl_list *nl, const float *x, const float *y, cons
     for (DevBuf *d : bufs) CK(d->ensure(b));
     if (!nl->side) {
         CK(cudaStreamCreateWithFlags(&nl->side, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&nl->side2, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&nl->ev_in, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&nl->ev_m, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&nl->ev_zh, cudaEventDisableTiming));
     }
-    // the side stream starts after earlier work on `stream` (which may still
-    // read the previous masses) and uploads m while the list is built
+    // the side streams start after earlier work on `stream` (which may still
+    // read the previous inputs): one uploads m while the list is built, the
+    // other z and h beside x and y on `stream`, so that the copies overlap
     CK(cudaEventRecord(nl->ev_in, s));
     CK(cudaStreamWaitEvent(nl->side, nl->ev_in, 0));
+    CK(cudaStreamWaitEvent(nl->side2, nl->ev_in, 0));
+    CK(cudaMemcpyAsync(nl->hz.p, z, b, cudaMemcpyHostToDevice, nl->side2));
+    CK(cudaMemcpyAsync(nl->hh.p, h, b, cudaMemcpyHostToDevice, nl->side2));
+    CK(cudaEventRecord(nl->ev_zh, nl->side2));
     CK(cudaMemcpyAsync(nl->hm.p, m, b, cudaMemcpyHostToDevice, nl->side));
     CK(cudaEventRecord(nl->ev_m, nl->side));
     CK(cudaMemcpyAsync(nl->hx.p, x, b, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(nl->hy.p, y, b, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(nl->hz.p, z, b, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(nl->hh.p, h, b, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamWaitEvent(s, nl->ev_zh, 0));
     nl_status st = nl_rebuild(nl, nl->hx.as<float>(), nl->hy.as<float>(), nl->hz.as<float>(),
                               nl->hh.as<float>(), n, box, p, stream);
     CK(cudaStreamWaitEvent(s, nl->ev_m, 0));  // also on failure: m stays owned by us
