@@ -165,9 +165,11 @@ __device__ __forceinline__ double f64_of(float x)
 // of the super-cluster's own clusters are complete as they are (both orders
 // of every pair are listed); an entry J beyond them is a pair of clusters
 // listed only here, so its pairs also add to the j particles: d2 < rj^2 gives
-// particle j the term with its own h.  Those j shares are summed over the
-// entry's i particles in a fixed shuffle order and added as integers (fixed
-// point for density), so the result does not depend on the order of the adds.
+// particle j the term with its own h (density, counts, LJ; SPH pairs share
+// one symmetric predicate).  Those j shares are summed over the entry's i
+// particles in a fixed shuffle order and added as integers (fixed point for
+// density), so the result does not depend on the order of the adds; forces
+// are added in FP64 and rounded once to FP32 by the finishing kernel.
 template <int M, int MJ, bool PER, int KIND, bool HL>
 __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pass(PassArgs a)
 {
@@ -308,7 +310,8 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
             }
             __syncwarp();
             // half list: the current entry feeds its j particles too (js), with
-            // the shares of this lane's j particles in jsh / jcn
+            // the shares of this lane's j particles in jsh (density), jcn
+            // (counts) or jfx, jfy, jfz (forces)
             bool js = false;
             float jsh[NP] = {};
             uint32_t jcn[NP] = {};
