@@ -54,3 +54,34 @@ def test_product_does_not_import_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "nl_oracle" not in txt, f
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Sizes and field offsets of the ctypes structs equal those of the C
+    structs of include/nl.h, measured by a C program compiled with gcc."""
+    import ctypes as C
+
+    from paper_2602_19873_gb300 import nl
+    structs = {"nl_box": nl.nl_box, "nl_params": nl.nl_params, "nl_sizes": nl.nl_sizes,
+               "nl_hiter_info": nl.nl_hiter_info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "nl.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (name, name))
+        for field, _ in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, field, name, field))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            a, b, c = line.split()
+            got[(a, b)] = int(c)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == C.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
