@@ -73,17 +73,21 @@ def test_graph_replay_matches_normal_build():
         L.free()
 
 
-def test_autotuner_returns_a_valid_faster_choice():
+@pytest.mark.parametrize("half", [0, 1])
+def test_autotuner_returns_a_valid_faster_choice(half):
     import torch
     stream = torch.cuda.Stream()
     systems, offs, dev = _batch(511, n_systems=6, log_n=(3.0, 3.8))
     boxes = [d["box"] for d in systems]
-    base = nl.make_params(key=1, cluster=8, support=2.0)
+    base = nl.make_params(key=1, cluster=8, support=2.0, half_list=half)
     with torch.cuda.stream(stream):
         best, ms = nl.autotune_batch(dev["x"], dev["y"], dev["z"], dev["h"], dev["m"], offs, boxes,
                                      base, reps=1, stream=stream)
         assert best.cluster in (4, 8, 16) and best.threads_per_block in (128, 256)
         assert best.j_cluster in (best.cluster, best.cluster // 2) and best.j_cluster >= 4
+        assert best.half_list == half
+        if half:  # half lists need j-clusters of the i-cluster size
+            assert best.j_cluster == best.cluster
         assert best.blocks_per_sm in (2, 3, 4) and ms > 0
         # the tuned parameters give the same densities within the FP32 tolerance
         a = _normal_density(dev, offs, boxes, base, stream)
