@@ -22,7 +22,7 @@ __all__ = [
     "sort", "octree", "brute_neighbors", "gather_all", "symmetrize", "cluster_lists", "half_lists",
     "encode_block", "encode_record", "decode_record", "record_bytes", "stream_nibbles",
     "w", "dw", "W", "density", "sph_force", "lj_force", "lj_energy", "ljc_force", "ljc_energy",
-    "gather_counts_brute",
+    "nearest", "gather_counts_brute",
     "pred", "dist2", "dist2_row", "num_threads", "pipeline_lists", "mlp_nparams",
     "mlp_forward", "mlp_loss_grad",
 ]
@@ -103,6 +103,7 @@ def lib():
                                          P, P, P, P, P]),
                 "orc_ljc_energy": (C.c_double, [P, P, P, P, C.c_double, C.c_double, P,
                                                 C.c_double, P]),
+                "orc_nearest": (None, [P, P, P, P, P, P]),
                 "orc_gather_counts_brute": (None, [I64, P, P, P, P, P, F32, I64, P, P]),
                 "orc_dist2_row": (None, [I64, P, P, P, P, I64, P]),
                 "orc_num_threads": (C.c_int, []),
@@ -436,6 +437,20 @@ def ljc_energy(xs, ys, zs, box, eps, sigma, q, kc, off, idx):
                                     None if qq is None else _p(qq), float(kc), h)
     finally:
         lib().orc_csr_free(h)
+
+
+def nearest(xs, ys, zs, box, off, idx):
+    """FP64 distance of every particle (rows 0..n-1) to its nearest member of
+    its interaction set (off, idx); +inf for an empty set."""
+    xs, ys, zs = (_f32(a) for a in (xs, ys, zs))
+    h, keep = _csr_make(off, idx)
+    out = np.zeros(len(off) - 1)
+    b = _box(box)
+    try:
+        lib().orc_nearest(_p(xs), _p(ys), _p(zs), C.byref(b), h, _p(out))
+    finally:
+        lib().orc_csr_free(h)
+    return out
 
 
 def gather_counts_brute(xs, ys, zs, hs, box, support, queries):

@@ -1108,6 +1108,26 @@ double orc_ljc_energy(const float *xs, const float *ys, const float *zs, const o
     return e;
 }
 
+/* Distance from particle k to its nearest member of the interaction set
+ * P_k (the pair function of Sec. II-D with a minimum reduction), FP64 from
+ * the FP32 coordinates with the canonical periodic wrap; +inf for an empty
+ * set.  Rows are particles 0..n-1. */
+void orc_nearest(const float *xs, const float *ys, const float *zs, const orc_box *b,
+                 const orc_csr *P, double *out)
+{
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < P->n; ++i) {
+        double best = INFINITY;
+        for (int64_t t = P->off[i]; t < P->off[i + 1]; ++t) {
+            int64_t j = P->idx[t];
+            double dx = dx64(xs, i, j, b, 0), dy = dx64(ys, i, j, b, 1), dz = dx64(zs, i, j, b, 2);
+            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            if (r < best) best = r;
+        }
+        out[i] = best;
+    }
+}
+
 /* Number of predicate evaluations a cluster list implies (masked tiles x
  * cluster^2) and the number of particles-in-range pairs it serves. */
 void orc_cluster_overhead(const orc_clist *c, int cluster, int64_t *computed)

@@ -218,3 +218,32 @@ def test_half_lists_store_every_cluster_pair_once(orc, name, M):
         assert np.all(np.diff(Js) > 0) and np.all(Js >= 8 * s)
         assert np.all(m[o[s]:o[s + 1]] != 0)
     assert len(J) < len(orc.cluster_lists(n, M, p_off, p_idx, np.arange(n), sc)[1])
+
+
+@pytest.mark.parametrize("name", ["uniform", "plummer"])
+def test_nearest_distance_against_kd_tree(orc, name):
+    """The nearest member of each gather set against scipy's k-d tree (its
+    periodic box for the cube): the nearest other particle, if it lies inside
+    the radius, else +inf (radius ties within 1e-6 skipped)."""
+    from scipy.spatial import cKDTree
+    d = _small(name, 3000)
+    xs, ys, zs, hs0, ms = _sorted(orc, d)
+    # every third particle with a radius too small to hold a neighbor
+    hs = np.where(np.arange(len(xs)) % 3 == 0, hs0 * np.float32(0.02), hs0).astype(np.float32)
+    g_off, g_idx = orc.gather_all(xs, ys, zs, hs, d["box"], 2.0)
+    got = orc.nearest(xs, ys, zs, d["box"], g_off, g_idx)
+    P = np.stack([xs, ys, zs], 1).astype(np.float64)
+    if np.any(d["box"]["periodic"]):
+        L = float(np.float32(d["box"]["hi"][0]) - np.float32(d["box"]["lo"][0]))
+        tree = cKDTree(P - np.asarray(d["box"]["lo"], np.float64), boxsize=L)
+        dist, _ = tree.query(P - np.asarray(d["box"]["lo"], np.float64), k=2)
+    else:
+        tree = cKDTree(P)
+        dist, _ = tree.query(P, k=2)
+    d1 = dist[:, 1]
+    r = 2.0 * hs.astype(np.float64)
+    clear = np.abs(d1 - r) > 1e-6 * r
+    inside = clear & (d1 < r)
+    assert np.allclose(got[inside], d1[inside], rtol=1e-12, atol=0)
+    assert np.all(np.isinf(got[clear & (d1 >= r)]))
+    assert inside.sum() > 0.5 * len(xs) and (clear & (d1 >= r)).sum() > 0.2 * len(xs)
