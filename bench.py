@@ -328,6 +328,16 @@ def run_native(args):
     stages = {k: v / args.steps for k, v in stage_acc.items()}
     sizes = L.sizes()
 
+    # the minimum-reduction pass on the same list (nearest gather neighbor)
+    dist = torch.empty(n, dtype=torch.float32, device="cuda")
+    L.nearest_distance(dist, stream)
+    t0.record(stream)
+    for _ in range(args.steps):
+        L.nearest_distance(dist, stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    near_ms = max_over_ranks(t0.elapsed_time(t1) / args.steps, ws, "cuda")
+
     # the other storage of the same list (full <-> half), timed the same way
     alt_kind = "full" if args.list == "half" else "half"
     alt_params = nl.make_params(key=d["kind"], cluster=M, support=d["support"], compress=1,
@@ -436,6 +446,7 @@ def run_native(args):
         "gpu_launches": None,
         "clocks": clk,
         "other_list": alt,
+        "nearest_distance_pass_ms": near_ms,
     }
     out["gpu_launches"] = args.steps * launches_per_step(sizes, False,
                                                          half_list=args.list == "half")

@@ -163,6 +163,14 @@ nl_status nl_force_pass(const nl_list *nl, int32_t kind, const float *params, co
  * order, n device uint32.  Does not synchronise. */
 nl_status nl_neighbor_counts(const nl_list *nl, uint32_t *counts, void *stream);
 
+/* Distance from every particle to its nearest gather neighbor (j != i with
+ * d2 < ri^2): the pair function of Sec. II-D with a minimum reduction.  dist:
+ * n device floats, caller order; +inf for a particle without a neighbor.
+ * FP32 sqrt of the smallest squared distance (the accurate wrapped difference
+ * on periodic axes).  A minimum does not depend on the order of its
+ * operands, so full and half lists give the same bits.  Does not synchronise. */
+nl_status nl_nearest_distance(const nl_list *nl, float *dist, void *stream);
+
 /* List reuse across steps (the Verlet buffer of Sec. III-B and its
  * production remark: a list built at radius r_list serves an interaction
  * cutoff rc < r_list while particles move less than (r_list - rc)/2).

@@ -1754,6 +1754,25 @@ nl_status nl_neighbor_counts(const nl_list *cnl, uint32_t *counts, void *stream)
     return NL_OK;
 }
 
+nl_status nl_nearest_distance(const nl_list *cnl, float *dist, void *stream)
+{
+    nl_status st = check_list(cnl);
+    if (st != NL_OK) return st;
+    if (!dist) return fail(NL_ERR_ARG, "NULL dist");
+    nl_list *nl = const_cast<nl_list *>(cnl);
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool half = nl->p.half_list != 0;
+    if (half) {
+        CK(nl->hcnt.ensure((size_t)nl->npad * 4));
+        CK(launch_fill(nl->hcnt.as<float>(), nl->npad, INFINITY, s));
+    }
+    PassArgs a = pass_args(nl);
+    a.out0 = dist;
+    CK(run_pass(nl, a, PASS_MIN, s));
+    if (half) CK(launch_half_finish(a, PASS_MIN, nl->npad, s));
+    return NL_OK;
+}
+
 nl_status nl_get_sizes(const nl_list *nl, nl_sizes *out)
 {
     nl_status st = check_list(nl);

@@ -574,7 +574,7 @@ cudaError_t launch_fill_keys(uint64_t *keys, uint32_t cap, const unsigned long l
 cudaError_t exclusive_scan_u32(const uint32_t *cnt, uint32_t *seg_off, uint32_t n, uint32_t *bsum,
                                uint32_t *total, cudaStream_t s);
 
-enum PassKind { PASS_DENSITY = 0, PASS_COUNT = 1, PASS_SPH = 2, PASS_LJ = 3, PASS_LJC = 4 };
+enum PassKind { PASS_DENSITY = 0, PASS_COUNT = 1, PASS_SPH = 2, PASS_LJ = 3, PASS_LJC = 4, PASS_MIN = 5 };
 struct PassArgs {
     const float4 *pos;
     const uint8_t *list;
@@ -602,7 +602,7 @@ struct PassArgs {
     // finishing kernel turns them into the outputs.
     int half;
     unsigned long long *hsum;   // density: per sorted particle, sum m_j w in units of 2^-scale
-    uint32_t *hcnt;             // counts: per sorted particle
+    uint32_t *hcnt;             // counts (or nearest squared distance, float bits): per sorted particle
     double *hf;                 // forces: per sorted particle, 3 FP64 sums
 };
 

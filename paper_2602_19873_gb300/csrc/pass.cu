@@ -15,6 +15,8 @@ cudaError_t launch_pass_lj(const PassArgs &a, int M, int per, int grid, int thre
                           cudaStream_t s);
 cudaError_t launch_pass_ljc(const PassArgs &a, int M, int per, int grid, int threads,
                           cudaStream_t s);
+cudaError_t launch_pass_min(const PassArgs &a, int M, int per, int grid, int threads,
+                          cudaStream_t s);
 
 cudaError_t launch_pass(const PassArgs &a, int kind, int M, int any_periodic, int num_sms,
                         cudaStream_t s, int threads, int blocks_per_sm)
@@ -29,6 +31,7 @@ cudaError_t launch_pass(const PassArgs &a, int kind, int M, int any_periodic, in
     case PASS_SPH: return launch_pass_sph(a, M, any_periodic, grid, tpb, s);
     case PASS_LJ: return launch_pass_lj(a, M, any_periodic, grid, tpb, s);
     case PASS_LJC: return launch_pass_ljc(a, M, any_periodic, grid, tpb, s);
+    case PASS_MIN: return launch_pass_min(a, M, any_periodic, grid, tpb, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -82,6 +85,10 @@ __global__ void __launch_bounds__(256) k_half_finish(PassArgs a, int kind, uint3
         a.outc[o] = a.hcnt[k];
         return;
     }
+    if (kind == PASS_MIN) {  // +inf bits when no neighbor was found
+        a.out0[o] = sqrtf(__uint_as_float(a.hcnt[k]));
+        return;
+    }
     if (kind != PASS_DENSITY) {  // forces: the FP64 sums rounded once to FP32
         a.out0[o] = (float)a.hf[3 * (size_t)k + 0];
         a.out1[o] = (float)a.hf[3 * (size_t)k + 1];
@@ -97,7 +104,7 @@ __global__ void __launch_bounds__(256) k_half_finish(PassArgs a, int kind, uint3
 
 cudaError_t launch_half_finish(const PassArgs &a, int kind, uint32_t npad, cudaStream_t s)
 {
-    if (kind < PASS_DENSITY || kind > PASS_LJC) return cudaErrorInvalidValue;
+    if (kind < PASS_DENSITY || kind > PASS_MIN) return cudaErrorInvalidValue;
     k_half_finish<<<(npad + 255) / 256, 256, 0, s>>>(a, kind, npad);
     return cudaGetLastError();
 }

@@ -78,6 +78,8 @@ template <>
 struct Acc<PASS_LJ> { float x[kSC], y[kSC], z[kSC], bx[kSC], by[kSC], bz[kSC]; };
 template <>
 struct Acc<PASS_LJC> { float x[kSC], y[kSC], z[kSC], bx[kSC], by[kSC], bz[kSC]; };
+template <>
+struct Acc<PASS_MIN> { float v[kSC]; };  // smallest squared distance
 
 template <int KIND>
 __device__ __forceinline__ void acc_begin_block(Acc<KIND> &acc)
@@ -127,7 +129,8 @@ constexpr size_t pass_smem_per_warp()
 template <int KIND, bool HL>
 constexpr int ps_min_blocks()
 {
-    return (HL && KIND == PASS_DENSITY) ? 3 : (KIND == PASS_DENSITY || KIND == PASS_COUNT) ? 4 : 2;
+    return (HL && KIND == PASS_DENSITY) ? 3
+           : (KIND == PASS_DENSITY || KIND == PASS_COUNT || KIND == PASS_MIN) ? 4 : 2;
 }
 
 // Nearest integer of x (ties away from zero) as a 64-bit two's complement
@@ -236,6 +239,8 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                 acc.v[k] = 0.f; acc.c[k] = 0.f;
             } else if constexpr (KIND == PASS_COUNT) {
                 acc.v[k] = 0;
+            } else if constexpr (KIND == PASS_MIN) {
+                acc.v[k] = INFINITY;
             } else {
                 acc.x[k] = 0.f; acc.y[k] = 0.f; acc.z[k] = 0.f;
             }
@@ -287,7 +292,7 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                 const uint32_t e = min(q / MJ, 31u);
                 const uint32_t src = __shfl_sync(0xffffffffu, J, e) * MJ + (q % MJ);
                 if (q < nb * MJ) {
-                    if constexpr (HL && (KIND == PASS_DENSITY || KIND == PASS_COUNT)) {
+                    if constexpr (HL && (KIND == PASS_DENSITY || KIND == PASS_COUNT || KIND == PASS_MIN)) {
                         // half list: w holds rj^2, and the density input's
                         // second word 1/h_j (dummies: rj = 0, never a pair)
                         const float4 p = a.pos[src];
@@ -316,6 +321,9 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
             float jsh[NP] = {};
             uint32_t jcn[NP] = {};
             float jfx[NP] = {}, jfy[NP] = {}, jfz[NP] = {};
+            float jmn[NP];
+#pragma unroll
+            for (int tt = 0; tt < NP; ++tt) jmn[tt] = INFINITY;
             // one (i-cluster k, j particle) term per lane
             auto term = [&](int k, const float4 &pj, const float2 &aj, uint32_t jj, int tt) {
                 const uint32_t ii = (s * kSC + k) * M + II;
@@ -343,6 +351,19 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                     }
                 } else if constexpr (KIND == PASS_COUNT) {
                     if (owner && d2 < ri2[k]) acc.v[k] += 1u;  // i = j included (see selfseen)
+                } else if constexpr (HL && KIND == PASS_MIN) {
+                    const bool ini = d2 < ri2[k];
+                    const bool inj = js && d2 < pj.w;
+                    if (owner && ii != jj && (ini || inj)) {
+                        const float e2 = PER ? d2_of(pair_dx_acc<PER>(pi[k], pj, box)) : d2;
+                        if (ini) acc.v[k] = fminf(acc.v[k], e2);
+                        if (inj) jmn[tt] = fminf(jmn[tt], e2);
+                    }
+                } else if constexpr (KIND == PASS_MIN) {  // nearest gather neighbor
+                    if (owner && ii != jj && d2 < ri2[k]) {
+                        const float e2 = PER ? d2_of(pair_dx_acc<PER>(pi[k], pj, box)) : d2;
+                        acc.v[k] = fminf(acc.v[k], e2);
+                    }
                 } else if constexpr (KIND == PASS_SPH) {
                     const float rj = __fmul_rn(a.support, pj.w);
                     const float rr = fmaxf(ri[k], rj);
@@ -429,6 +450,7 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                 for (int tt = 0; tt < NP; ++tt) {
                     jsh[tt] = 0.f; jcn[tt] = 0u;
                     jfx[tt] = 0.f; jfy[tt] = 0.f; jfz[tt] = 0.f;
+                    jmn[tt] = INFINITY;
                 }
                 if constexpr (SELF_IN_LOOP) {
                     const uint32_t rel = Je - s * kSC * RJ;  // j-cluster within the own ones
@@ -492,6 +514,13 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                                     atomicAdd(&a.hf[3 * (size_t)jj + 1], f64_of(vy));
                                     atomicAdd(&a.hf[3 * (size_t)jj + 2], f64_of(vz));
                                 }
+                            } else if constexpr (KIND == PASS_MIN) {
+                                // a minimum is the same in any order: integer
+                                // minimum of the bits of non-negative floats
+                                float v = jmn[tt];
+#pragma unroll
+                                for (int o = 1; o < M; o <<= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+                                if (owner && II == 0 && v < INFINITY) atomicMin(&a.hcnt[jj], __float_as_uint(v));
                             } else {
                                 uint32_t v = jcn[tt];
 #pragma unroll
@@ -515,6 +544,8 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                     acc.v[k] += __shfl_xor_sync(0xffffffffu, acc.v[k], o);
                 } else if constexpr (KIND == PASS_COUNT) {
                     acc.v[k] += __shfl_xor_sync(0xffffffffu, acc.v[k], o);
+                } else if constexpr (KIND == PASS_MIN) {
+                    acc.v[k] = fminf(acc.v[k], __shfl_xor_sync(0xffffffffu, acc.v[k], o));
                 } else {
                     acc.x[k] += __shfl_xor_sync(0xffffffffu, acc.x[k], o);
                     acc.y[k] += __shfl_xor_sync(0xffffffffu, acc.y[k], o);
@@ -549,6 +580,10 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                 a.out0[o] = (acc.v[k] + self) * (0.318309886183790672f * hinv[k] * hinv[k] * hinv[k]);
             } else if constexpr (KIND == PASS_COUNT) {
                 a.outc[o] = acc.v[k] - (took_self ? 1u : 0u);
+            } else if constexpr (HL && KIND == PASS_MIN) {
+                if (acc.v[k] < INFINITY) atomicMin(&a.hcnt[i], __float_as_uint(acc.v[k]));
+            } else if constexpr (KIND == PASS_MIN) {
+                a.out0[o] = sqrtf(acc.v[k]);  // +inf without a neighbor
             } else if constexpr (KIND == PASS_SPH) {
                 a.out0[o] = acc.x[k];
                 a.out1[o] = acc.y[k];

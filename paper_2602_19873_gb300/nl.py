@@ -60,6 +60,7 @@ _SIGS = {
     "nl_neighbor_counts": (C.c_int, [P, P, P]),
     "nl_force_pass": (C.c_int, [P, C.c_int32, P, P, P, P, P, P, P, P]),
     "nl_refresh_positions": (C.c_int, [P, P, P, P, P, P]),
+    "nl_nearest_distance": (C.c_int, [P, P, P]),
     "nl_free": (C.c_int, [P]),
     "nl_get_sizes": (C.c_int, [P, P]),
     "nl_copy_sorted": (C.c_int, [P, P, P]),
@@ -409,6 +410,9 @@ class NeighborList:
 
     def neighbor_counts(self, counts, stream=None):
         _check(load().nl_neighbor_counts(self.handle, _ptr(counts), _stream(stream)))
+
+    def nearest_distance(self, dist, stream=None):
+        _check(load().nl_nearest_distance(self.handle, _ptr(dist), _stream(stream)))
 
     def refresh_positions(self, x, y, z, max_disp=None, stream=None):
         _check(load().nl_refresh_positions(self.handle, _ptr(x), _ptr(y), _ptr(z), _ptr(max_disp),
