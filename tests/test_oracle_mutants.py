@@ -4,7 +4,6 @@ pin, and must make that pin fail.  This shows the pins catch the mistakes a
 restatement of the paper is likely to make (a sign, a dropped term, an index,
 an exponent, an offset)."""
 import contextlib
-import os
 import subprocess
 
 import pytest
@@ -99,3 +98,19 @@ def test_planted_mistake_fails_its_pin(tmp_path, orc, name, old, new, pin):
             pin(orc)
     # and again after the oracle is back
     pin(orc)
+
+
+def test_planted_mistake_in_the_half_list_filter(orc, monkeypatch):
+    """The half-list definition with the super-cluster's own first cluster
+    left out fails the half-list pin."""
+    import inspect
+
+    import oracle
+    src = inspect.getsource(orc_api.half_lists)
+    assert src.count("Js >= 8 * s") == 1
+    ns = dict(orc_api.__dict__)
+    exec(compile(src.replace("Js >= 8 * s", "Js > 8 * s"), "half_lists_mutant", "exec"), ns)
+    tneigh.test_half_lists_store_every_cluster_pair_once(orc, "uniform", 8)
+    monkeypatch.setattr(oracle, "half_lists", ns["half_lists"])
+    with pytest.raises(AssertionError):
+        tneigh.test_half_lists_store_every_cluster_pair_once(orc, "uniform", 8)
