@@ -11,7 +11,10 @@
  *   (Sec. II-A) -> cluster-pair search against bounding boxes inflated by the
  *   largest radius -> one record per super-cluster: count, 8-bit masks, and
  *   the nibble-compressed j-cluster indices (Sec. II-A/B/C) -> decode inside
- *   the SPH density / force and Lennard-Jones passes (Sec. II-A, II-D).
+ *   the SPH density / force, Lennard-Jones (+ Coulomb), neighbor-count and
+ *   nearest-neighbor passes (Sec. II-A, II-D).  Lists are stored in full or
+ *   with every pair of clusters of two super-clusters once (half lists,
+ *   Sec. II-D), and can take new positions for several steps (Sec. III-B).
  *
  * Conventions shared by every entry point:
  *  - Particle arrays are DEVICE pointers in the caller's order, borrowed for
@@ -27,7 +30,7 @@
  *      dx = xj - xi, wrapped once by +-L on a periodic axis when |dx| > L/2,
  *      d2 = (dx*dx + dy*dy) + dz*dz, r = support*h,
  *      symmetric pair (the list): i != j and d2 < max(ri, rj)^2
- *      gather pair (density, counts): i != j and d2 < ri^2.
+ *      gather pair (density, counts, LJ, nearest): i != j and d2 < ri^2.
  */
 #ifndef NL_H
 #define NL_H

@@ -1,6 +1,7 @@
 // Neighborhood passes over the compressed list (Sec. II-A: loop in parallel
 // over super-clusters, decode the list iteratively as needed, process each
-// cluster-cluster interaction; Sec. II-D: pure pair function + sum).
+// cluster-cluster interaction; Sec. II-D: pure pair function + a sum or a
+// minimum).
 //
 // One warp per super-cluster (atomic work counter, persistent grid).  The
 // warp decodes 32 differences at a time: the block mask is read at its
