@@ -343,9 +343,8 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
                     // exact FP32 test of the candidate M x MJ tiles
                     uint32_t mask = 0;
                     ttests += __popc(cm);
-#pragma unroll
-                    for (int k = 0; k < kSC; ++k) {
-                        if (!((cm >> k) & 1u)) continue;
+                    for (uint32_t bits = cm; bits; bits &= bits - 1u) {
+                        const int k = __ffs(bits) - 1;  // candidate tiles only, ascending
                         const uint32_t ii = base + k * M + II;
                         const float4 pik = S.ip[k * M + II];
 #pragma unroll
