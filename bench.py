@@ -37,9 +37,9 @@ ALGO_BYTES_PER_PARTICLE = 145    # keygen 20 + sort 24 + permute 49 + octree 2 +
 # cluster-box round then exact tile tests), scaled by the particle count (the
 # traffic grows with the particles).  "full": the half search with transposed
 # tuples for full lists, 45.1 MB + 12.7 MB; "half": the same walk storing half
-# lists, 44.9 MB + 0.9 MB.  Valid for those kernel versions only; a list kind
-# without a capture reports no traffic.
-SEARCH_DRAM_BYTES_PER_PARTICLE = {"full": 57.8e6 / 2097152, "half": 45.8e6 / 2097152}
+# lists (tile tests over the set mask bits), 44.9 MB + 0.7 MB.  Valid for those
+# kernel versions only; a list kind without a capture reports no traffic.
+SEARCH_DRAM_BYTES_PER_PARTICLE = {"full": 57.8e6 / 2097152, "half": 45.5e6 / 2097152}
 
 
 def peaks():
