@@ -276,9 +276,10 @@ nl_status nl_iterate_h(nl_list *nl, const float *x, const float *y, const float 
 
 /* Allocation-free SFC ordering.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory where they
- * need the order -- inside a CUDA stream capture, in a latency-critical loop
- * that cannot afford cudaMalloc's implicit synchronisation, or under a host
- * framework that owns all device memory.  It computes exactly what nl_build
+ * need the order: a latency-critical simulation loop that cannot afford
+ * cudaMalloc's implicit device synchronisation, or a host framework that owns
+ * all device memory through its own pool and forbids driver allocations by
+ * the libraries it calls.  It computes exactly what nl_build
  * computes for its first two steps: keys[k] = the k-th smallest 63-bit SFC
  * key (NL_KEY_MORTON or NL_KEY_HILBERT) and perm[k] = the caller index of
  * that particle (stable: equal keys keep caller order), for n <= 1048576.
@@ -286,8 +287,9 @@ nl_status nl_iterate_h(nl_list *nl, const float *x, const float *y, const float 
  * keys (n uint64) and perm (n uint32) are device arrays owned by the caller.
  * Scratch comes from a fixed device array inside the library (about
  * 12.3 MB, held by every GPU that loads the library until exit); nothing is
- * allocated.  The first call on a device looks up that array's address, so
- * make it once before any stream capture.  Concurrent calls that overlap on
+ * allocated.  The first call made with a device current looks up that
+ * array's address on that device (cudaGetSymbolAddress); make that first call
+ * before any stream capture begins.  Concurrent calls that overlap on
  * the GPU share the array and race; serialise them.  n > NL_NOALLOC_MAX_N
  * returns NL_ERR_ARG.  Synchronises `stream` (one status read). */
 #define NL_NOALLOC_MAX_N 1048576

@@ -635,13 +635,8 @@ __global__ void k_mlp_reduce_adam(int nslots, const float *__restrict__ partial,
 cudaError_t mlp_predict(int64_t n, const float *X, const float *P, float *out, int num_sms,
                         cudaStream_t s)
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_mlp_predict, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)mlp_predict_smem());
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    cudaError_t e = set_max_dynamic_smem((const void *)k_mlp_predict, mlp_predict_smem());
+    if (e != cudaSuccess) return e;
     const int64_t tiles = (n + 15) / 16;
     const int grid = (int)min_i64((tiles + 3) / 4, (int64_t)num_sms * 8);
     if (grid > 0) k_mlp_predict<<<grid, 128, mlp_predict_smem(), s>>>(n, X, P, out);
@@ -653,13 +648,8 @@ cudaError_t mlp_train_step(int64_t nb, const int64_t *idx, const float *X, const
                            int slots, float *grad, float *loss, int adam, float lr, int step,
                            float inv_n, cudaStream_t s)
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)mlp_train_smem());
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    cudaError_t e = set_max_dynamic_smem((const void *)k_mlp_train, mlp_train_smem());
+    if (e != cudaSuccess) return e;
     const int grid = (int)min_i64((nb + 63) / 64, slots);
     if (grid <= 0) return cudaSuccess;
     k_mlp_train<<<grid, 128, mlp_train_smem(), s>>>(nb, idx, X, Y, W, P, inv_n, partial, loss);

@@ -422,6 +422,13 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *sh, ui
 // ---------------------------------------------------------------------------
 // Host-side launchers implemented in the .cu files
 // ---------------------------------------------------------------------------
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current
+// device.  The attribute belongs to the device's context, so it is recorded
+// per (kernel, device) under a lock: a second device, or several host threads
+// on first use, each get it set before their launch.  Returns the error of
+// cudaFuncSetAttribute (or of cudaGetDevice).
+cudaError_t set_max_dynamic_smem(const void *func, size_t bytes);
+
 cudaError_t launch_keys(int64_t n, const float *x, const float *y, const float *z, const float *h,
                         const DevBox &box, float support, int kind, uint64_t *keys, uint32_t *vals,
                         Status *st, cudaStream_t s);

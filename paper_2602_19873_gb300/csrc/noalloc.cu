@@ -4,17 +4,17 @@
 // words) taken from one file-scope device array instead of cudaMalloc.
 //
 // Why: some callers cannot allocate device memory at the point where they
-// need an SFC order -- code running between cudaStreamBeginCapture and
-// EndCapture, where a cudaMalloc would break the capture; latency-critical
-// simulation loops where cudaMalloc's implicit device synchronisation is not
-// acceptable; and host frameworks that own all device memory through their
-// own pool and forbid driver allocations.  They pass their own output arrays
-// and get the same keys and permutation as nl_build computes.
+// need an SFC order -- latency-critical simulation loops where cudaMalloc's
+// implicit device synchronisation is not acceptable, and host frameworks that
+// own all device memory through their own pool and forbid driver allocations
+// by the libraries they call.  They pass their own output arrays and get the
+// same keys and permutation as nl_build computes.
 //
 // The array is part of this library's device image, so every GPU that loads
 // the library holds it (about 12.3 MB) until the process exits.  Its device
 // address is looked up once per device with cudaGetSymbolAddress, on the
-// first call made with that device current.  All calls share the one array:
+// first call made with that device current; that first call belongs before
+// any stream capture begins.  All calls share the one array:
 // the status words are cleared at the start of each call, and calls that
 // overlap on the GPU (different streams, or several host threads) race on it.
 #include <mutex>

@@ -599,23 +599,20 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
 }
 
 template <int M, int MJ, int KIND, bool HL = false>
-static void launch_mk(const PassArgs &a, int per, int grid, int threads, cudaStream_t s)
+static cudaError_t launch_mk(const PassArgs &a, int per, int grid, int threads, cudaStream_t s)
 {
     // the attribute is set for the largest block so that any shape fits
     const size_t smax = (size_t)(PS_THREADS / 32) * pass_smem_per_warp<MJ, KIND, HL>();
     const size_t smem = (size_t)(threads / 32) * pass_smem_per_warp<MJ, KIND, HL>();
-    static bool attr[2] = {false, false};
-    if (!attr[per ? 1 : 0]) {
-        if (per)
-            cudaFuncSetAttribute(k_pass<M, MJ, true, KIND, HL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
-        else
-            cudaFuncSetAttribute(k_pass<M, MJ, false, KIND, HL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
-        attr[per ? 1 : 0] = true;
-    }
+    const void *fn = per ? (const void *)k_pass<M, MJ, true, KIND, HL>
+                         : (const void *)k_pass<M, MJ, false, KIND, HL>;
+    cudaError_t e = set_max_dynamic_smem(fn, smax);
+    if (e != cudaSuccess) return e;
     if (per)
         k_pass<M, MJ, true, KIND, HL><<<grid, threads, smem, s>>>(a);
     else
         k_pass<M, MJ, false, KIND, HL><<<grid, threads, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 template <int KIND>
@@ -624,22 +621,20 @@ static cudaError_t launch_k(const PassArgs &a, int M, int per, int grid, int thr
     if (threads != 128 && threads != PS_THREADS) return cudaErrorInvalidValue;
     if (a.half) {
         switch (M * 100 + a.mj) {
-        case 404: launch_mk<4, 4, KIND, true>(a, per, grid, threads, s); break;
-        case 808: launch_mk<8, 8, KIND, true>(a, per, grid, threads, s); break;
-        case 1616: launch_mk<16, 16, KIND, true>(a, per, grid, threads, s); break;
+        case 404: return launch_mk<4, 4, KIND, true>(a, per, grid, threads, s);
+        case 808: return launch_mk<8, 8, KIND, true>(a, per, grid, threads, s);
+        case 1616: return launch_mk<16, 16, KIND, true>(a, per, grid, threads, s);
         default: return cudaErrorInvalidValue;
         }
-        return cudaGetLastError();
     }
     switch (M * 100 + a.mj) {
-    case 404: launch_mk<4, 4, KIND>(a, per, grid, threads, s); break;
-    case 808: launch_mk<8, 8, KIND>(a, per, grid, threads, s); break;
-    case 804: launch_mk<8, 4, KIND>(a, per, grid, threads, s); break;
-    case 1616: launch_mk<16, 16, KIND>(a, per, grid, threads, s); break;
-    case 1608: launch_mk<16, 8, KIND>(a, per, grid, threads, s); break;
+    case 404: return launch_mk<4, 4, KIND>(a, per, grid, threads, s);
+    case 808: return launch_mk<8, 8, KIND>(a, per, grid, threads, s);
+    case 804: return launch_mk<8, 4, KIND>(a, per, grid, threads, s);
+    case 1616: return launch_mk<16, 16, KIND>(a, per, grid, threads, s);
+    case 1608: return launch_mk<16, 8, KIND>(a, per, grid, threads, s);
     default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 }  // namespace nlg

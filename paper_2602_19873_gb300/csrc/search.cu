@@ -464,23 +464,20 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
 }
 
 template <int M, int MJ, int MODE>
-static void launch_m(const SearchArgs &a, const SearchCtl &c, int per, int grid, int threads,
-                     cudaStream_t s)
+static cudaError_t launch_m(const SearchArgs &a, const SearchCtl &c, int per, int grid, int threads,
+                            cudaStream_t s)
 {
     const size_t smem = (size_t)(threads / 32) * sizeof(SearchSmem<M, MJ>);
     const size_t smax = (size_t)SR_WARPS * sizeof(SearchSmem<M, MJ>);
-    static bool attr[2] = {false, false};
-    if (!attr[per ? 1 : 0]) {
-        if (per)
-            cudaFuncSetAttribute(k_search<M, MJ, true, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
-        else
-            cudaFuncSetAttribute(k_search<M, MJ, false, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
-        attr[per ? 1 : 0] = true;
-    }
+    const void *fn = per ? (const void *)k_search<M, MJ, true, MODE>
+                         : (const void *)k_search<M, MJ, false, MODE>;
+    cudaError_t e = set_max_dynamic_smem(fn, smax);
+    if (e != cudaSuccess) return e;
     if (per)
         k_search<M, MJ, true, MODE><<<grid, threads, smem, s>>>(a, c);
     else
         k_search<M, MJ, false, MODE><<<grid, threads, smem, s>>>(a, c);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_search_ctl(const SearchArgs &a, const uint32_t *work, uint32_t count,
@@ -493,25 +490,21 @@ cudaError_t launch_search_ctl(const SearchArgs &a, const uint32_t *work, uint32_
     if (a.half < 0 || a.half > 2) return cudaErrorInvalidValue;
     switch (M * 100 + a.mj) {
     case 404:
-        if (a.half == 1) launch_m<4, 4, 1>(a, c, any_periodic, grid, threads, s);
-        else if (a.half == 2) launch_m<4, 4, 2>(a, c, any_periodic, grid, threads, s);
-        else launch_m<4, 4, 0>(a, c, any_periodic, grid, threads, s);
-        break;
+        if (a.half == 1) return launch_m<4, 4, 1>(a, c, any_periodic, grid, threads, s);
+        if (a.half == 2) return launch_m<4, 4, 2>(a, c, any_periodic, grid, threads, s);
+        return launch_m<4, 4, 0>(a, c, any_periodic, grid, threads, s);
     case 808:
-        if (a.half == 1) launch_m<8, 8, 1>(a, c, any_periodic, grid, threads, s);
-        else if (a.half == 2) launch_m<8, 8, 2>(a, c, any_periodic, grid, threads, s);
-        else launch_m<8, 8, 0>(a, c, any_periodic, grid, threads, s);
-        break;
-    case 804: launch_m<8, 4, 0>(a, c, any_periodic, grid, threads, s); break;
+        if (a.half == 1) return launch_m<8, 8, 1>(a, c, any_periodic, grid, threads, s);
+        if (a.half == 2) return launch_m<8, 8, 2>(a, c, any_periodic, grid, threads, s);
+        return launch_m<8, 8, 0>(a, c, any_periodic, grid, threads, s);
+    case 804: return launch_m<8, 4, 0>(a, c, any_periodic, grid, threads, s);
     case 1616:
-        if (a.half == 1) launch_m<16, 16, 1>(a, c, any_periodic, grid, threads, s);
-        else if (a.half == 2) launch_m<16, 16, 2>(a, c, any_periodic, grid, threads, s);
-        else launch_m<16, 16, 0>(a, c, any_periodic, grid, threads, s);
-        break;
-    case 1608: launch_m<16, 8, 0>(a, c, any_periodic, grid, threads, s); break;
+        if (a.half == 1) return launch_m<16, 16, 1>(a, c, any_periodic, grid, threads, s);
+        if (a.half == 2) return launch_m<16, 16, 2>(a, c, any_periodic, grid, threads, s);
+        return launch_m<16, 16, 0>(a, c, any_periodic, grid, threads, s);
+    case 1608: return launch_m<16, 8, 0>(a, c, any_periodic, grid, threads, s);
     default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 // Record assembly of the half search: one warp per super-cluster t.  Its

@@ -298,13 +298,8 @@ cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
                              uint32_t n, int bits, uint32_t *hist, cudaStream_t s)
 {
     if (n <= 1) return cudaSuccess;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_rs_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)rs_down_smem());
-        if (e != cudaSuccess) return e;
-        attr_done = true;
-    }
+    cudaError_t e = set_max_dynamic_smem((const void *)k_rs_downsweep, rs_down_smem());
+    if (e != cudaSuccess) return e;
     const uint32_t ntiles = rs_tiles(n);
     uint32_t *tot = hist + (size_t)256 * ntiles;
     uint64_t *ka = keys, *kb = keys_alt;
@@ -319,7 +314,7 @@ cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
     }
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ka != keys) {
         // odd number of passes: copy back
@@ -335,6 +330,8 @@ cudaError_t radix_sort_by_system(uint64_t *keys, uint32_t *vals, uint64_t *keys_
                                  uint32_t nsys, uint32_t *hist, cudaStream_t s)
 {
     if (n <= 1 || nsys <= 1) return cudaSuccess;
+    cudaError_t e = set_max_dynamic_smem((const void *)k_rs_downsweep, rs_down_smem());
+    if (e != cudaSuccess) return e;
     const uint32_t ntiles = rs_tiles(n);
     uint32_t *tot = hist + (size_t)256 * ntiles;
     const DigitSrc dg{sys_off, nsys};
@@ -350,7 +347,7 @@ cudaError_t radix_sort_by_system(uint64_t *keys, uint32_t *vals, uint64_t *keys_
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
     }
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e == cudaSuccess && ka != keys) {
         e = cudaMemcpyAsync(keys, ka, (size_t)n * 8, cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(vals, va, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);

@@ -184,9 +184,28 @@ def params_dict(p):
 NL_NOALLOC_MAX_N = 1048576
 
 
+def _require(t, name, dtype, n):
+    """A contiguous CUDA tensor of `dtype` with at least n elements."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError("%s must be a torch tensor" % name)
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise ValueError("%s must have dtype %s, not %s" % (name, dtype, t.dtype))
+    if t.numel() < n:
+        raise ValueError("%s has %d elements, needs %d" % (name, t.numel(), n))
+
+
 def sfc_order_noalloc(x, y, z, h, box, key, support, keys, perm, stream=None):
     """nl_sfc_order_noalloc: keys (int64 tensor viewed as uint64) and perm
     (int32 tensor) are caller-owned CUDA outputs of n entries."""
+    import torch
+    n = int(x.numel()) if hasattr(x, "numel") else 0
+    for name, t in (("x", x), ("y", y), ("z", z), ("h", h)):
+        _require(t, name, torch.float32, n)
+    _require(keys, "keys", torch.int64, n)
+    _require(perm, "perm", torch.int32, n)
     b = make_box(box) if isinstance(box, dict) else box
     _check(load().nl_sfc_order_noalloc(_ptr(x), _ptr(y), _ptr(z), _ptr(h), int(x.numel()),
                                        C.byref(b), int(key), float(support), _ptr(keys),

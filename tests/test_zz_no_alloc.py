@@ -1,7 +1,7 @@
 """The allocation-free SFC ordering entry point (nl_sfc_order_noalloc), for
-callers that cannot allocate device memory where they need the order
-(inside a stream capture, in a loop that cannot afford cudaMalloc's
-synchronisation, or under a framework that owns all device memory).
+callers that cannot allocate device memory where they need the order (a
+simulation loop that cannot afford cudaMalloc's implicit synchronisation, or
+a framework that owns all device memory and forbids driver allocations).
 
 It must return the same keys and permutation as the allocating path
 (nl_build followed by nl_copy_sorted), bit for bit, on two calls in a row
