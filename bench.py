@@ -31,6 +31,7 @@ UNIT = "Mparticles/s"
 WORKLOAD = "plummer64_16m"
 N_FULL = 1 << 24
 ALU_OPS_PER_PAIR_SEARCH = 9      # predicate: 3 sub, 3 mul, 2 add, 1 compare (non-periodic)
+ALU_OPS_PER_DENSITY_SIDE = 12    # gather pair in range: square root, scale, spline, weighted add
 ALGO_BYTES_PER_PARTICLE = 145    # keygen 20 + sort 24 + permute 49 + octree 2 + search 19 + density 31
 # DRAM bytes (read + write) of one k_search launch per particle, from ncu
 # captures on this generator at 2^21 particles (8x8 clusters, leaf bucket 256,
@@ -49,6 +50,28 @@ def peaks():
             d = json.load(f)
         return d.get("hbm_gbs", 6800.0), "measured", d.get("sm_max_mhz", 2070.0)
     return 6800.0, "fallback", 2070.0
+
+
+def fp32_peak(stream, device_index=0):
+    """Measured FP32 rate of this GPU (element ops/s, scalar and packed
+    fused multiply-add chains on every lane, CUDA events), with the SM clock
+    sampled while the probe runs.  The peak is the faster of the two forms;
+    the nominal figure (SMs x 128 lanes x max clock) is given beside it."""
+    import torch
+    from paper_2602_19873_gb300 import nl
+    clocks = Clocks(device_index)
+    clocks.start()
+    scalar, scalar_ms = nl.probe_fp32_rate(False, 10, stream)
+    packed, packed_ms = nl.probe_fp32_rate(True, 10, stream)
+    clk = clocks.stop()
+    sms = torch.cuda.get_device_properties(device_index).multi_processor_count
+    _, _, sm_max = peaks()
+    return {"tops": max(scalar, packed) / 1e12, "scalar_tops": scalar / 1e12,
+            "packed_tops": packed / 1e12, "scalar_ms": scalar_ms, "packed_ms": packed_ms,
+            "sms": sms, "nominal_tops": sms * 128 * sm_max * 1e6 / 1e12,
+            "sm_mhz": clk.get("sm_mhz"), "reasons": clk.get("reasons"),
+            "how": "nl_probe_fp32_rate: 8 independent FMA chains per thread on every lane of "
+                   "every SM, best of 10 launches (CUDA events); one element FMA = one op"}
 
 
 class Clocks:
@@ -371,9 +394,13 @@ def run_native(args):
                "unit": UNIT, "stages_ms": {k: v / args.steps for k, v in a_acc.items()},
                "bytes_per_particle": asz["list_bytes"] / n, "entries": asz["n_entries"]}
         A.free()
-    # pair slots of the symmetric relation the search decides: the full
-    # list's tiles (a half list stores each pair of super-clusters once)
-    full_tiles = sizes["n_tiles"] if args.list == "full" else (asz["n_tiles"] if alt else None)
+    # gather pairs of the timed list (the density pass evaluates the kernel
+    # once per gather pair and particle): one count pass after the timing
+    cnt = torch.empty(n, dtype=torch.int32, device="cuda")
+    L.neighbor_counts(cnt, stream)
+    torch.cuda.synchronize()
+    gather_pairs = int(cnt.to(torch.int64).sum().item())
+    del cnt
 
     # end to end through the host-buffer entry point (pinned memory)
     pin = {k: torch.from_numpy(d[k]).pin_memory().numpy() for k in ("x", "y", "z", "h", "m")}
@@ -393,10 +420,15 @@ def run_native(args):
     e_ms = max_over_ranks(e_ms, ws, "cuda")
 
     hbm, hbm_kind, sm_max = peaks()
-    alu_peak = 152 * 128 * sm_max * 1e6 / 1e12  # FP32 instructions per second, Tops
+    fp32 = fp32_peak(stream, local)
+    alu_peak = fp32["tops"]
     search_ms = stages.get("search", float("nan"))
-    pairs = (full_tiles if full_tiles is not None else sizes["n_tiles"]) * params.cluster * sizes["j_cluster"]
+    pass_ms = stages.get("pass", float("nan"))
+    # computed pairs of the timed list: its tiles with the mask bit set x M x MJ
+    pairs = sizes["n_tiles"] * params.cluster * sizes["j_cluster"]
     achieved = pairs * ALU_OPS_PER_PAIR_SEARCH / (search_ms * 1e-3) / 1e12
+    pass_ops = pairs * ALU_OPS_PER_PAIR_SEARCH + (gather_pairs + n) * ALU_OPS_PER_DENSITY_SIDE
+    pass_achieved = pass_ops / (pass_ms * 1e-3) / 1e12
     step_bytes = ALGO_BYTES_PER_PARTICLE * n
     out = {
         "metric": METRIC, "value": job_rate(n, ws, ms), "unit": UNIT, "n_gpus": ws,
@@ -414,13 +446,23 @@ def run_native(args):
         "stages_ms": stages,
         "roofline": {"bound": "alu", "kernel": "k_search (cluster-pair search + encode)",
                      "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                     "peak_kind": "FP32 lanes x max SM clock (152 SMs x 128 x %.0f MHz)" % sm_max,
+                     "peak_kind": "measured FP32 rate (nl_probe_fp32_rate, faster of scalar "
+                                  "and packed FMA chains)",
                      "frac": achieved / alu_peak,
                      "traffic": (SEARCH_DRAM_BYTES_PER_PARTICLE[args.list] * n
                                  if (M, MJ) == (8, 8) and params.leaf_bucket == 256
                                  and SEARCH_DRAM_BYTES_PER_PARTICLE.get(args.list) else None),
                      "algorithmic": "%d FP32 ops per computed pair, %d computed pairs (tiles of "
-                                    "the full list x M x MJ)" % (ALU_OPS_PER_PAIR_SEARCH, pairs)},
+                                    "the timed %s list with the mask bit set x M x MJ)"
+                                    % (ALU_OPS_PER_PAIR_SEARCH, pairs, args.list)},
+        "roofline_pass": {"bound": "alu", "kernel": "k_pass (decode + density)",
+                          "achieved": pass_achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                          "frac": pass_achieved / alu_peak,
+                          "algorithmic": "%d FP32 ops per computed pair (%d) + %d per gather "
+                                         "pair or self term in range (%d + %d)"
+                                         % (ALU_OPS_PER_PAIR_SEARCH, pairs,
+                                            ALU_OPS_PER_DENSITY_SIDE, gather_pairs, n)},
+        "fp32_peak": fp32,
         "hbm_step": {"achieved_gbs": step_bytes / (ms * 1e-3) / 1e9, "peak_gbs": hbm,
                      "peak_kind": hbm_kind,
                      "frac": step_bytes / (ms * 1e-3) / 1e9 / hbm,

@@ -401,6 +401,20 @@ nl_status nl_set_mlp(nl_list *nl, const nl_mlp *mlp);
 /* Thread-local description of the last error (never NULL). */
 const char *nl_last_error(void);
 
+/* Measured FP32 rate of the current GPU, the denominator of the rooflines of
+ * the search and the passes (bound by FP32 issue, not memory).  The paper has
+ * no counterpart; it is measurement support.  Runs independent fused
+ * multiply-add chains on every lane of every SM -- scalar fma.rn.f32
+ * (packed = 0) or the two-element fma.rn.f32x2 (packed = 1) -- and times
+ * reps launches (after one warm-up) with CUDA events on `stream`.
+ * *ops_per_s = FP32 element operations per second of the fastest launch (one
+ * add, multiply, fused multiply-add or compare of one element = one op; a
+ * packed instruction = two); *ms_out (may be NULL) = that launch's time.
+ * reps in 1..1000, else NL_ERR_ARG.  Allocates one word (stream-ordered) and
+ * synchronises `stream` once per launch. */
+nl_status nl_probe_fp32_rate(int32_t packed, int32_t reps, double *ops_per_s, double *ms_out,
+                             void *stream);
+
 #ifdef __cplusplus
 }
 #endif

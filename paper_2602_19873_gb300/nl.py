@@ -93,6 +93,7 @@ _SIGS = {
                                C.c_uint64, P, P]),
     "nl_mlp_predict": (C.c_int, [P, P, C.c_int64, P, P]),
     "nl_set_mlp": (C.c_int, [P, P]),
+    "nl_probe_fp32_rate": (C.c_int, [C.c_int32, C.c_int32, P, P, P]),
     "nl_iterate_h": (C.c_int, [P, P, P, P, P, C.c_int64, P, P, C.c_float, C.c_float, C.c_int32,
                                C.c_float, C.c_int32, P, P, P]),
 }
@@ -472,3 +473,12 @@ class NeighborList:
             self.free()
         except Exception:
             pass
+
+
+def probe_fp32_rate(packed=False, reps=5, stream=None):
+    """nl_probe_fp32_rate: (FP32 element ops per second, ms of the best launch)."""
+    ops = C.c_double()
+    ms = C.c_double()
+    _check(load().nl_probe_fp32_rate(int(bool(packed)), int(reps), C.byref(ops), C.byref(ms),
+                                     _stream(stream)))
+    return ops.value, ms.value
