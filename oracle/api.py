@@ -24,7 +24,8 @@ __all__ = [
     "w", "dw", "W", "density", "sph_force", "lj_force", "lj_energy", "ljc_force", "ljc_energy",
     "nearest", "gather_counts_brute",
     "pred", "dist2", "dist2_row", "num_threads", "pipeline_lists", "mlp_nparams",
-    "mlp_forward", "mlp_loss_grad",
+    "mlp_forward", "mlp_loss_grad", "mlp_features", "mlp_targets", "h_at_count",
+    "computed_pairs", "cluster_overhead",
 ]
 
 
@@ -110,6 +111,10 @@ def lib():
                 "orc_mlp_nparams": (I64, []),
                 "orc_mlp_forward": (None, [I64, P, P, P]),
                 "orc_mlp_loss_grad": (C.c_double, [I64, P, P, P, P]),
+                "orc_mlp_features": (C.c_int, [I64, P, P, P, P, C.c_int, P, P]),
+                "orc_mlp_targets": (None, [I64, P, C.c_int, P, P, P]),
+                "orc_h_at_count": (C.c_int, [I64, P, P, P, P, P, F32, C.c_int, P]),
+                "orc_computed_pairs": (I64, [I64, P, C.c_int, C.c_int]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -504,3 +509,52 @@ def mlp_loss_grad(X, t, P):
     G = np.zeros(mlp_nparams())
     loss = lib().orc_mlp_loss_grad(len(X), _p(X), _p(t), _p(P), _p(G))
     return loss, G
+
+
+def mlp_features(xs, ys, zs, box, cluster):
+    """Learned-start features of one system in sorted order: (X [clusters x 8],
+    e64 [super-clusters]), FP64."""
+    xs, ys, zs = _f32(xs), _f32(ys), _f32(zs)
+    n = len(xs)
+    nsc = (n + 8 * cluster - 1) // (8 * cluster)
+    X = np.zeros((8 * nsc, 8))
+    e64 = np.zeros(nsc)
+    b = _box(box)
+    if lib().orc_mlp_features(n, _p(xs), _p(ys), _p(zs), C.byref(b), int(cluster), _p(X),
+                              _p(e64)) != 0:
+        raise MemoryError("orc_mlp_features")
+    return X, e64
+
+
+def mlp_targets(hs, cluster, e64):
+    """Targets (y, w) per cluster from sorted smoothing lengths and e64."""
+    hs = _f32(hs)
+    e64 = np.ascontiguousarray(e64, dtype=np.float64)
+    ncl = 8 * len(e64)
+    y, w = np.zeros(ncl), np.zeros(ncl)
+    lib().orc_mlp_targets(len(hs), _p(hs), int(cluster), _p(e64), _p(y), _p(w))
+    return y, w
+
+
+def h_at_count(xs, ys, zs, sorted_keys, box, support, k):
+    """FP32 smoothing lengths (sorted order) with exactly k gather neighbors:
+    halfway, in squared distance, between the k-th and (k+1)-th neighbor."""
+    xs, ys, zs = _f32(xs), _f32(ys), _f32(zs)
+    keys = np.ascontiguousarray(sorted_keys, dtype=np.uint64)
+    out = np.zeros(len(xs), np.float32)
+    b = _box(box)
+    if lib().orc_h_at_count(len(xs), _p(xs), _p(ys), _p(zs), _p(keys), C.byref(b),
+                            float(support), int(k), _p(out)) != 0:
+        raise ValueError("orc_h_at_count: n <= k or out of memory")
+    return out
+
+
+def computed_pairs(mask, cluster, jcluster=None):
+    """Particle pairs a list's tiles evaluate: set mask bits x M x MJ."""
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    return int(lib().orc_computed_pairs(len(m), _p(m), int(cluster), int(jcluster or cluster)))
+
+
+def cluster_overhead(mask, cluster, n_pairs, n, jcluster=None):
+    """Computed pairs / (ordered neighbor pairs + self terms)."""
+    return computed_pairs(mask, cluster, jcluster) / float(n_pairs + n)

@@ -51,8 +51,9 @@
  *    no reaction field); the list is built at a larger radius (Verlet buffer)
  *    and the interaction set is the gather set at rc.
  *
- * Parity unpinned: orc_cluster_overhead's normalisation (the paper's Fig. 2
- * values are not printed); it is reported, never compared.
+ * The paper's Fig. 2 cluster-overhead values are not printed, so the overhead
+ * is pinned by closed forms (1x1 clusters, all pairs in range, isolated
+ * clusters), not by the paper's numbers.
  */
 #define _DEFAULT_SOURCE
 #include <math.h>
@@ -1128,13 +1129,15 @@ void orc_nearest(const float *xs, const float *ys, const float *zs, const orc_bo
     }
 }
 
-/* Number of predicate evaluations a cluster list implies (masked tiles x
- * cluster^2) and the number of particles-in-range pairs it serves. */
-void orc_cluster_overhead(const orc_clist *c, int cluster, int64_t *computed)
+/* Computed pairs of a cluster list (Sec. III-A): every listed tile, i.e.
+ * every set mask bit, costs its M x MJ particle pairs.  The cluster overhead
+ * is this count divided by the pairs the list serves (ordered neighbor pairs
+ * plus one self term per particle). */
+int64_t orc_computed_pairs(int64_t nnz, const uint8_t *mask, int cluster, int jcluster)
 {
     int64_t s = 0;
-    for (int64_t t = 0; t < c->off[c->nsc]; ++t) s += __builtin_popcount(c->mask[t]);
-    *computed = s * (int64_t)cluster * (int64_t)cluster;
+    for (int64_t t = 0; t < nnz; ++t) s += __builtin_popcount(mask[t]);
+    return s * (int64_t)cluster * (int64_t)jcluster;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1276,4 +1279,293 @@ double orc_mlp_loss_grad(int64_t n, const double *X, const double *t, const doub
         }
     }
     return loss / (double)n;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Learned-start inputs (not in the paper; the features are this project's  */
+/* own proposal).  One system in SFC-sorted order, n particles, clusters of */
+/* M = `cluster` consecutive particles, super-clusters of 8 clusters; the   */
+/* tail cluster slots beyond n hold no particle.  With e(B) the largest     */
+/* side of box B (floored at 1e-7 L), e8 the box of the cluster's real      */
+/* particles, e64 the box of its super-cluster, e512 / e4096 the boxes of    */
+/* super-clusters s-3..s+4 / s-31..s+32 clipped to the system, L the largest */
+/* side of the system box and N_s its particle count, cluster c gets        */
+/*   log(e8/e64), log(e512/e64), log(e4096/e64), log(ex/e8), log(ey/e8),     */
+/*   log(ez/e8), log(count/M), log(e64/L) + log(N_s)/3                       */
+/* and an empty cluster gets zeros.  Plain FP64 on the FP32 inputs.          */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double lo[3], hi[3];
+} dbox;
+
+static void dbox_empty(dbox *b)
+{
+    for (int a = 0; a < 3; ++a) {
+        b->lo[a] = INFINITY;
+        b->hi[a] = -INFINITY;
+    }
+}
+
+static void dbox_add_box(dbox *b, const dbox *o)
+{
+    for (int a = 0; a < 3; ++a) {
+        if (o->lo[a] < b->lo[a]) b->lo[a] = o->lo[a];
+        if (o->hi[a] > b->hi[a]) b->hi[a] = o->hi[a];
+    }
+}
+
+static double dbox_side(const dbox *b, int a, double floor_len)
+{
+    double e = b->hi[a] - b->lo[a];
+    return e > floor_len ? e : floor_len;
+}
+
+static double dbox_extent(const dbox *b, double floor_len)
+{
+    double e = dbox_side(b, 0, floor_len);
+    for (int a = 1; a < 3; ++a) {
+        double v = dbox_side(b, a, floor_len);
+        if (v > e) e = v;
+    }
+    return e;
+}
+
+int orc_mlp_features(int64_t n, const float *xs, const float *ys, const float *zs,
+                     const orc_box *box, int cluster, double *X, double *e64)
+{
+    const int64_t M = cluster, scp = 8 * (int64_t)cluster;
+    const int64_t nsc = (n + scp - 1) / scp, ncl = 8 * nsc;
+    double L = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double len = (double)box->hi[a] - (double)box->lo[a];
+        if (len > L) L = len;
+    }
+    const double fl = 1e-7 * L;
+    dbox *cb = (dbox *)malloc((size_t)(ncl > 0 ? ncl : 1) * sizeof(dbox));
+    dbox *sb = (dbox *)malloc((size_t)(nsc > 0 ? nsc : 1) * sizeof(dbox));
+    int64_t *cnt = (int64_t *)calloc((size_t)(ncl > 0 ? ncl : 1), sizeof(int64_t));
+    if (!cb || !sb || !cnt) return -1;
+    const float *p[3] = {xs, ys, zs};
+    for (int64_t c = 0; c < ncl; ++c) {
+        dbox_empty(&cb[c]);
+        for (int64_t i = c * M; i < (c + 1) * M && i < n; ++i) {
+            for (int a = 0; a < 3; ++a) {
+                double v = (double)p[a][i];
+                if (v < cb[c].lo[a]) cb[c].lo[a] = v;
+                if (v > cb[c].hi[a]) cb[c].hi[a] = v;
+            }
+            cnt[c]++;
+        }
+    }
+    for (int64_t s = 0; s < nsc; ++s) {
+        dbox_empty(&sb[s]);
+        for (int k = 0; k < 8; ++k) dbox_add_box(&sb[s], &cb[8 * s + k]);
+        e64[s] = dbox_extent(&sb[s], fl);
+    }
+    for (int64_t s = 0; s < nsc; ++s) {
+        dbox r8, r64;
+        dbox_empty(&r8);
+        dbox_empty(&r64);
+        for (int64_t t = s - 3; t < s + 5; ++t)
+            if (t >= 0 && t < nsc) dbox_add_box(&r8, &sb[t]);
+        for (int64_t t = s - 31; t < s + 33; ++t)
+            if (t >= 0 && t < nsc) dbox_add_box(&r64, &sb[t]);
+        const double e512 = dbox_extent(&r8, fl), e4096 = dbox_extent(&r64, fl);
+        const double dens = log(e64[s] / L) + log((double)n) / 3.0;
+        for (int k = 0; k < 8; ++k) {
+            const int64_t c = 8 * s + k;
+            double *x = X + c * 8;
+            if (cnt[c] == 0) {
+                for (int f = 0; f < 8; ++f) x[f] = 0.0;
+                continue;
+            }
+            const double ex = dbox_side(&cb[c], 0, fl), ey = dbox_side(&cb[c], 1, fl);
+            const double ez = dbox_side(&cb[c], 2, fl);
+            const double e8 = dbox_extent(&cb[c], fl);
+            x[0] = log(e8 / e64[s]);
+            x[1] = log(e512 / e64[s]);
+            x[2] = log(e4096 / e64[s]);
+            x[3] = log(ex / e8);
+            x[4] = log(ey / e8);
+            x[5] = log(ez / e8);
+            x[6] = log((double)cnt[c] / (double)M);
+            x[7] = dens;
+        }
+    }
+    free(cb);
+    free(sb);
+    free(cnt);
+    return 0;
+}
+
+/* Targets of the learned start: y[c] = log(mean h of the real particles of
+ * cluster c / e64 of its super-cluster), w[c] = 1; empty clusters y = w = 0.
+ * hs in SFC-sorted order. */
+void orc_mlp_targets(int64_t n, const float *hs, int cluster, const double *e64, double *y,
+                     double *w)
+{
+    const int64_t M = cluster, scp = 8 * (int64_t)cluster;
+    const int64_t ncl = 8 * ((n + scp - 1) / scp);
+    for (int64_t c = 0; c < ncl; ++c) {
+        double s = 0.0;
+        int64_t k = 0;
+        for (int64_t i = c * M; i < (c + 1) * M && i < n; ++i, ++k) s += (double)hs[i];
+        y[c] = k ? log(s / (double)k / e64[c / 8]) : 0.0;
+        w[c] = k ? 1.0 : 0.0;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Smoothing lengths at exactly k gather neighbors (the centre of the h     */
+/* iteration's window, which is not in the paper): for particle i, with      */
+/* d2_(k) <= d2_(k+1) its k-th and (k+1)-th smallest canonical FP32 squared  */
+/* distances to the other particles, h_i = sqrt((d2_(k) + d2_(k+1)) / 2) /   */
+/* support, rounded once to FP32, so #{j != i : d2_ij < (support h_i)^2} = k */
+/* unless distances tie within a rounding.  The k+1 nearest come from an     */
+/* exact nearest-neighbor descent of the octree of the sorted keys (node     */
+/* boxes in FP64, pruning only where the whole node lies beyond the current  */
+/* (k+1)-th distance with a margin far above the FP32 rounding).  Inputs in  */
+/* SFC-sorted order with their sorted keys; returns 0, or -1 when n <= k or  */
+/* memory runs out.                                                         */
+/* ------------------------------------------------------------------------ */
+static double gap1(double x, double lo, double hi)
+{
+    return x < lo ? lo - x : (x > hi ? x - hi : 0.0);
+}
+
+static double box_gap2(const dbox *bx, const double *x, const orc_box *b)
+{
+    double s = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double g = gap1(x[a], bx->lo[a], bx->hi[a]);
+        if (b->periodic[a] && g > 0.0) {
+            double L = (double)b->hi[a] - (double)b->lo[a];
+            double g1 = gap1(x[a] - L, bx->lo[a], bx->hi[a]);
+            double g2 = gap1(x[a] + L, bx->lo[a], bx->hi[a]);
+            if (g1 < g) g = g1;
+            if (g2 < g) g = g2;
+        }
+        s += g * g;
+    }
+    return s;
+}
+
+/* max-heap of floats: push while not full, else replace the maximum */
+static void heap_offer(float *hp, int *size, int cap, float v)
+{
+    int i;
+    if (*size < cap) {
+        i = (*size)++;
+        while (i > 0 && hp[(i - 1) / 2] < v) {
+            hp[i] = hp[(i - 1) / 2];
+            i = (i - 1) / 2;
+        }
+        hp[i] = v;
+        return;
+    }
+    if (!(v < hp[0])) return;
+    i = 0;
+    for (;;) {
+        int l = 2 * i + 1, r = l + 1, m = i;
+        float big = v;
+        if (l < cap && hp[l] > big) { m = l; big = hp[l]; }
+        if (r < cap && hp[r] > big) { m = r; }
+        if (m == i) break;
+        hp[i] = hp[m];
+        i = m;
+    }
+    hp[i] = v;
+}
+
+int orc_h_at_count(int64_t n, const float *xs, const float *ys, const float *zs,
+                   const uint64_t *sorted_keys, const orc_box *b, float support, int k,
+                   float *hout)
+{
+    if (n <= k || k < 1) return -1;
+    const int bucket = 64;
+    int64_t cap = 4 * n / bucket * 22 + 64;
+    int32_t *level = NULL, *leaf = NULL;
+    int64_t *first = NULL, *end = NULL, cnt = 0;
+    for (;;) {
+        level = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
+        leaf = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
+        first = (int64_t *)malloc((size_t)cap * sizeof(int64_t));
+        end = (int64_t *)malloc((size_t)cap * sizeof(int64_t));
+        if (!level || !leaf || !first || !end) return -1;
+        cnt = orc_octree(n, sorted_keys, bucket, level, first, end, leaf, cap);
+        if (cnt <= cap) break;
+        free(level), free(leaf), free(first), free(end);
+        cap = cnt;
+    }
+    int64_t *skip = (int64_t *)malloc((size_t)cnt * sizeof(int64_t));
+    dbox *nb = (dbox *)malloc((size_t)cnt * sizeof(dbox));
+    if (!skip || !nb) return -1;
+    for (int64_t t = cnt - 1; t >= 0; --t) {
+        int64_t c = t + 1;
+        if (!leaf[t])
+            while (c < cnt && first[c] < end[t]) c = skip[c];
+        skip[t] = c;
+    }
+    const float *p[3] = {xs, ys, zs};
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t t = 0; t < cnt; ++t) {
+        dbox_empty(&nb[t]);
+        for (int64_t i = first[t]; i < end[t]; ++i)
+            for (int a = 0; a < 3; ++a) {
+                double v = (double)p[a][i];
+                if (v < nb[t].lo[a]) nb[t].lo[a] = v;
+                if (v > nb[t].hi[a]) nb[t].hi[a] = v;
+            }
+    }
+    int fail = 0;
+#pragma omp parallel
+    {
+        float *hp = (float *)malloc((size_t)(k + 1) * sizeof(float));
+        int64_t *stack = (int64_t *)malloc((size_t)(8 * (ORC_MAX_LEVEL + 2)) * sizeof(int64_t));
+        if (!hp || !stack) {
+#pragma omp atomic write
+            fail = 1;
+        }
+#pragma omp for schedule(dynamic, 256)
+        for (int64_t i = 0; i < n; ++i) {
+            if (!hp || !stack) continue;
+            const double x[3] = {(double)xs[i], (double)ys[i], (double)zs[i]};
+            int size = 0, top = 0;
+            stack[top++] = 0;
+            while (top > 0) {
+                const int64_t t = stack[--top];
+                if (size == k + 1 && box_gap2(&nb[t], x, b) * (1.0 - 1e-5) > (double)hp[0])
+                    continue;
+                if (leaf[t]) {
+                    for (int64_t j = first[t]; j < end[t]; ++j)
+                        if (j != i) heap_offer(hp, &size, k + 1, dist2_32(xs, ys, zs, i, j, b));
+                    continue;
+                }
+                /* children, pushed farthest first so the nearest is visited first */
+                int64_t ch[8];
+                double cd[8];
+                int nc = 0;
+                for (int64_t c = t + 1; c < cnt && first[c] < end[t]; c = skip[c]) {
+                    double d = box_gap2(&nb[c], x, b);
+                    int q = nc++;
+                    while (q > 0 && cd[q - 1] < d) {
+                        ch[q] = ch[q - 1];
+                        cd[q] = cd[q - 1];
+                        --q;
+                    }
+                    ch[q] = c;
+                    cd[q] = d;
+                }
+                for (int q = 0; q < nc; ++q) stack[top++] = ch[q];
+            }
+            /* hp[0] = d2_(k+1); the k-th is the larger of the root's children */
+            float dk1 = hp[0], dk = hp[1];
+            if (k + 1 > 2 && hp[2] > dk) dk = hp[2];
+            hout[i] = (float)(sqrt(0.5 * ((double)dk + (double)dk1)) / (double)support);
+        }
+        free(hp);
+        free(stack);
+    }
+    free(level), free(leaf), free(first), free(end), free(skip), free(nb);
+    return fail ? -1 : 0;
 }

@@ -132,3 +132,39 @@ def test_learned_start_needs_fewer_passes():
     Lp.free()
     Ll.free()
     mlp.free()
+
+
+# Features and targets are logs of ratios of FP32 box sides and of mean h:
+# each ratio carries a few FP32 roundings (relative 2^-23 each, about 2.4e-7
+# in the log) and logf adds 2 ulp of its result (|log| <= 20: about 4e-6).
+FEATURE_ATOL = 1e-5
+
+
+@pytest.mark.parametrize("name,M", [("plummer", 8), ("uniform", 8), ("evrard", 16),
+                                    ("plummer", 4)])
+def test_features_and_targets_match_oracle(name, M):
+    """Per-cluster features and training targets of the learned start,
+    element by element against the FP64 oracle on the oracle's own sort of
+    the same particles (ragged sizes: partly filled last super-clusters)."""
+    import torch
+    d = {"plummer": lambda: wl.plummer(30011, n_spheres=4, seed=41),
+         "uniform": lambda: wl.uniform(20005, seed=42),
+         "evrard": lambda: wl.evrard(25003, seed=43)}[name]()
+    o = oracle_sorted(d)
+    Xw, e64w = orc.mlp_features(o["xs"], o["ys"], o["zs"], d["box"], M)
+    yw, ww = orc.mlp_targets(o["hs"], M, e64w)
+    t = {k: torch.from_numpy(np.ascontiguousarray(d[k], dtype=np.float32)).cuda()
+         for k in ("x", "y", "z", "h")}
+    p = nl.make_params(key=d["kind"], cluster=M, support=d["support"])
+    L = nl.NeighborList().build(t["x"], t["y"], t["z"], t["h"], d["box"], p)
+    X, e64 = L.mlp_features()
+    y, w = L.mlp_targets(t["h"], e64)
+    torch.cuda.synchronize()
+    X, e64, y, w = (a.cpu().numpy().astype(np.float64) for a in (X, e64, y, w))
+    assert X.shape == Xw.shape and e64.shape == e64w.shape
+    assert np.max(np.abs(e64 - e64w) / e64w) <= 1e-6
+    err = np.abs(X - Xw)
+    assert err.max() <= FEATURE_ATOL, (np.unravel_index(err.argmax(), err.shape), err.max())
+    assert np.array_equal(w, ww)
+    assert np.max(np.abs(y - yw)) <= FEATURE_ATOL
+    L.free()
