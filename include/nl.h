@@ -401,6 +401,57 @@ nl_status nl_set_mlp(nl_list *nl, const nl_mlp *mlp);
 /* Thread-local description of the last error (never NULL). */
 const char *nl_last_error(void);
 
+/* SFC domain decomposition across ranks (Sec. I: the domain is split into
+ * contiguous key ranges of the space-filling curve; Sec. IV: every rank builds
+ * its list over its own particles plus a halo received from the others).
+ * These are the per-rank device steps; the caller exchanges their results
+ * between ranks (paper_2602_19873_gb300/domain.py does it over
+ * torch.distributed: two all-reduces of key histograms for the splitters,
+ * one all-to-all of the particles, one all-gather of the rank boxes, one
+ * all-to-all of the halo).  At most 64 ranks: destinations are the bits of a
+ * 64-bit mask per particle.  All arrays are device arrays in the caller's
+ * order; none of these calls synchronises except nl_sfc_keys.
+ *
+ * nl_sfc_keys: the 63-bit key of every particle in `box` exactly as nl_build
+ *   computes it (NL_KEY_MORTON / NL_KEY_HILBERT, 21 bits per axis), caller
+ *   order, unsorted.  Validates like nl_build (NL_ERR_ARG, NL_ERR_RADIUS);
+ *   allocates stream-ordered scratch (4n + 256 bytes) and synchronises
+ *   `stream` once.  n = 0 is allowed (nothing written). */
+nl_status nl_sfc_keys(const float *x, const float *y, const float *z, const float *h, int64_t n,
+                      const nl_box *box, int32_t key, float support, uint64_t *keys, void *stream);
+/* hist[b] = #{i : keys[i] >= lo and (keys[i] - lo) >> shift == b}, b < nbins
+ *   (nbins uint64 counters, overwritten).  0 <= shift <= 63, 1 <= nbins <= 2^24. */
+nl_status nl_key_histogram(const uint64_t *keys, int64_t n, uint64_t lo, int32_t shift,
+                           int32_t nbins, uint64_t *hist, void *stream);
+/* mask[i] = 1 << (number of splitters <= keys[i]): the owner rank of every
+ *   particle, for P ranks and P-1 ascending splitters (device uint64). */
+nl_status nl_domain_owner_mask(const uint64_t *keys, int64_t n, const uint64_t *splitters,
+                               int32_t P, uint64_t *mask, void *stream);
+/* out[0..7] = lo.x lo.y lo.z rmax hi.x hi.y hi.z 0: the tight box of the
+ *   particles and their largest radius support*h (device floats; n = 0 gives
+ *   lo = +inf, hi = -inf, rmax = 0).  Allocates 32 bytes stream-ordered. */
+nl_status nl_domain_box(const float *x, const float *y, const float *z, const float *h,
+                        int64_t n, float support, float *out, void *stream);
+/* Halo destinations: mask[i] bit q (q != self) is set when particle i, of
+ *   radius support*h_i, could be a symmetric neighbor of some particle inside
+ *   rank q's box dom[8q .. 8q+7] (the layout of nl_domain_box; an empty box
+ *   is skipped): the search's conservative point-box test with monotone
+ *   rounding and periodic gaps of `box`, so no pair of the predicate is lost.
+ *   dom: P x 8 device floats, 16-byte aligned. */
+nl_status nl_domain_halo_mask(const float *x, const float *y, const float *z, const float *h,
+                              int64_t n, const nl_box *box, float support, const float *dom,
+                              int32_t P, int32_t self, uint64_t *mask, void *stream);
+/* counts[q] = number of set bits q over the n masks (P device int64). */
+nl_status nl_domain_count(const uint64_t *mask, int64_t n, int32_t P, int64_t *counts,
+                          void *stream);
+/* Stable grouping by destination: for every bit q of mask[i], i is written to
+ *   idx[offsets[q] + (number of j < i with bit q)].  offsets: P device int64
+ *   (typically the exclusive sums of nl_domain_count); idx must hold every
+ *   destination's range.  n <= 2^32.  Allocates 4 P ceil(n/1024) bytes
+ *   stream-ordered. */
+nl_status nl_domain_group(const uint64_t *mask, int64_t n, int32_t P, const int64_t *offsets,
+                          uint32_t *idx, void *stream);
+
 /* Measured FP32 rate of the current GPU, the denominator of the rooflines of
  * the search and the passes (bound by FP32 issue, not memory).  The paper has
  * no counterpart; it is measurement support.  Runs independent fused

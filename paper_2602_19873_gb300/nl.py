@@ -94,6 +94,14 @@ _SIGS = {
     "nl_mlp_predict": (C.c_int, [P, P, C.c_int64, P, P]),
     "nl_set_mlp": (C.c_int, [P, P]),
     "nl_probe_fp32_rate": (C.c_int, [C.c_int32, C.c_int32, P, P, P]),
+    "nl_sfc_keys": (C.c_int, [P, P, P, P, C.c_int64, P, C.c_int32, C.c_float, P, P]),
+    "nl_key_histogram": (C.c_int, [P, C.c_int64, C.c_uint64, C.c_int32, C.c_int32, P, P]),
+    "nl_domain_owner_mask": (C.c_int, [P, C.c_int64, P, C.c_int32, P, P]),
+    "nl_domain_box": (C.c_int, [P, P, P, P, C.c_int64, C.c_float, P, P]),
+    "nl_domain_halo_mask": (C.c_int, [P, P, P, P, C.c_int64, P, C.c_float, P, C.c_int32,
+                                      C.c_int32, P, P]),
+    "nl_domain_count": (C.c_int, [P, C.c_int64, C.c_int32, P, P]),
+    "nl_domain_group": (C.c_int, [P, C.c_int64, C.c_int32, P, P, P]),
     "nl_iterate_h": (C.c_int, [P, P, P, P, P, C.c_int64, P, P, C.c_float, C.c_float, C.c_int32,
                                C.c_float, C.c_int32, P, P, P]),
 }
@@ -482,3 +490,82 @@ def probe_fp32_rate(packed=False, reps=5, stream=None):
     _check(load().nl_probe_fp32_rate(int(bool(packed)), int(reps), C.byref(ops), C.byref(ms),
                                      _stream(stream)))
     return ops.value, ms.value
+
+
+# ------------------------------------------------------------ domain decomposition
+def sfc_keys(x, y, z, h, box, key, support, keys, stream=None):
+    """nl_sfc_keys: keys (int64 CUDA tensor of n, viewed as uint64) of the
+    particles in caller order."""
+    import torch
+    n = int(x.numel())
+    for name, t in (("x", x), ("y", y), ("z", z), ("h", h)):
+        _require(t, name, torch.float32, n)
+    _require(keys, "keys", torch.int64, n)
+    b = make_box(box) if isinstance(box, dict) else box
+    _check(load().nl_sfc_keys(_ptr(x), _ptr(y), _ptr(z), _ptr(h), n, C.byref(b), int(key),
+                              float(support), _ptr(keys), _stream(stream)))
+
+
+def key_histogram(keys, lo, shift, nbins, hist, stream=None):
+    """nl_key_histogram into hist (int64 CUDA tensor of nbins)."""
+    import torch
+    _require(keys, "keys", torch.int64, int(keys.numel()))
+    _require(hist, "hist", torch.int64, int(nbins))
+    _check(load().nl_key_histogram(_ptr(keys), int(keys.numel()), int(lo), int(shift), int(nbins),
+                                   _ptr(hist), _stream(stream)))
+
+
+def domain_owner_mask(keys, splitters, P, mask, stream=None):
+    """nl_domain_owner_mask: splitters int64 CUDA tensor of P-1."""
+    import torch
+    n = int(keys.numel())
+    _require(keys, "keys", torch.int64, n)
+    _require(mask, "mask", torch.int64, n)
+    if P > 1:
+        _require(splitters, "splitters", torch.int64, P - 1)
+    _check(load().nl_domain_owner_mask(_ptr(keys), n, _ptr(splitters) if P > 1 else None, int(P),
+                                       _ptr(mask), _stream(stream)))
+
+
+def domain_box(x, y, z, h, support, out, stream=None):
+    """nl_domain_box into out (float32 CUDA tensor of 8)."""
+    import torch
+    n = int(x.numel())
+    for name, t in (("x", x), ("y", y), ("z", z), ("h", h)):
+        _require(t, name, torch.float32, n)
+    _require(out, "out", torch.float32, 8)
+    _check(load().nl_domain_box(_ptr(x), _ptr(y), _ptr(z), _ptr(h), n, float(support), _ptr(out),
+                                _stream(stream)))
+
+
+def domain_halo_mask(x, y, z, h, box, support, dom, P, self_rank, mask, stream=None):
+    """nl_domain_halo_mask: dom float32 CUDA tensor [P, 8] (nl_domain_box rows)."""
+    import torch
+    n = int(x.numel())
+    for name, t in (("x", x), ("y", y), ("z", z), ("h", h)):
+        _require(t, name, torch.float32, n)
+    _require(dom, "dom", torch.float32, 8 * int(P))
+    _require(mask, "mask", torch.int64, n)
+    b = make_box(box) if isinstance(box, dict) else box
+    _check(load().nl_domain_halo_mask(_ptr(x), _ptr(y), _ptr(z), _ptr(h), n, C.byref(b),
+                                      float(support), _ptr(dom), int(P), int(self_rank), _ptr(mask),
+                                      _stream(stream)))
+
+
+def domain_count(mask, P, counts, stream=None):
+    import torch
+    _require(mask, "mask", torch.int64, int(mask.numel()))
+    _require(counts, "counts", torch.int64, int(P))
+    _check(load().nl_domain_count(_ptr(mask), int(mask.numel()), int(P), _ptr(counts),
+                                  _stream(stream)))
+
+
+def domain_group(mask, P, offsets, idx, stream=None):
+    """nl_domain_group: offsets int64 CUDA tensor of P, idx int32 CUDA tensor."""
+    import torch
+    _require(mask, "mask", torch.int64, int(mask.numel()))
+    _require(offsets, "offsets", torch.int64, int(P))
+    if not (isinstance(idx, torch.Tensor) and idx.is_cuda and idx.dtype == torch.int32):
+        raise ValueError("idx must be an int32 CUDA tensor")
+    _check(load().nl_domain_group(_ptr(mask), int(mask.numel()), int(P), _ptr(offsets), _ptr(idx),
+                                  _stream(stream)))
