@@ -231,6 +231,47 @@ __device__ __forceinline__ float wrap_len(float d, float len)
     return d;
 }
 
+// ---------------------------------------------------------------------------
+// Two FP32 values in one 64-bit register for the packed arithmetic of sm_100
+// and later (add / sub / mul .rn.f32x2: each half rounded to nearest on its
+// own, exactly as the scalar __fadd_rn / __fsub_rn / __fmul_rn, without
+// contraction), so the canonical predicate keeps its bits.
+// ---------------------------------------------------------------------------
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pk2(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void unpk2(f32x2 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+__device__ __forceinline__ f32x2 sub2_rn(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ f32x2 add2_rn(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ f32x2 mul2_rn(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
 template <bool PER>
 __device__ __forceinline__ float pair_d2(const float4 &pi, const float4 &pj, const PerLen &L)
 {
@@ -243,6 +284,25 @@ __device__ __forceinline__ float pair_d2(const float4 &pi, const float4 &pj, con
         dz = wrap_len(dz, L.z);
     }
     return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+// Canonical d2 of two pairs at once: (xa, xb) - (xi, xi) etc. in packed
+// registers; the periodic wrap of each half is the scalar one.
+template <bool PER>
+__device__ __forceinline__ f32x2 pair_d2_x2(f32x2 jx, f32x2 jy, f32x2 jz, f32x2 ix, f32x2 iy,
+                                             f32x2 iz, const PerLen &L)
+{
+    f32x2 dx = sub2_rn(jx, ix), dy = sub2_rn(jy, iy), dz = sub2_rn(jz, iz);
+    if (PER) {
+        float a, b;
+        unpk2(dx, a, b);
+        dx = pk2(wrap_len(a, L.x), wrap_len(b, L.x));
+        unpk2(dy, a, b);
+        dy = pk2(wrap_len(a, L.y), wrap_len(b, L.y));
+        unpk2(dz, a, b);
+        dz = pk2(wrap_len(a, L.z), wrap_len(b, L.z));
+    }
+    return add2_rn(add2_rn(mul2_rn(dx, dx), mul2_rn(dy, dy)), mul2_rn(dz, dz));
 }
 
 template <bool PER>

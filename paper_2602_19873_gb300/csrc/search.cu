@@ -238,13 +238,19 @@ __device__ bool half_output(uint32_t cnt, const uint32_t *stJ, const uint8_t *st
 // Shared memory of one warp: the super-cluster's particles, a chunk of 32
 // consecutive octree nodes, the queue of candidate j-clusters, the particles
 // and boxes of the 4 j-clusters being tested, and the encoder window.
+// The tile operands are laid out for packed (two-pair) arithmetic: an i
+// particle as (x, x, y, y) and (z, z, r^2, r^2); the j particles of a lane's
+// two pairs a and b as (xa, xb, ya, yb) and (za, zb, ra^2, rb^2).  Squared
+// radii suffice: fl(max(ri, rj)^2) = max(fl(ri^2), fl(rj^2)), squaring being
+// monotone.
 template <int M, int MJ>
 struct SearchSmem {
-    float4 ip[kSC * M];            // i particles (x, y, z, h)
+    float4 ipA[kSC * M], ipB[kSC * M];  // i particles
     float4 nlo[32], nhi[32];       // node chunk
     int2 nrg[32];
     uint32_t jq[SR_QCAP];          // candidate j-clusters, ascending
-    float4 jp[4 * MJ];             // particles of the 4 j-clusters under test
+    float4 jpA[4 * MJ], jpB[4 * MJ];  // particles of the 4 j-clusters under test
+    float4 ilo[kSC], ihi[kSC];     // boxes of the 8 i-clusters
     uint32_t win[WIN_WORDS];
 };
 
@@ -289,8 +295,10 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
         const uint32_t vend = min((uint32_t)__float_as_int(a.nhi[vroot].w), a.nnodes);
 
         // i-cluster box of this lane's cluster (lane & 7)
-        const float4 ilo = a.clo[s * kSC + (lane & 7)];
-        const float4 ihi = a.chi[s * kSC + (lane & 7)];
+        if (lane < kSC) {
+            S.ilo[lane] = a.clo[s * kSC + lane];
+            S.ihi[lane] = a.chi[s * kSC + lane];
+        }
         // pruning particles base + lane + 32 t, staged as (x, y, z, r) for
         // the tile tests.  Dummies sit at infinity, which no open axis comes
         // near; on periodic systems they are flagged off as well (a point at
@@ -305,7 +313,9 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
         for (int t = 0; t < NPI; ++t) {
             const float4 p = a.pos[base + lane + 32 * t];
             const float r = __fmul_rn(a.support, p.w);
-            S.ip[lane + 32 * t] = make_float4(p.x, p.y, p.z, r);
+            const float rr = __fmul_rn(r, r);
+            S.ipA[lane + 32 * t] = make_float4(p.x, p.x, p.y, p.y);
+            S.ipB[lane + 32 * t] = make_float4(p.z, p.z, rr, rr);
             const bool real = p.x == p.x;
             qp[t] = real ? p : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
             qr[t] = real ? r : 0.f;
@@ -328,11 +338,25 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
 #pragma unroll
                     for (uint32_t jl = lane & 7; jl < (uint32_t)MJ; jl += 8) {
                         const float4 p = a.pos[Jl * MJ + jl];
-                        S.jp[grp * MJ + jl] = make_float4(p.x, p.y, p.z, __fmul_rn(a.support, p.w));
+                        const float r = __fmul_rn(a.support, p.w);
+                        // slot of the lane's pair (a, b) holding jl, and its half
+                        uint32_t slot = jl, half = 0;
+                        if constexpr (NP >= 2) {
+                            const uint32_t t = jl / JSTEP;
+                            slot = (jl - t * JSTEP) + (t >> 1) * 2u * JSTEP;
+                            half = t & 1u;
+                        }
+                        float *pa = reinterpret_cast<float *>(&S.jpA[grp * MJ + slot]);
+                        float *pb = reinterpret_cast<float *>(&S.jpB[grp * MJ + slot]);
+                        pa[half] = p.x;
+                        pa[2 + half] = p.y;
+                        pb[half] = p.z;
+                        pb[2 + half] = __fmul_rn(r, r);
                     }
                     // 4 j-clusters x 8 i-cluster boxes, one per lane: may some
                     // pair be neighbors?
-                    cand = boxes_near<PER>(ilo, ihi, a.jlo[Jl], a.jhi[Jl], box);
+                    cand = boxes_near<PER>(S.ilo[lane & 7], S.ihi[lane & 7], a.jlo[Jl], a.jhi[Jl],
+                                           box);
                 }
                 const uint32_t bal = __ballot_sync(0xffffffffu, cand);
                 __syncwarp();
@@ -345,19 +369,37 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
                     ttests += __popc(cm);
                     for (uint32_t bits = cm; bits; bits &= bits - 1u) {
                         const int k = __ffs(bits) - 1;  // candidate tiles only, ascending
-                        const uint32_t ii = base + k * M + II;
-                        const float4 pik = S.ip[k * M + II];
+                        const float4 iA = S.ipA[k * M + II], iB = S.ipB[k * M + II];
+                        // pair (i, j) is a self pair iff II - jl == delta
+                        const int delta = (int)(J * MJ) - (int)(base + k * M);
+                        bool hit = false;
+                        if constexpr (NP >= 2) {
+                            const f32x2 ix = pk2(iA.x, iA.y), iy = pk2(iA.z, iA.w);
+                            const f32x2 iz = pk2(iB.x, iB.y);
 #pragma unroll
-                        for (int t = 0; t < NP; ++t) {  // stops at the first hit
-                            const uint32_t jl = JJ0 + t * JSTEP;
-                            const float4 pj = S.jp[q * MJ + jl];
-                            const float d2 = pair_d2<PER>(pik, pj, box);
-                            const float r = fmaxf(pik.w, pj.w);
-                            if (__any_sync(0xffffffffu, (ii != J * MJ + jl) && d2 < __fmul_rn(r, r))) {
-                                mask |= 1u << k;
-                                break;
+                            for (int u = 0; u < NP / 2; ++u) {  // stops at the first hit
+                                const uint32_t slot = JJ0 + 2u * u * JSTEP;
+                                const float4 jA = S.jpA[q * MJ + slot], jB = S.jpB[q * MJ + slot];
+                                const f32x2 d2 = pair_d2_x2<PER>(pk2(jA.x, jA.y), pk2(jA.z, jA.w),
+                                                                 pk2(jB.x, jB.y), ix, iy, iz, box);
+                                float d2a, d2b;
+                                unpk2(d2, d2a, d2b);
+                                const int ca = (int)II - (int)slot, cb = ca - JSTEP;
+                                const bool h = (d2a < fmaxf(iB.z, jB.z) && ca != delta) ||
+                                               (d2b < fmaxf(iB.w, jB.w) && cb != delta);
+                                if (__any_sync(0xffffffffu, h)) {
+                                    hit = true;
+                                    break;
+                                }
                             }
+                        } else {
+                            const float4 jA = S.jpA[q * MJ + JJ0], jB = S.jpB[q * MJ + JJ0];
+                            const float d2 = pair_d2<PER>(make_float4(iA.x, iA.z, iB.x, 0.f),
+                                                          make_float4(jA.x, jA.z, jB.x, 0.f), box);
+                            hit = __any_sync(0xffffffffu, d2 < fmaxf(iB.z, jB.z) &&
+                                                              (int)II - (int)JJ0 != delta);
                         }
+                        if (hit) mask |= 1u << k;
                     }
                     if (mask) {
                         if (lane == 0 && cnt < a.stage_cap) {
