@@ -229,6 +229,24 @@ def converge_h(L, dev, d, params, start, stream):
     return h, info, (time.perf_counter() - t) * 1e3
 
 
+def time_h_iteration(H, dev, d, params, start, stream, reps):
+    """One warm-up and `reps` timed h iterations from `start`: the median,
+    spread and per-pass trace (list sizes and times) of the runs."""
+    converge_h(H, dev, d, params, start, stream)       # warm-up
+    runs = []
+    for _ in range(max(1, reps)):
+        h, info, ms = converge_h(H, dev, d, params, start, stream)
+        runs.append(ms)
+    trace = H.hiter_trace()
+    return h, {"ms": statistics.median(runs), "ms_min": min(runs), "ms_max": max(runs),
+               "runs": len(runs), "iterations": info["iterations"],
+               "rebuilds": info["rebuilds"], "unconverged": info["unconverged"],
+               "passes": [{"rebuilt": t["rebuilt"], "active_superclusters": t["active"],
+                           "unconverged": t["unconverged"], "entries": t["entries"],
+                           "computed_pairs": t["tiles"] * params.cluster * params.cluster,
+                           "ms": t["ms"]} for t in trace]}
+
+
 TRAIN_SEEDS = list(range(100, 108))
 TRAIN_N = 1 << 19
 
@@ -295,21 +313,32 @@ def run_native(args):
     hcache = os.path.join(__import__("tempfile").gettempdir(), "nlgb_workloads",
                           "hconv_%d_%d.npy" % (n, 4 + rank))
     learned = None
-    if args.reuse_h and os.path.exists(hcache):
+    if args.h_source == "generator":
+        # profiling runs: the generator's h (no iteration, no learned start)
+        hconv = dev["h"].clone()
+        hinfo, hms = {"iterations": None, "rebuilds": None, "unconverged": None}, None
+        plain = None
+    elif args.reuse_h and os.path.exists(hcache):
         hconv = torch.from_numpy(np.load(hcache)).cuda()
         hinfo, hms = {"iterations": None, "rebuilds": None, "unconverged": None}, None
+        plain = None
     else:
-        converge_h(H, dev, d, params, nl.NL_HSTART_PLAIN, stream)       # warm-up
-        hconv, hinfo, hms = converge_h(H, dev, d, params, nl.NL_HSTART_PLAIN, stream)
+        hconv, plain = time_h_iteration(H, dev, d, params, nl.NL_HSTART_PLAIN, stream,
+                                        args.h_reps)
+        hinfo, hms = plain, plain["ms"]
         np.save(hcache, hconv.cpu().numpy())
         if not args.no_learned:
             mlp, tinfo = train_mlp(params, stream, args.reuse_h)
             H.set_mlp(mlp)
-            converge_h(H, dev, d, params, nl.NL_HSTART_LEARNED, stream)  # warm-up
-            hl, linfo, lms = converge_h(H, dev, d, params, nl.NL_HSTART_LEARNED, stream)
-            learned = {"ms": lms, "iterations": linfo["iterations"], "rebuilds": linfo["rebuilds"],
-                       "unconverged": linfo["unconverged"], "training": tinfo,
-                       "speedup_vs_plain": hms / lms}
+            _, learned = time_h_iteration(H, dev, d, params, nl.NL_HSTART_LEARNED, stream,
+                                          args.h_reps)
+            learned["training"] = tinfo
+            learned["speedup_vs_plain"] = hms / learned["ms"]
+            cost = (tinfo.get("data_ms") or 0.0) + (tinfo.get("train_ms") or 0.0)
+            gain = hms - learned["ms"]
+            learned["break_even_runs"] = (cost / gain) if (cost > 0 and gain > 0) else None
+            learned["break_even_note"] = ("training cost (data generation + training, ms) over "
+                                          "the median time saved per h iteration of this system")
             H.set_mlp(None)
             mlp.free()
     H.free()
@@ -440,7 +469,8 @@ def run_native(args):
                                "compressed %s list" % (WORKLOAD, M, MJ, args.list),
                    "n": n, "cluster": params.cluster, "j_cluster": sizes["j_cluster"],
                    "leaf_bucket": params.leaf_bucket,
-                   "h": "iterated on the GPU to 200 +- 2 gather neighbors (plain start)",
+                   "h": ("iterated on the GPU to 200 +- 2 gather neighbors (plain start)"
+                         if args.h_source == "iterated" else "the generator's (not iterated)"),
                    "l2": "inputs larger than L2 (268 MB of positions), no flush",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "stages_ms": stages,
@@ -478,7 +508,8 @@ def run_native(args):
         "e2e": None if args.no_e2e else {
             "value": job_rate(n, ws, e_ms), "unit": UNIT,
             "h2d_bytes_per_step": 20 * n, "d2h_bytes_per_step": 4 * n},
-        "h_iteration": {"plain": {"ms": hms, "iterations": hinfo["iterations"],
+        "h_iteration": {"plain": plain if plain is not None else {
+                                  "ms": hms, "iterations": hinfo["iterations"],
                                   "rebuilds": hinfo["rebuilds"],
                                   "unconverged": hinfo["unconverged"]},
                         "learned": learned,
@@ -900,6 +931,11 @@ def main():
     ap.add_argument("--tile", default="8x8", choices=["8x8", "8x4", "16x8", "16x16", "4x4"],
                     help="i-cluster x j-cluster size of the single-system bench")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-h comparison")
+    ap.add_argument("--h-source", default="iterated", choices=["iterated", "generator"],
+                    help="smoothing lengths of the timed step: iterated to 200 +- 2 (the "
+                         "benchmark), or the generator's (short profiling runs)")
+    ap.add_argument("--h-reps", type=int, default=5,
+                    help="timed h iterations per start (median and spread reported)")
     ap.add_argument("--list", default="half", choices=["full", "half"],
                     help="full lists, or half lists (every cluster pair once; density workloads)")
     ap.add_argument("--workload", default=WORKLOAD,

@@ -274,6 +274,25 @@ nl_status nl_iterate_h(nl_list *nl, const float *x, const float *y, const float 
                        int32_t max_iter, float margin, int32_t start, uint8_t *converged,
                        nl_hiter_info *info, void *stream);
 
+/* Per-pass record of the last nl_iterate_h / nl_iterate_h_batch on this
+ * list: whether the pass rebuilt the list first, the super-clusters it
+ * counted (all on the first pass, then the ones with unconverged particles),
+ * the particles still outside the window after it, the list's entries and
+ * computed cluster pairs (tiles) at that pass, and its host wall time in ms
+ * (every pass ends with a stream synchronisation).  Copies
+ * min(cap, passes) records; *count = passes. */
+typedef struct {
+    int32_t rebuilt;
+    int32_t pad0;
+    int64_t active;
+    int64_t unconverged;
+    int64_t entries;
+    int64_t tiles;
+    float ms;
+    int32_t pad1;
+} nl_hiter_step;
+nl_status nl_get_hiter_trace(const nl_list *nl, nl_hiter_step *steps, int32_t cap, int32_t *count);
+
 /* Allocation-free SFC ordering.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory where they
  * need the order: a latency-critical simulation loop that cannot afford

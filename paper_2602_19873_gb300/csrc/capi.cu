@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstddef>
 #include <cstdlib>
+#include <chrono>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -118,6 +119,7 @@ struct nl_list {
     int any_per = 0;
     unsigned long long list_bytes = 0, n_entries = 0, n_tiles = 0;
     unsigned long long node_visits = 0, leaf_visits = 0, j_examined = 0, tile_tests = 0;
+    std::vector<nl_hiter_step> hiter_trace;  // one entry per count pass of the last h iteration
     uint32_t stage_cap = kStageCap0;
     int stage_grown = 0;
     int64_t n_prepared = 0;
@@ -1345,7 +1347,12 @@ static nl_status do_iterate_h(nl_list *nl, const float *x, const float *y, const
     bool rebuild = true, first = true;
     int iters = 0, rebuilds = 0;
     unsigned int words[4] = {0, 0, 0, 0};
+    nl->hiter_trace.clear();
     for (; iters < max_iter;) {
+        const auto t_iter = std::chrono::steady_clock::now();
+        nl_hiter_step step{};
+        step.rebuilt = rebuild ? 1 : 0;
+        step.active = first ? (int64_t)nsc : (int64_t)words[2];
         if (rebuild) {
             CK(launch_hsearch(npad, hs.hq, hs.hhi, hs.conv, margin, hs.hcap_sys, T, hs.hs, s));
             CK(launch_pos_h(npad, hs.hs, nl->pos.as<float4>(), s));
@@ -1374,6 +1381,11 @@ static nl_status do_iterate_h(nl_list *nl, const float *x, const float *y, const
         CK(launch_active_list(nsc, hs, s));
         CK(cudaMemcpyAsync(words, hs.words, 16, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
+        step.unconverged = words[0];
+        step.entries = (int64_t)nl->n_entries;
+        step.tiles = (int64_t)nl->n_tiles;
+        step.ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t_iter).count();
+        nl->hiter_trace.push_back(step);
         if (words[0] == 0) break;
         rebuild = words[1] != 0;
     }
@@ -1787,6 +1799,16 @@ nl_status nl_nearest_distance(const nl_list *cnl, float *dist, void *stream)
     a.out0 = dist;
     CK(run_pass(nl, a, PASS_MIN, s));
     if (half) CK(launch_half_finish(a, PASS_MIN, nl->npad, s));
+    return NL_OK;
+}
+
+nl_status nl_get_hiter_trace(const nl_list *nl, nl_hiter_step *steps, int32_t cap, int32_t *count)
+{
+    if (!nl || !count || cap < 0 || (cap > 0 && !steps))
+        return fail(NL_ERR_ARG, "nl_get_hiter_trace: bad argument");
+    const int32_t k = (int32_t)nl->hiter_trace.size();
+    for (int32_t i = 0; i < k && i < cap; ++i) steps[i] = nl->hiter_trace[(size_t)i];
+    *count = k;
     return NL_OK;
 }
 

@@ -94,6 +94,7 @@ _SIGS = {
     "nl_mlp_predict": (C.c_int, [P, P, C.c_int64, P, P]),
     "nl_set_mlp": (C.c_int, [P, P]),
     "nl_probe_fp32_rate": (C.c_int, [C.c_int32, C.c_int32, P, P, P]),
+    "nl_get_hiter_trace": (C.c_int, [P, P, C.c_int32, P]),
     "nl_sfc_keys": (C.c_int, [P, P, P, P, C.c_int64, P, C.c_int32, C.c_float, P, P]),
     "nl_key_histogram": (C.c_int, [P, C.c_int64, C.c_uint64, C.c_int32, C.c_int32, P, P]),
     "nl_domain_owner_mask": (C.c_int, [P, C.c_int64, P, C.c_int32, P, P]),
@@ -112,6 +113,12 @@ NL_FORCE_SPH_PRESSURE, NL_FORCE_LJ, NL_FORCE_LJ_COULOMB = 0, 1, 2
 
 class nl_hiter_info(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("rebuilds", C.c_int32), ("unconverged", C.c_int64)]
+
+
+class nl_hiter_step(C.Structure):
+    _fields_ = [("rebuilt", C.c_int32), ("pad0", C.c_int32), ("active", C.c_int64),
+                ("unconverged", C.c_int64), ("entries", C.c_int64), ("tiles", C.c_int64),
+                ("ms", C.c_float), ("pad1", C.c_int32)]
 
 STAGES = ["keys", "sort", "permute", "octree", "search", "assemble", "pass_gather", "pass"]
 
@@ -445,6 +452,15 @@ class NeighborList:
     def refresh_positions(self, x, y, z, max_disp=None, stream=None):
         _check(load().nl_refresh_positions(self.handle, _ptr(x), _ptr(y), _ptr(z), _ptr(max_disp),
                                            _stream(stream)))
+
+    def hiter_trace(self):
+        """Per-pass records of the last h iteration (nl_get_hiter_trace)."""
+        cnt = C.c_int32()
+        _check(load().nl_get_hiter_trace(self.handle, None, 0, C.byref(cnt)))
+        arr = (nl_hiter_step * max(1, cnt.value))()
+        _check(load().nl_get_hiter_trace(self.handle, arr, cnt.value, C.byref(cnt)))
+        return [{f: getattr(arr[i], f) for f, _ in nl_hiter_step._fields_ if not f.startswith("pad")}
+                for i in range(cnt.value)]
 
     def sizes(self):
         s = nl_sizes()

@@ -63,7 +63,7 @@ def test_binding_structs_match_the_header(tmp_path):
 
     from paper_2602_19873_gb300 import nl
     structs = {"nl_box": nl.nl_box, "nl_params": nl.nl_params, "nl_sizes": nl.nl_sizes,
-               "nl_hiter_info": nl.nl_hiter_info}
+               "nl_hiter_info": nl.nl_hiter_info, "nl_hiter_step": nl.nl_hiter_step}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "nl.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (name, name))
