@@ -62,6 +62,41 @@ __device__ __forceinline__ float spline_dw(float q)
     return q < 1.f ? inner : (q < 2.f ? outer : 0.f);
 }
 
+// Decode the next 32 entries of a record (one per lane; Sec. II-B): the
+// block mask is read at nibble offset pos with a funnel shift, each lane
+// finds its info nibble by popcount and its data nibbles by a warp scan of
+// data lengths, and a warp scan of the differences rebuilds the j-cluster
+// indices from prevJ.  Advances pos and prevJ; uncompressed records hold
+// the u32 indices (entry t of lane).
+__device__ __forceinline__ uint32_t decode_block(const uint32_t *body, int compress, uint32_t t,
+                                                 bool valid, uint32_t &pos, uint32_t &prevJ)
+{
+    const unsigned lane = lane_id();
+    uint32_t J;
+    if (compress) {
+        const uint8_t *bodyb = reinterpret_cast<const uint8_t *>(body);
+        const uint32_t w0 = body[pos >> 3];
+        const uint32_t w1 = (pos & 7u) ? body[(pos >> 3) + 1] : 0u;
+        const uint32_t bm = __funnelshift_r(w0, w1, (pos & 7u) * 4u);
+        const bool bit = (bm >> lane) & 1u;
+        const uint32_t nbits = __popc(bm);
+        uint32_t info = bit ? get_nibble(bodyb, pos + 8 + __popc(bm & lanemask_lt())) : 0u;
+        uint32_t ndat = (bit && info < 8u) ? info + 1u : 0u;
+        uint32_t incl = warp_incl_scan(ndat);
+        uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        uint32_t pd = pos + 8 + nbits + incl - ndat;
+        uint32_t v = 0;
+        for (uint32_t q = 0; q < ndat; ++q) v = (v << 4) | get_nibble(bodyb, pd + q);
+        uint32_t d = !bit ? 1u : (info >= 8u ? info - 6u : v);
+        J = prevJ + warp_incl_scan(d);
+        pos += 8 + nbits + tot;
+    } else {
+        J = valid ? body[t] : 0u;
+    }
+    prevJ = __shfl_sync(0xffffffffu, J, 31);
+    return J;
+}
+
 // Accumulators per i-cluster.  Floating sums are two-level: terms of one
 // block of 32 list entries go to a plain FP32 partial (b*), and each
 // partial is added to the running sum with Kahan compensation (density)
@@ -189,7 +224,6 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
     // fixed-point scale of the half-list density (2^ex)
     const float hscale = (HL && KIND == PASS_DENSITY) ? __int_as_float((half_scale_exp(a.st->m_absmax) + 127) << 23) : 0.f;
     const unsigned lane = lane_id();
-    const unsigned lt = lanemask_lt();
     const uint32_t II = lane % M;
     const uint32_t JJ0 = (lane / M) % MJ;
     // lanes that hold a distinct (i, j) pair; for M x MJ = 4 x 4 lanes 16..31 repeat
@@ -254,34 +288,13 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
         const uint32_t cnt = roff == kBadRecord ? 0u : rec[0];
         const uint8_t *masks = reinterpret_cast<const uint8_t *>(rec + 1);
         const uint32_t *body = rec + 1 + ((cnt + 3u) >> 2);
-        const uint8_t *bodyb = reinterpret_cast<const uint8_t *>(body);
         uint32_t pos = 0;
         uint32_t prevJ = 0xffffffffu;
 
         for (uint32_t b0 = 0; b0 < cnt; b0 += 32) {
             const uint32_t t = b0 + lane;
             const bool valid = t < cnt;
-            uint32_t J;
-            if (a.compress) {
-                const uint32_t w0 = body[pos >> 3];
-                const uint32_t w1 = (pos & 7u) ? body[(pos >> 3) + 1] : 0u;
-                const uint32_t bm = __funnelshift_r(w0, w1, (pos & 7u) * 4u);
-                const bool bit = (bm >> lane) & 1u;
-                const uint32_t nbits = __popc(bm);
-                uint32_t info = bit ? get_nibble(bodyb, pos + 8 + __popc(bm & lt)) : 0u;
-                uint32_t ndat = (bit && info < 8u) ? info + 1u : 0u;
-                uint32_t incl = warp_incl_scan(ndat);
-                uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
-                uint32_t pd = pos + 8 + nbits + incl - ndat;
-                uint32_t v = 0;
-                for (uint32_t q = 0; q < ndat; ++q) v = (v << 4) | get_nibble(bodyb, pd + q);
-                uint32_t d = !bit ? 1u : (info >= 8u ? info - 6u : v);
-                J = prevJ + warp_incl_scan(d);
-                pos += 8 + nbits + tot;
-            } else {
-                J = valid ? body[t] : 0u;
-            }
-            prevJ = __shfl_sync(0xffffffffu, J, 31);
+            const uint32_t J = decode_block(body, a.compress, t, valid, pos, prevJ);
             const uint32_t mk = valid ? masks[t] : 0u;
             const uint32_t nb = min(32u, cnt - b0);
             acc_begin_block<KIND>(acc);
