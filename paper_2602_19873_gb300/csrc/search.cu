@@ -239,13 +239,14 @@ __device__ bool half_output(uint32_t cnt, const uint32_t *stJ, const uint8_t *st
 // consecutive octree nodes, the queue of candidate j-clusters, the particles
 // and boxes of the 4 j-clusters being tested, and the encoder window.
 // The tile operands are laid out for packed (two-pair) arithmetic: an i
-// particle as (x, x, y, y) and (z, z, r^2, r^2); the j particles of a lane's
-// two pairs a and b as (xa, xb, ya, yb) and (za, zb, ra^2, rb^2).  Squared
-// radii suffice: fl(max(ri, rj)^2) = max(fl(ri^2), fl(rj^2)), squaring being
-// monotone.
+// particle as (x, y, z, r^2), one 16-byte load per tile (the tile tests are
+// bound by shared-memory bandwidth); the j particles of a lane's two pairs a
+// and b as (xa, xb, ya, yb) and (za, zb, ra^2, rb^2), loaded once per
+// j-cluster.  Squared radii suffice: fl(max(ri, rj)^2) = max(fl(ri^2),
+// fl(rj^2)), squaring being monotone.
 template <int M, int MJ>
 struct SearchSmem {
-    float4 ipA[kSC * M], ipB[kSC * M];  // i particles
+    float4 ip[kSC * M];            // i particles
     float4 nlo[32], nhi[32];       // node chunk
     int2 nrg[32];
     uint32_t jq[SR_QCAP];          // candidate j-clusters, ascending
@@ -314,8 +315,7 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
             const float4 p = a.pos[base + lane + 32 * t];
             const float r = __fmul_rn(a.support, p.w);
             const float rr = __fmul_rn(r, r);
-            S.ipA[lane + 32 * t] = make_float4(p.x, p.x, p.y, p.y);
-            S.ipB[lane + 32 * t] = make_float4(p.z, p.z, rr, rr);
+            S.ip[lane + 32 * t] = make_float4(p.x, p.y, p.z, rr);
             const bool real = p.x == p.x;
             qp[t] = real ? p : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
             qr[t] = real ? r : 0.f;
@@ -364,39 +364,40 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
                     const uint32_t cm = (bal >> (8 * q)) & 0xffu;
                     if (!cm) continue;
                     const uint32_t J = S.jq[b + q];
-                    // exact FP32 test of the candidate M x MJ tiles
+                    // exact FP32 test of the candidate M x MJ tiles; the j
+                    // operands of the first two pairs stay in registers
                     uint32_t mask = 0;
                     ttests += __popc(cm);
+                    const float4 jA0 = S.jpA[q * MJ + JJ0], jB0 = S.jpB[q * MJ + JJ0];
                     for (uint32_t bits = cm; bits; bits &= bits - 1u) {
                         const int k = __ffs(bits) - 1;  // candidate tiles only, ascending
-                        const float4 iA = S.ipA[k * M + II], iB = S.ipB[k * M + II];
+                        const float4 pi = S.ip[k * M + II];
                         // pair (i, j) is a self pair iff II - jl == delta
                         const int delta = (int)(J * MJ) - (int)(base + k * M);
                         bool hit = false;
                         if constexpr (NP >= 2) {
-                            const f32x2 ix = pk2(iA.x, iA.y), iy = pk2(iA.z, iA.w);
-                            const f32x2 iz = pk2(iB.x, iB.y);
+                            const f32x2 ix = pk2(pi.x, pi.x), iy = pk2(pi.y, pi.y);
+                            const f32x2 iz = pk2(pi.z, pi.z);
 #pragma unroll
                             for (int u = 0; u < NP / 2; ++u) {  // stops at the first hit
                                 const uint32_t slot = JJ0 + 2u * u * JSTEP;
-                                const float4 jA = S.jpA[q * MJ + slot], jB = S.jpB[q * MJ + slot];
+                                const float4 jA = u == 0 ? jA0 : S.jpA[q * MJ + slot];
+                                const float4 jB = u == 0 ? jB0 : S.jpB[q * MJ + slot];
                                 const f32x2 d2 = pair_d2_x2<PER>(pk2(jA.x, jA.y), pk2(jA.z, jA.w),
                                                                  pk2(jB.x, jB.y), ix, iy, iz, box);
                                 float d2a, d2b;
                                 unpk2(d2, d2a, d2b);
                                 const int ca = (int)II - (int)slot, cb = ca - JSTEP;
-                                const bool h = (d2a < fmaxf(iB.z, jB.z) && ca != delta) ||
-                                               (d2b < fmaxf(iB.w, jB.w) && cb != delta);
+                                const bool h = (d2a < fmaxf(pi.w, jB.z) && ca != delta) ||
+                                               (d2b < fmaxf(pi.w, jB.w) && cb != delta);
                                 if (__any_sync(0xffffffffu, h)) {
                                     hit = true;
                                     break;
                                 }
                             }
                         } else {
-                            const float4 jA = S.jpA[q * MJ + JJ0], jB = S.jpB[q * MJ + JJ0];
-                            const float d2 = pair_d2<PER>(make_float4(iA.x, iA.z, iB.x, 0.f),
-                                                          make_float4(jA.x, jA.z, jB.x, 0.f), box);
-                            hit = __any_sync(0xffffffffu, d2 < fmaxf(iB.z, jB.z) &&
+                            const float d2 = pair_d2<PER>(pi, make_float4(jA0.x, jA0.z, jB0.x, 0.f), box);
+                            hit = __any_sync(0xffffffffu, d2 < fmaxf(pi.w, jB0.z) &&
                                                               (int)II - (int)JJ0 != delta);
                         }
                         if (hit) mask |= 1u << k;
