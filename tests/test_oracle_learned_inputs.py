@@ -97,3 +97,25 @@ def test_axis_features_follow_an_exchange_of_axes(orc):
     n = len(xs)
     last = (n - 1) // 8
     assert math.isclose(X[last, 6], math.log((n - 8 * last) / 8.0), abs_tol=1e-12)
+
+
+def test_region_features_of_a_line_of_super_clusters(orc):
+    """Twelve super-clusters of M = 4 (32 particles each) on a line: super-
+    cluster s spans x in [s, s + 0.25] at y = z = 0.5.  Its own box is 0.25
+    wide; the 8 super-clusters around it are s-3 .. s+4 clipped to 0 .. 11,
+    the 64 around it all twelve, so the region features are known by hand."""
+    nsc = 12
+    j = np.arange(32, dtype=np.float64)
+    x = np.concatenate([s + 0.25 * j / 31.0 for s in range(nsc)]).astype(np.float32)
+    y = np.full(len(x), 0.5, np.float32)
+    box = {"lo": np.zeros(3, np.float32), "hi": np.full(3, 16.0, np.float32),
+           "periodic": np.zeros(3, np.int32)}
+    X, e64 = orc.mlp_features(x, y, y.copy(), box, 4)
+    assert np.allclose(e64, 0.25, rtol=0, atol=1e-12)
+    # s: (first, last) super-cluster of the 8 around it
+    spans = {0: (0, 4), 1: (0, 5), 3: (0, 7), 4: (1, 8), 6: (3, 10), 8: (5, 11), 10: (7, 11),
+             11: (8, 11)}
+    for s, (a, b) in spans.items():
+        for c in range(8 * s, 8 * s + 8):
+            assert abs(X[c, 1] - math.log((b - a + 0.25) / 0.25)) < 1e-12, (s, c)
+            assert abs(X[c, 2] - math.log(11.25 / 0.25)) < 1e-12, (s, c)

@@ -11,7 +11,9 @@ import pytest
 from oracle import api as orc_api
 
 import test_oracle_codec as tcodec
+import test_oracle_counts as tcounts
 import test_oracle_keys as tkeys
+import test_oracle_learned_inputs as tlearn
 import test_oracle_neighbors as tneigh
 import test_oracle_sph as tsph
 
@@ -82,6 +84,26 @@ MUTANTS = [
      "if (u->idx != v->idx) return u->idx < v->idx ? -1 : 1;",
      "if (u->idx != v->idx) return u->idx < v->idx ? 1 : -1;",
      lambda orc: tkeys.test_sort_is_stable_by_original_index(orc)),
+    ("feature window of 8 super-clusters shifted by one",
+     "for (int64_t t = s - 3; t < s + 5; ++t)",
+     "for (int64_t t = s - 4; t < s + 4; ++t)",
+     lambda orc: tlearn.test_region_features_of_a_line_of_super_clusters(orc)),
+    ("feature length floor dropped",
+     "return e > floor_len ? e : floor_len;",
+     "return e;",
+     lambda orc: tlearn.test_features_of_hand_built_system(orc)),
+    ("target mean over the cluster's M slots instead of its real particles",
+     "y[c] = k ? log(s / (double)k / e64[c / 8]) : 0.0;",
+     "y[c] = k ? log(s / (double)M / e64[c / 8]) : 0.0;",
+     lambda orc: tlearn.test_targets_of_hand_built_system(orc)),
+    ("h at count between the (k+1)-th and (k+2)-th neighbor",
+     "float dk1 = hp[0], dk = hp[1];",
+     "float dk1 = hp[0] * 1.5f, dk = hp[0];",
+     lambda orc: tcounts.test_h_at_count_has_exactly_k_neighbors(orc, "uniform", 40)),
+    ("computed pairs count M x M for M x MJ tiles",
+     "return s * (int64_t)cluster * (int64_t)jcluster;",
+     "return s * (int64_t)cluster * (int64_t)cluster;",
+     lambda orc: tcounts.test_computed_pairs_all_in_range_and_isolated(orc, 8, 4)),
     ("nearest keeps the largest distance",
      "if (r < best) best = r;",
      "if (r > best || best == INFINITY) best = r;",
