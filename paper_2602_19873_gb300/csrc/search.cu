@@ -322,6 +322,14 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
             qok |= real ? 1u << t : 0u;
         }
 
+        // open systems, two pruning particles per lane: their coordinates as
+        // packed pairs for the node tests
+        f32x2 qx2 = 0, qy2 = 0, qz2 = 0;
+        if constexpr (!PER && NPI == 2) {
+            qx2 = pk2(qp[0].x, qp[1].x);
+            qy2 = pk2(qp[0].y, qp[1].y);
+            qz2 = pk2(qp[0].z, qp[1].z);
+        }
         uint32_t cnt = 0, tiles = 0, nvis = 0, lvis = 0, jex = 0, ttests = 0, qn = 0;
         // the half search takes only j-clusters from its own first one on
         int lastJ = HALF ? (int)(base / MJ) - 1 : -1;
@@ -441,9 +449,33 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
             }
             ++nvis;
             bool near = false;
+            if constexpr (!PER && NPI == 2) {
+                // the gap of each particle to the node box per axis, packed
+                float g[3][2];
+                const f32x2 lo2[3] = {pk2(nlo.x, nlo.x), pk2(nlo.y, nlo.y), pk2(nlo.z, nlo.z)};
+                const f32x2 hi2[3] = {pk2(nhi.x, nhi.x), pk2(nhi.y, nhi.y), pk2(nhi.z, nhi.z)};
+                const f32x2 q2[3] = {qx2, qy2, qz2};
 #pragma unroll
-            for (int t = 0; t < NPI; ++t)
-                near |= (!PER || ((qok >> t) & 1u)) && point_near<PER>(qp[t], qr[t], nlo, nhi, box);
+                for (int ax = 0; ax < 3; ++ax) {
+                    float a0, a1, b0, b1;
+                    unpk2(sub2_rn(lo2[ax], q2[ax]), a0, a1);
+                    unpk2(sub2_rn(q2[ax], hi2[ax]), b0, b1);
+                    g[ax][0] = fmaxf(0.f, fmaxf(a0, b0));
+                    g[ax][1] = fmaxf(0.f, fmaxf(a1, b1));
+                }
+                const f32x2 gx = pk2(g[0][0], g[0][1]), gy = pk2(g[1][0], g[1][1]);
+                const f32x2 gz = pk2(g[2][0], g[2][1]);
+                const f32x2 d2 = add2_rn(add2_rn(mul2_rn(gx, gx), mul2_rn(gy, gy)), mul2_rn(gz, gz));
+                const float ra = fmaxf(qr[0], nlo.w), rb = fmaxf(qr[1], nlo.w);
+                float d2a, d2b, rra, rrb;
+                unpk2(d2, d2a, d2b);
+                unpk2(mul2_rn(pk2(ra, rb), pk2(ra, rb)), rra, rrb);
+                near = d2a <= rra || d2b <= rrb;
+            } else {
+#pragma unroll
+                for (int t = 0; t < NPI; ++t)
+                    near |= (!PER || ((qok >> t) & 1u)) && point_near<PER>(qp[t], qr[t], nlo, nhi, box);
+            }
             if (!__any_sync(0xffffffffu, near)) {
                 v = skip > v ? skip : v + 1;  // always advances
                 continue;
