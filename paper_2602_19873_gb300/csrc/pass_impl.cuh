@@ -155,8 +155,7 @@ template <int MJ, int KIND, bool HL = false>
 constexpr size_t pass_smem_per_warp()
 {
     return (size_t)32 * MJ * (sizeof(float4) + ((KIND == PASS_DENSITY || KIND == PASS_SPH || KIND == PASS_LJC) ? sizeof(float2) : 0)) +
-           (HL ? (size_t)kSC * MJ * sizeof(float) : 0) +
-           ((HL && KIND == PASS_DENSITY) ? (size_t)2 * kSC * 32 * sizeof(float) : 0);
+           (HL ? (size_t)kSC * MJ * sizeof(float) : 0);
 }
 
 // Resident blocks per SM the register budget is cut for: the scalar passes
@@ -222,9 +221,6 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
     float4 *sp = reinterpret_cast<float4 *>(pass_smem + (threadIdx.x >> 5) * pass_smem_per_warp<MJ, KIND, HL>());
     float2 *sa = reinterpret_cast<float2 *>(sp + 32 * MJ);
     float *smi = AUX ? reinterpret_cast<float *>(sa + 32 * MJ) : reinterpret_cast<float *>(sp + 32 * MJ);
-    // half-list density: the Kahan running sums per i-cluster and lane live in
-    // shared memory (touched once per 32 entries), not in registers
-    float *skv = smi + kSC * MJ, *skc = skv + kSC * 32;
     // fixed-point scale of the half-list density (2^ex)
     const float hscale = (HL && KIND == PASS_DENSITY) ? __int_as_float((half_scale_exp(a.st->m_absmax) + 127) << 23) : 0.f;
     const unsigned lane = lane_id();
@@ -276,7 +272,6 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
         for (int k = 0; k < kSC; ++k) {
             if constexpr (KIND == PASS_DENSITY) {
                 acc.v[k] = 0.f; acc.c[k] = 0.f;
-                if constexpr (HL) { skv[k * 32 + lane] = 0.f; skc[k * 32 + lane] = 0.f; }
             } else if constexpr (KIND == PASS_COUNT) {
                 acc.v[k] = 0;
             } else if constexpr (KIND == PASS_MIN) {
@@ -550,18 +545,7 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                     }
                 }
             }
-            if constexpr (HL && KIND == PASS_DENSITY) {
-#pragma unroll
-                for (int k = 0; k < kSC; ++k) {
-                    const float v = skv[k * 32 + lane], c = skc[k * 32 + lane];
-                    const float y = __fsub_rn(acc.b[k], c);
-                    const float t = __fadd_rn(v, y);
-                    skc[k * 32 + lane] = __fsub_rn(__fsub_rn(t, v), y);
-                    skv[k * 32 + lane] = t;
-                }
-            } else {
-                acc_end_block<KIND>(acc);
-            }
+            acc_end_block<KIND>(acc);
         }
 
         // combine lanes holding the same i particle, write in caller order
@@ -570,10 +554,7 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
 #pragma unroll
             for (int o = M; o < 32; o <<= 1) {
                 if constexpr (KIND == PASS_DENSITY) {
-                    if (o == M) {
-                        if constexpr (HL) acc.v[k] = __fsub_rn(skv[k * 32 + lane], skc[k * 32 + lane]);
-                        else acc.v[k] = __fsub_rn(acc.v[k], acc.c[k]);
-                    }
+                    if (o == M) acc.v[k] = __fsub_rn(acc.v[k], acc.c[k]);
                     acc.v[k] += __shfl_xor_sync(0xffffffffu, acc.v[k], o);
                 } else if constexpr (KIND == PASS_COUNT) {
                     acc.v[k] += __shfl_xor_sync(0xffffffffu, acc.v[k], o);
