@@ -33,14 +33,13 @@ N_FULL = 1 << 24
 ALU_OPS_PER_PAIR_SEARCH = 9      # predicate: 3 sub, 3 mul, 2 add, 1 compare (non-periodic)
 ALU_OPS_PER_DENSITY_SIDE = 12    # gather pair in range: square root, scale, spline, weighted add
 ALGO_BYTES_PER_PARTICLE = 145    # keygen 20 + sort 24 + permute 49 + octree 2 + search 19 + density 31
-# DRAM bytes (read + write) of one k_search launch per particle, from ncu
-# captures on this generator at 2^21 particles (8x8 clusters, leaf bucket 256,
-# cluster-box round then exact tile tests), scaled by the particle count (the
-# traffic grows with the particles).  "full": the half search with transposed
-# tuples for full lists, 45.1 MB + 12.7 MB; "half": the same walk storing half
-# lists (tile tests over the set mask bits), 44.9 MB + 0.7 MB.  Valid for those
-# kernel versions only; a list kind without a capture reports no traffic.
-SEARCH_DRAM_BYTES_PER_PARTICLE = {"full": 57.8e6 / 2097152, "half": 45.5e6 / 2097152}
+# DRAM bytes (read + write) of one k_search launch per particle, from an ncu
+# capture on this generator at 2^21 particles (8x8 clusters, leaf bucket 256,
+# half list: packed tile and node tests), 44.9 MB + 0.9 MB, scaled by the
+# particle count (the traffic grows with the particles).  Valid for that kernel
+# version only; a list kind without a capture of the current kernel reports no
+# traffic.
+SEARCH_DRAM_BYTES_PER_PARTICLE = {"half": 45.8e6 / 2097152}
 
 
 def peaks():
