@@ -91,3 +91,22 @@ def test_iteration_cap_reports_not_converged():
     assert info["status"] == 6 and info["iterations"] == 1
     assert info["unconverged"] == int((conv == 0).sum()) > 0
     L.free()
+
+
+def test_iteration_trace_is_consistent():
+    """nl_get_hiter_trace: one record per count pass; the first pass counts
+    every super-cluster after a rebuild, later ones only the unconverged
+    ones, the last leaves none unconverged, and the rebuilt passes are the
+    iteration's rebuilds."""
+    d = wl.plummer(30001, n_spheres=4, seed=205, n_target=100)
+    L, h, conv, info = _iterate(d, 100.0, 2.0, nl.NL_HSTART_PLAIN)
+    assert info["status"] == 0
+    tr = L.hiter_trace()
+    assert len(tr) == info["iterations"]
+    assert sum(t["rebuilt"] for t in tr) == info["rebuilds"]
+    nsc = L.sizes()["n_superclusters"]
+    assert tr[0]["rebuilt"] == 1 and tr[0]["active"] == nsc
+    assert all(t["active"] <= nsc and t["entries"] > 0 and t["tiles"] >= t["entries"] for t in tr)
+    assert tr[-1]["unconverged"] == 0 and all(t["unconverged"] > 0 for t in tr[:-1])
+    assert all(t["ms"] > 0 for t in tr)
+    L.free()
