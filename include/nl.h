@@ -118,7 +118,9 @@ typedef struct {
 /* Builds a new list (Sec. II-A, Listing "build"): keys, sort, clusters,
  * octree, cluster-pair search, encoding.  x,y,z,h: n device floats (caller
  * order).  On success *out owns the list; on failure *out is NULL.
- * Synchronises `stream` twice (validation + size word, final status). */
+ * Synchronises `stream` twice (validation + size word, final status).
+ * NL_ERR_TIMEOUT if a tile of the key sort waited in vain (a bounded wait)
+ * for the counts of the tiles before it; nothing of the list is kept. */
 nl_status nl_build(const float *x, const float *y, const float *z, const float *h, int64_t n,
                    const nl_box *box, const nl_params *p, void *stream, nl_list **out);
 
@@ -305,7 +307,7 @@ nl_status nl_get_hiter_trace(const nl_list *nl, nl_hiter_step *steps, int32_t ca
  * x, y, z, h: n device floats (caller order), validated as in nl_build;
  * keys (n uint64) and perm (n uint32) are device arrays owned by the caller.
  * Scratch comes from a fixed device array inside the library (about
- * 12.3 MB, held by every GPU that loads the library until exit); nothing is
+ * 14.7 MB, held by every GPU that loads the library until exit); nothing is
  * allocated.  The first call made with a device current looks up that
  * array's address on that device (cudaGetSymbolAddress); make that first call
  * before any stream capture begins.  Concurrent calls that overlap on

@@ -279,6 +279,8 @@ nl_status read_status(nl_list *nl, cudaStream_t s)
 {
     CK(cudaMemcpyAsync(nl->hst, nl->status.p, sizeof(Status), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (nl->hst->sort_stall)
+        return fail(NL_ERR_TIMEOUT, "a radix-sort look-back gave up its bounded wait; rebuild");
     return NL_OK;
 }
 
@@ -404,15 +406,18 @@ nl_status do_prep(nl_list *nl, const float *x, const float *y, const float *z, c
 
     // 1. keys (+ validation), 2. stable sort, 3. permute + cluster boxes
     CK(nl->mark(0, s));
+    // the key kernel also counts the sort's digits (scratch cleared first)
+    CK(radix_sort_clear(nl->hist.as<uint32_t>(), N, 3 * kKeyBits, s));
     CK(launch_keys_batch(n, x, y, z, h, T, p->support, p->key, nl->keys.as<uint64_t>(),
-                         nl->vals.as<uint32_t>(), dst, s));
+                         nl->vals.as<uint32_t>(), dst, nl->hist.as<uint32_t>(), s));
     CK(nl->mark(1, s));
     CK(radix_sort_pairs(nl->keys.as<uint64_t>(), nl->vals.as<uint32_t>(),
                         nl->keys_alt.as<uint64_t>(), nl->vals_alt.as<uint32_t>(), N,
-                        3 * kKeyBits, nl->hist.as<uint32_t>(), s));
+                        3 * kKeyBits, nl->hist.as<uint32_t>(), &dst->sort_stall, s, true));
     CK(radix_sort_by_system(nl->keys.as<uint64_t>(), nl->vals.as<uint32_t>(),
                             nl->keys_alt.as<uint64_t>(), nl->vals_alt.as<uint32_t>(), N,
-                            nl->sys_off.as<uint32_t>(), (uint32_t)nsys, nl->hist.as<uint32_t>(), s));
+                            nl->sys_off.as<uint32_t>(), (uint32_t)nsys, nl->hist.as<uint32_t>(),
+                            &dst->sort_stall, s));
     CK(nl->mark(2, s));
     CK(launch_permute(npad, M, MJ, T, nl->vals.as<uint32_t>(), x, y, z, h, p->support,
                       nl->pos.as<float4>(), nl->perm_pad.as<uint32_t>(), nl->clo.as<float4>(),
@@ -622,7 +627,7 @@ nl_status do_search_half(nl_list *nl, cudaStream_t s)
                             bits >= 64 ? ~0ull : (1ull << bits) - 1ull, s));
         CK(radix_sort_pairs(nl->tkey.as<uint64_t>(), nl->tval.as<uint32_t>(),
                             nl->tkey_alt.as<uint64_t>(), nl->tval_alt.as<uint32_t>(),
-                            (uint32_t)gcap, bits, nl->thist.as<uint32_t>(), s));
+                            (uint32_t)gcap, bits, nl->thist.as<uint32_t>(), &dst->sort_stall, s));
         CK(exclusive_scan_u32(nl->lower_cnt.as<uint32_t>(), nl->seg_off.as<uint32_t>(), nsc,
                               nl->bsum.as<uint32_t>(), &dst->seg_total, s));
         CK(launch_assemble(sa, grid0, s));
@@ -706,7 +711,7 @@ nl_status do_search_half(nl_list *nl, cudaStream_t s)
         CK(nl->thist.ensure(radix_hist_words(ntu) * 4));
         CK(radix_sort_pairs(nl->tkey.as<uint64_t>(), nl->tval.as<uint32_t>(),
                             nl->tkey_alt.as<uint64_t>(), nl->tval_alt.as<uint32_t>(), ntu, bits,
-                            nl->thist.as<uint32_t>(), s));
+                            nl->thist.as<uint32_t>(), &dst->sort_stall, s));
     }
     CK(nl->bsum.ensure(scan_bsum_words(nsc) * 4));
     CK(exclusive_scan_u32(nl->lower_cnt.as<uint32_t>(), nl->seg_off.as<uint32_t>(), nsc,

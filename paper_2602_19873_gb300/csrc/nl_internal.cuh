@@ -54,7 +54,8 @@ struct Status {
     unsigned int n_leaves;
     unsigned int n_nodes;
     unsigned int node_overflow;  // nodes beyond the preallocated capacity (graph replays)
-    unsigned int pad0[3];
+    unsigned int sort_stall;     // a radix-sort look-back gave up its bounded wait
+    unsigned int pad0[2];
     // search words (reset before every search); ticket is the first of them
     unsigned int ticket;      // work counter of persistent kernels
     unsigned int stage_overflow;
@@ -493,20 +494,30 @@ cudaError_t launch_keys(int64_t n, const float *x, const float *y, const float *
                         const DevBox &box, float support, int kind, uint64_t *keys, uint32_t *vals,
                         Status *st, cudaStream_t s);
 // batch form: each particle uses its own system's box
+// ghist (optional): add the counts of all eight 8-bit digits of the keys for
+// a following radix_sort_pairs(..., counted = true) (ghist cleared first).
 cudaError_t launch_keys_batch(int64_t n, const float *x, const float *y, const float *z,
                               const float *h, const SysTables &t, float support, int kind,
-                              uint64_t *keys, uint32_t *vals, Status *st, cudaStream_t s);
+                              uint64_t *keys, uint32_t *vals, Status *st, uint32_t *ghist,
+                              cudaStream_t s);
 
 // Stable LSD radix sort of (key, value) pairs on the low `bits` key bits.
-// Scratch: keys_alt/vals_alt (n each), hist (radix_hist_words(n) words).
+// Scratch: keys_alt/vals_alt (n each), hist (radix_hist_words(n) words,
+// cleared by the sort itself).  A look-back that gives up its bounded wait
+// sets *stall to 1 (the order is then wrong; callers report NL_ERR_TIMEOUT).
+// counted: hist was cleared by radix_sort_clear and the digit counts of all
+// passes were added to it (launch_keys_batch with ghist = hist).
 size_t radix_hist_words(uint32_t n);
+cudaError_t radix_sort_clear(uint32_t *hist, uint32_t n, int bits, cudaStream_t s);
 cudaError_t radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
-                             uint32_t n, int bits, uint32_t *hist, cudaStream_t s);
+                             uint32_t n, int bits, uint32_t *hist, unsigned int *stall,
+                             cudaStream_t s, bool counted = false);
 // Final stable passes by system (digit = system of the value, a caller index):
 // sorts (system, key) when run after radix_sort_pairs.
 cudaError_t radix_sort_by_system(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt,
                                  uint32_t *vals_alt, uint32_t n, const uint32_t *sys_off,
-                                 uint32_t nsys, uint32_t *hist, cudaStream_t s);
+                                 uint32_t nsys, uint32_t *hist, unsigned int *stall,
+                                 cudaStream_t s);
 
 // Boxes of the aligned groups of M consecutive lanes (one particle per lane,
 // M | 32, whole warps present): lo = (min xyz, max r), hi = (max xyz, min r),

@@ -11,7 +11,7 @@
 // same keys and permutation as nl_build computes.
 //
 // The array is part of this library's device image, so every GPU that loads
-// the library holds it (about 12.3 MB) until the process exits.  Its device
+// the library holds it (about 14.7 MB) until the process exits.  Its device
 // address is looked up once per device with cudaGetSymbolAddress, on the
 // first call made with that device current; that first call belongs before
 // any stream capture begins.  All calls share the one array:
@@ -33,7 +33,7 @@ constexpr uint32_t kMaxN = NL_NOALLOC_MAX_N;
 constexpr size_t kStatusBytes = 256;
 constexpr size_t kKeysBytes = (size_t)kMaxN * 8;
 constexpr size_t kValsBytes = (size_t)kMaxN * 4;
-constexpr size_t kHistWords = 256 * ((size_t)(kMaxN + 4095) / 4096) + 256;
+constexpr size_t kHistWords = 8 * 256 + 64 + (size_t)8 * 256 * ((kMaxN + 4095) / 4096);
 constexpr size_t kScratchBytes = kStatusBytes + kKeysBytes + kValsBytes + kHistWords * 4;
 static_assert(sizeof(Status) <= kStatusBytes, "status words must fit their slot");
 
@@ -115,7 +115,8 @@ extern "C" nl_status nl_sfc_order_noalloc(const float *x, const float *y, const 
 
     cudaError_t e = cudaMemsetAsync(dst, 0, sizeof(Status), s);
     if (e == cudaSuccess) e = launch_keys(n, x, y, z, h, b, support, key, keys, perm, dst, s);
-    if (e == cudaSuccess) e = radix_sort_pairs(keys, perm, keys_alt, vals_alt, N, 3 * kKeyBits, hist, s);
+    if (e == cudaSuccess) e = radix_sort_pairs(keys, perm, keys_alt, vals_alt, N, 3 * kKeyBits, hist,
+                                                      &dst->sort_stall, s);
     Status hs{};
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, dst, sizeof(Status), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -123,6 +124,9 @@ extern "C" nl_status nl_sfc_order_noalloc(const float *x, const float *y, const 
         (void)cudaGetLastError();
         return report_error(NL_ERR_CUDA, cudaGetErrorString(e));
     }
+    if (hs.sort_stall)
+        return report_error(NL_ERR_TIMEOUT, "nl_sfc_order_noalloc: a radix-sort look-back gave up "
+                                            "its bounded wait");
     if (hs.bad_input)
         return report_error(NL_ERR_ARG, "nl_sfc_order_noalloc: invalid particle input "
                                         "(non-finite or out-of-box coordinate, or h <= 0)");
