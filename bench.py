@@ -186,19 +186,20 @@ def reference_sample(steps, warmup, requested=None):
 
 
 def launches_per_step(sizes, batched, mixed=False, half_list=False):
-    """Kernels of one build + density step (graph replay when batched): keys,
-    radix sort (8 passes x 3, a 9th by system in batches), permute, octree
-    (10), search (open, interior and boundary launches plus a classification
-    when a batch mixes open and periodic systems),
-    and for the half search the tuple sort (3 per 8 key bits, plus the fill of
-    unused slots in a graph), the lower-entry scan (3) and the record
-    assembly; then the pass input gather and the pass (three when mixed);
-    a half list stores the search's records directly and adds the pass's
-    finishing kernel."""
-    sort_passes = 9 if batched else 8
+    """Kernels of one build + density step (graph replay when batched): keys
+    (which also count the sort's digits), the key sort (digit starts and 8
+    passes; in batches a histogram, the starts and one pass by system),
+    permute, octree (10), search (open, interior and boundary launches plus a
+    classification when a batch mixes open and periodic systems), and for the
+    half search the tuple sort (histogram, starts, one pass per 8 key bits,
+    plus the fill of unused slots in a graph), the lower-entry scan (3) and
+    the record assembly; then the pass input gather and the pass (three when
+    mixed); a half list stores the search's records directly and adds the
+    pass's finishing kernel."""
+    sort_launches = 1 + 8 + (3 if batched else 0)
     # mixed batches: open, interior and boundary launches of the search and
     # the pass, plus the interior classification
-    n = 1 + 3 * sort_passes + 1 + 10 + (3 + 1 if mixed else 1) + (2 if mixed else 0)
+    n = 1 + sort_launches + 1 + 10 + (3 + 1 if mixed else 1) + (2 if mixed else 0)
     if half_list:
         return n + 3
     if sizes["j_cluster"] == sizes["cluster"]:
@@ -206,7 +207,7 @@ def launches_per_step(sizes, batched, mixed=False, half_list=False):
         bits = 1
         while bits < 64 and (nsc * 8 * nsc) >> bits:
             bits += 1
-        n += 3 * ((bits + 7) // 8) + 3 + 1 + (1 if batched else 0)
+        n += 2 + (bits + 7) // 8 + 3 + 1 + (1 if batched else 0)
     return n + 2
 
 
