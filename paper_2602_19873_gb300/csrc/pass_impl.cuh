@@ -148,14 +148,29 @@ __device__ __forceinline__ void acc_end_block(Acc<KIND> &acc)
     }
 }
 
-// Shared memory per warp: the j particles (and pass inputs) of one block
-// of 32 list entries, loaded in bulk before the block is computed; on a
-// half list also the masses of the super-cluster's own particles.
+// The half-list density pass keeps the super-cluster's own particles in
+// shared memory (position and r^2, 1/h) instead of registers, read once per
+// listed tile: 48 fewer registers per lane, so it runs 4 blocks per SM
+// without spills; its j particles are staged 16 entries at a time to leave
+// room for that.
+template <int KIND, bool HL>
+constexpr bool pass_i_in_smem() { return HL && KIND == PASS_DENSITY; }
+
+// list entries whose j particles are staged together
+template <int KIND, bool HL>
+constexpr int pass_stage_entries() { return pass_i_in_smem<KIND, HL>() ? 16 : 32; }
+
+// Shared memory per warp: the j particles (and pass inputs) of one stage of
+// list entries, loaded in bulk before they are computed; on a half list also
+// the masses of the super-cluster's own particles, and (half-list density)
+// their positions, r^2 and 1/h.
 template <int MJ, int KIND, bool HL = false>
 constexpr size_t pass_smem_per_warp()
 {
-    return (size_t)32 * MJ * (sizeof(float4) + ((KIND == PASS_DENSITY || KIND == PASS_SPH || KIND == PASS_LJC) ? sizeof(float2) : 0)) +
-           (HL ? (size_t)kSC * MJ * sizeof(float) : 0);
+    return (size_t)pass_stage_entries<KIND, HL>() * MJ *
+               (sizeof(float4) + ((KIND == PASS_DENSITY || KIND == PASS_SPH || KIND == PASS_LJC) ? sizeof(float2) : 0)) +
+           (HL ? (size_t)kSC * MJ * sizeof(float) : 0) +
+           (pass_i_in_smem<KIND, HL>() ? (size_t)kSC * MJ * (sizeof(float4) + sizeof(float)) : 0);
 }
 
 // Resident blocks per SM the register budget is cut for: the scalar passes
@@ -165,7 +180,7 @@ constexpr size_t pass_smem_per_warp()
 template <int KIND, bool HL>
 constexpr int ps_min_blocks()
 {
-    return (HL && KIND == PASS_DENSITY) ? 3
+    return (HL && KIND == PASS_DENSITY) ? 4
            : (KIND == PASS_DENSITY || KIND == PASS_COUNT || KIND == PASS_MIN) ? 4 : 2;
 }
 
@@ -218,9 +233,14 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
     static_assert(!HL || M == MJ, "half lists have j-clusters of the i-cluster size");
     constexpr bool FORCE = (KIND == PASS_SPH || KIND == PASS_LJ || KIND == PASS_LJC);
     extern __shared__ __align__(16) unsigned char pass_smem[];
+    constexpr bool ISM = pass_i_in_smem<KIND, HL>();
+    constexpr uint32_t SE = pass_stage_entries<KIND, HL>();
     float4 *sp = reinterpret_cast<float4 *>(pass_smem + (threadIdx.x >> 5) * pass_smem_per_warp<MJ, KIND, HL>());
-    float2 *sa = reinterpret_cast<float2 *>(sp + 32 * MJ);
-    float *smi = AUX ? reinterpret_cast<float *>(sa + 32 * MJ) : reinterpret_cast<float *>(sp + 32 * MJ);
+    float2 *sa = reinterpret_cast<float2 *>(sp + SE * MJ);
+    float *smi = AUX ? reinterpret_cast<float *>(sa + SE * MJ) : reinterpret_cast<float *>(sp + SE * MJ);
+    // ISM: own particle k*M + II at sip (x, y, z, r^2) and shv (1/h)
+    float4 *sip = reinterpret_cast<float4 *>(smi + (HL ? kSC * MJ : 0));
+    float *shv = reinterpret_cast<float *>(sip + (ISM ? kSC * M : 0));
     // fixed-point scale of the half-list density (2^ex)
     const float hscale = (HL && KIND == PASS_DENSITY) ? __int_as_float((half_scale_exp(a.st->m_absmax) + 127) << 23) : 0.f;
     const unsigned lane = lane_id();
@@ -257,7 +277,13 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
             __syncwarp();
             if (lane < (uint32_t)M) {
 #pragma unroll
-                for (int k = 0; k < kSC; ++k) smi[k * M + II] = a.aux[(s * kSC + k) * M + II].x;
+                for (int k = 0; k < kSC; ++k) {
+                    smi[k * M + II] = a.aux[(s * kSC + k) * M + II].x;
+                    if constexpr (ISM) {
+                        sip[k * M + II] = make_float4(pi[k].x, pi[k].y, pi[k].z, ri2[k]);
+                        shv[k * M + II] = hinv[k];
+                    }
+                }
             }
             __syncwarp();
         }
@@ -298,14 +324,17 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
             const uint32_t mk = valid ? masks[t] : 0u;
             const uint32_t nb = min(32u, cnt - b0);
             acc_begin_block<KIND>(acc);
-            // stage the block's j clusters: entry e's particles at sp[e*MJ ..]
+            // stage the j clusters of entries c0 .. c0 + SE - 1 of the block:
+            // entry c0 + e's particles at sp[e*MJ ..]
+            auto stage = [&](uint32_t c0) {
+            const uint32_t ns = min(SE, nb - c0);
             __syncwarp();
 #pragma unroll 4
-            for (uint32_t q0 = 0; q0 < nb * MJ; q0 += 32) {  // whole warp in every shuffle
+            for (uint32_t q0 = 0; q0 < ns * MJ; q0 += 32) {  // whole warp in every shuffle
                 const uint32_t q = q0 + lane;
-                const uint32_t e = min(q / MJ, 31u);
+                const uint32_t e = min(c0 + q / MJ, 31u);
                 const uint32_t src = __shfl_sync(0xffffffffu, J, e) * MJ + (q % MJ);
-                if (q < nb * MJ) {
+                if (q < ns * MJ) {
                     if constexpr (HL && (KIND == PASS_DENSITY || KIND == PASS_COUNT || KIND == PASS_MIN)) {
                         // half list: w holds rj^2, and the density input's
                         // second word 1/h_j (dummies: rj = 0, never a pair)
@@ -328,6 +357,7 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                 }
             }
             __syncwarp();
+            };
             // half list: the current entry feeds its j particles too (js), with
             // the shares of this lane's j particles in jsh (density), jcn
             // (counts) or jfx, jfy, jfz (forces)
@@ -339,18 +369,21 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
 #pragma unroll
             for (int tt = 0; tt < NP; ++tt) jmn[tt] = INFINITY;
             // one (i-cluster k, j particle) term per lane
-            auto term = [&](int k, const float4 &pj, const float2 &aj, uint32_t jj, int tt) {
+            // pik, hik: i particle (x, y, z; w = r^2 when in shared memory) and 1/h
+            auto term = [&](int k, const float4 &pik, float hik, const float4 &pj, const float2 &aj,
+                            uint32_t jj, int tt) {
                 const uint32_t ii = (s * kSC + k) * M + II;
                 // canonical distance decides the pair; the sums use the
                 // accurate vector (identical unless wrapped)
-                const float d2 = pair_d2<PER>(pi[k], pj, box);
+                const float d2 = pair_d2<PER>(pik, pj, box);
                 if constexpr (HL && KIND == PASS_DENSITY) {
-                    const bool ini = d2 < ri2[k];        // i = j included (see selfseen)
+                    static_assert(ISM, "the half-list density pass reads its i particles from shared memory");
+                    const bool ini = d2 < pik.w;         // i = j included (see selfseen)
                     const bool inj = js && d2 < pj.w;    // the j share (entries beyond the own clusters)
                     if (owner && (ini || inj)) {
-                        const float e2 = PER ? d2_of(pair_dx_acc<PER>(pi[k], pj, box)) : d2;
+                        const float e2 = PER ? d2_of(pair_dx_acc<PER>(pik, pj, box)) : d2;
                         const float r = sqrt_approx(e2);
-                        if (ini) acc.b[k] += aj.x * spline_w_inside(r * hinv[k]);
+                        if (ini) acc.b[k] += aj.x * spline_w_inside(r * hik);
                         if (inj) jsh[tt] += smi[k * M + II] * spline_w_inside(r * aj.y);
                     }
                 } else if constexpr (HL && KIND == PASS_COUNT) {
@@ -456,6 +489,8 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                 }
             };
             for (uint32_t e = 0; e < nb; ++e) {
+                if (e % SE == 0) stage(e);
+                const uint32_t el = e % SE;  // staged slot of the entry
                 const uint32_t Je = __shfl_sync(0xffffffffu, J, e);
                 const uint32_t me = __shfl_sync(0xffffffffu, mk, e);
                 // half list: an entry beyond the own clusters also feeds its j particles
@@ -481,23 +516,30 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                     float2 aj[NP];
 #pragma unroll
                     for (int tt = 0; tt < NP; ++tt) {
-                        pj[tt] = sp[e * MJ + JJ0 + tt * JSTEP];
-                        aj[tt] = AUX ? sa[e * MJ + JJ0 + tt * JSTEP] : make_float2(0.f, 0.f);
+                        pj[tt] = sp[el * MJ + JJ0 + tt * JSTEP];
+                        aj[tt] = AUX ? sa[el * MJ + JJ0 + tt * JSTEP] : make_float2(0.f, 0.f);
                     }
 #pragma unroll
                     for (int k = 0; k < kSC; ++k) {
                         if (!((me >> k) & 1u)) continue;
+                        const float4 pik = ISM ? sip[k * M + II] : pi[k];
+                        const float hik = ISM ? shv[k * M + II] : hinv[k];
 #pragma unroll
-                        for (int tt = 0; tt < NP; ++tt) term(k, pj[tt], aj[tt], Je * MJ + JJ0 + tt * JSTEP, tt);
+                        for (int tt = 0; tt < NP; ++tt)
+                            term(k, pik, hik, pj[tt], aj[tt], Je * MJ + JJ0 + tt * JSTEP, tt);
                     }
                 } else {
 #pragma unroll
                     for (int tt = 0; tt < NP; ++tt) {
-                        const float4 pj = sp[e * MJ + JJ0 + tt * JSTEP];
-                        const float2 aj = AUX ? sa[e * MJ + JJ0 + tt * JSTEP] : make_float2(0.f, 0.f);
+                        const float4 pj = sp[el * MJ + JJ0 + tt * JSTEP];
+                        const float2 aj = AUX ? sa[el * MJ + JJ0 + tt * JSTEP] : make_float2(0.f, 0.f);
 #pragma unroll
                         for (int k = 0; k < kSC; ++k)
-                            if ((me >> k) & 1u) term(k, pj, aj, Je * MJ + JJ0 + tt * JSTEP, tt);
+                            if ((me >> k) & 1u) {
+                                const float4 pik = ISM ? sip[k * M + II] : pi[k];
+                                const float hik = ISM ? shv[k * M + II] : hinv[k];
+                                term(k, pik, hik, pj, aj, Je * MJ + JJ0 + tt * JSTEP, tt);
+                            }
                     }
                 }
                 if constexpr (HL) {
@@ -579,7 +621,7 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
             const uint32_t o = a.sorted_out ? i : pc;
             // the loop took i = j iff its entry was listed and the radius is
             // nonzero (d2 = 0 < r^2)
-            const bool took_self = ((selfseen >> k) & 1u) && ri2[k] > 0.f;
+            const bool took_self = ((selfseen >> k) & 1u) && (ISM ? sip[k * M + II].w : ri2[k]) > 0.f;
             if constexpr (HL && KIND == PASS_DENSITY) {
                 const float self = took_self ? 0.f : a.aux[i].x;  // m_i w(0) = m_i
                 atomicAdd(&a.hsum[i], fixed_of((acc.v[k] + self) * hscale));
