@@ -148,13 +148,13 @@ __device__ __forceinline__ void acc_end_block(Acc<KIND> &acc)
     }
 }
 
-// The half-list density pass keeps the super-cluster's own particles in
+// The density and count passes keep the super-cluster's own particles in
 // shared memory (position and r^2, 1/h) instead of registers, read once per
-// listed tile: 48 fewer registers per lane, so it runs 4 blocks per SM
-// without spills; its j particles are staged 16 entries at a time to leave
+// listed tile: 48 fewer registers per lane, so they run 4 blocks per SM with
+// few spills; their j particles are staged 16 entries at a time to leave
 // room for that.
 template <int KIND, bool HL>
-constexpr bool pass_i_in_smem() { return HL && KIND == PASS_DENSITY; }
+constexpr bool pass_i_in_smem() { return KIND == PASS_DENSITY || KIND == PASS_COUNT; }
 
 // list entries whose j particles are staged together
 template <int KIND, bool HL>
@@ -164,13 +164,13 @@ constexpr int pass_stage_entries() { return pass_i_in_smem<KIND, HL>() ? 16 : 32
 // list entries, loaded in bulk before they are computed; on a half list also
 // the masses of the super-cluster's own particles, and (half-list density)
 // their positions, r^2 and 1/h.
-template <int MJ, int KIND, bool HL = false>
+template <int M, int MJ, int KIND, bool HL = false>
 constexpr size_t pass_smem_per_warp()
 {
     return (size_t)pass_stage_entries<KIND, HL>() * MJ *
                (sizeof(float4) + ((KIND == PASS_DENSITY || KIND == PASS_SPH || KIND == PASS_LJC) ? sizeof(float2) : 0)) +
            (HL ? (size_t)kSC * MJ * sizeof(float) : 0) +
-           (pass_i_in_smem<KIND, HL>() ? (size_t)kSC * MJ * (sizeof(float4) + sizeof(float)) : 0);
+           (pass_i_in_smem<KIND, HL>() ? (size_t)kSC * M * (sizeof(float4) + sizeof(float)) : 0);
 }
 
 // Resident blocks per SM the register budget is cut for: the scalar passes
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
     extern __shared__ __align__(16) unsigned char pass_smem[];
     constexpr bool ISM = pass_i_in_smem<KIND, HL>();
     constexpr uint32_t SE = pass_stage_entries<KIND, HL>();
-    float4 *sp = reinterpret_cast<float4 *>(pass_smem + (threadIdx.x >> 5) * pass_smem_per_warp<MJ, KIND, HL>());
+    float4 *sp = reinterpret_cast<float4 *>(pass_smem + (threadIdx.x >> 5) * pass_smem_per_warp<M, MJ, KIND, HL>());
     float2 *sa = reinterpret_cast<float2 *>(sp + SE * MJ);
     float *smi = AUX ? reinterpret_cast<float *>(sa + SE * MJ) : reinterpret_cast<float *>(sp + SE * MJ);
     // ISM: own particle k*M + II at sip (x, y, z, r^2) and shv (1/h)
@@ -277,16 +277,21 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
             __syncwarp();
             if (lane < (uint32_t)M) {
 #pragma unroll
+                for (int k = 0; k < kSC; ++k) smi[k * M + II] = a.aux[(s * kSC + k) * M + II].x;
+            }
+        }
+        if constexpr (ISM) {
+            // own particles for the tile terms (written once per super-cluster)
+            __syncwarp();
+            if (lane < (uint32_t)M) {
+#pragma unroll
                 for (int k = 0; k < kSC; ++k) {
-                    smi[k * M + II] = a.aux[(s * kSC + k) * M + II].x;
-                    if constexpr (ISM) {
-                        sip[k * M + II] = make_float4(pi[k].x, pi[k].y, pi[k].z, ri2[k]);
-                        shv[k * M + II] = hinv[k];
-                    }
+                    sip[k * M + II] = make_float4(pi[k].x, pi[k].y, pi[k].z, ri2[k]);
+                    shv[k * M + II] = hinv[k];
                 }
             }
-            __syncwarp();
         }
+        if constexpr (ISM || (HL && (KIND == PASS_DENSITY || KIND == PASS_SPH))) __syncwarp();
         Acc<KIND> acc;
         // density and counts take the self pair i = j inside the loop when the
         // j-cluster holding i is listed against its i-cluster (d2 = 0, w(0) = 1);
@@ -388,16 +393,16 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                     }
                 } else if constexpr (HL && KIND == PASS_COUNT) {
                     if (owner) {
-                        if (d2 < ri2[k]) acc.v[k] += 1u;  // i = j included (see selfseen)
+                        if (d2 < pik.w) acc.v[k] += 1u;  // i = j included (see selfseen)
                         if (js && d2 < pj.w) jcn[tt] += 1u;
                     }
                 } else if constexpr (KIND == PASS_DENSITY) {
-                    if (owner && d2 < ri2[k]) {  // i = j included (see selfseen)
-                        const float e2 = PER ? d2_of(pair_dx_acc<PER>(pi[k], pj, box)) : d2;
-                        acc.b[k] += aj.x * spline_w_inside(sqrt_approx(e2) * hinv[k]);
+                    if (owner && d2 < pik.w) {  // i = j included (see selfseen)
+                        const float e2 = PER ? d2_of(pair_dx_acc<PER>(pik, pj, box)) : d2;
+                        acc.b[k] += aj.x * spline_w_inside(sqrt_approx(e2) * hik);
                     }
                 } else if constexpr (KIND == PASS_COUNT) {
-                    if (owner && d2 < ri2[k]) acc.v[k] += 1u;  // i = j included (see selfseen)
+                    if (owner && d2 < pik.w) acc.v[k] += 1u;  // i = j included (see selfseen)
                 } else if constexpr (HL && KIND == PASS_MIN) {
                     const bool ini = d2 < ri2[k];
                     const bool inj = js && d2 < pj.w;
@@ -633,7 +638,8 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                 atomicAdd(&a.hf[3 * (size_t)i + 2], f64_of(acc.z[k]));
             } else if constexpr (KIND == PASS_DENSITY) {
                 const float self = took_self ? 0.f : a.aux[i].x;  // m_i w(0) = m_i
-                a.out0[o] = (acc.v[k] + self) * (0.318309886183790672f * hinv[k] * hinv[k] * hinv[k]);
+                const float hk = ISM ? shv[k * M + II] : hinv[k];
+                a.out0[o] = (acc.v[k] + self) * (0.318309886183790672f * hk * hk * hk);
             } else if constexpr (KIND == PASS_COUNT) {
                 a.outc[o] = acc.v[k] - (took_self ? 1u : 0u);
             } else if constexpr (HL && KIND == PASS_MIN) {
@@ -657,8 +663,8 @@ template <int M, int MJ, int KIND, bool HL = false>
 static cudaError_t launch_mk(const PassArgs &a, int per, int grid, int threads, cudaStream_t s)
 {
     // the attribute is set for the largest block so that any shape fits
-    const size_t smax = (size_t)(PS_THREADS / 32) * pass_smem_per_warp<MJ, KIND, HL>();
-    const size_t smem = (size_t)(threads / 32) * pass_smem_per_warp<MJ, KIND, HL>();
+    const size_t smax = (size_t)(PS_THREADS / 32) * pass_smem_per_warp<M, MJ, KIND, HL>();
+    const size_t smem = (size_t)(threads / 32) * pass_smem_per_warp<M, MJ, KIND, HL>();
     const void *fn = per ? (const void *)k_pass<M, MJ, true, KIND, HL>
                          : (const void *)k_pass<M, MJ, false, KIND, HL>;
     cudaError_t e = set_max_dynamic_smem(fn, smax);
