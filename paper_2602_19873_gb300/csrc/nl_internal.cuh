@@ -234,9 +234,14 @@ __device__ __forceinline__ float wrap_len(float d, float len)
 
 // ---------------------------------------------------------------------------
 // Two FP32 values in one 64-bit register for the packed arithmetic of sm_100
-// and later (add / sub / mul .rn.f32x2: each half rounded to nearest on its
-// own, exactly as the scalar __fadd_rn / __fsub_rn / __fmul_rn, without
-// contraction), so the canonical predicate keeps its bits.
+// and later.  One sub / mul .rn.f32x2 rounds each half to nearest exactly as
+// the scalar __fsub_rn / __fmul_rn (checked bit for bit on 8.4M random
+// operand pairs each).  A packed product whose only use is a packed sum is
+// however contracted into a fused multiply-add by the code generator, .rn
+// notwithstanding (22.6 % of random squared distances came out different,
+// mostly equal to the fused value), so the sums of the canonical predicate
+// are taken in scalar add.rn, which is never contracted (0 differences in
+// 79.7M).  No packed add is used for it.
 // ---------------------------------------------------------------------------
 typedef unsigned long long f32x2;
 
@@ -256,13 +261,6 @@ __device__ __forceinline__ f32x2 sub2_rn(f32x2 a, f32x2 b)
 {
     f32x2 r;
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-
-__device__ __forceinline__ f32x2 add2_rn(f32x2 a, f32x2 b)
-{
-    f32x2 r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
 }
 
@@ -287,11 +285,24 @@ __device__ __forceinline__ float pair_d2(const float4 &pi, const float4 &pj, con
     return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
 }
 
+// (x^2 + y^2) + z^2 of both halves, the squares packed and the sums in
+// scalar add.rn (see above: a packed sum of packed products is contracted)
+__device__ __forceinline__ void sum_sq_x2(f32x2 x, f32x2 y, f32x2 z, float &da, float &db)
+{
+    float xa, xb, ya, yb, za, zb;
+    unpk2(mul2_rn(x, x), xa, xb);
+    unpk2(mul2_rn(y, y), ya, yb);
+    unpk2(mul2_rn(z, z), za, zb);
+    da = __fadd_rn(__fadd_rn(xa, ya), za);
+    db = __fadd_rn(__fadd_rn(xb, yb), zb);
+}
+
 // Canonical d2 of two pairs at once: (xa, xb) - (xi, xi) etc. in packed
-// registers; the periodic wrap of each half is the scalar one.
+// registers; the periodic wrap of each half is the scalar one.  Bit for bit
+// the scalar pair_d2 of each pair.
 template <bool PER>
-__device__ __forceinline__ f32x2 pair_d2_x2(f32x2 jx, f32x2 jy, f32x2 jz, f32x2 ix, f32x2 iy,
-                                             f32x2 iz, const PerLen &L)
+__device__ __forceinline__ void pair_d2_x2(f32x2 jx, f32x2 jy, f32x2 jz, f32x2 ix, f32x2 iy,
+                                           f32x2 iz, const PerLen &L, float &d2a, float &d2b)
 {
     f32x2 dx = sub2_rn(jx, ix), dy = sub2_rn(jy, iy), dz = sub2_rn(jz, iz);
     if (PER) {
@@ -303,7 +314,7 @@ __device__ __forceinline__ f32x2 pair_d2_x2(f32x2 jx, f32x2 jy, f32x2 jz, f32x2 
         unpk2(dz, a, b);
         dz = pk2(wrap_len(a, L.z), wrap_len(b, L.z));
     }
-    return add2_rn(add2_rn(mul2_rn(dx, dx), mul2_rn(dy, dy)), mul2_rn(dz, dz));
+    sum_sq_x2(dx, dy, dz, d2a, d2b);
 }
 
 template <bool PER>

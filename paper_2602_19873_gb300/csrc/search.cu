@@ -391,10 +391,9 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
                                 const uint32_t slot = JJ0 + 2u * u * JSTEP;
                                 const float4 jA = u == 0 ? jA0 : S.jpA[q * MJ + slot];
                                 const float4 jB = u == 0 ? jB0 : S.jpB[q * MJ + slot];
-                                const f32x2 d2 = pair_d2_x2<PER>(pk2(jA.x, jA.y), pk2(jA.z, jA.w),
-                                                                 pk2(jB.x, jB.y), ix, iy, iz, box);
                                 float d2a, d2b;
-                                unpk2(d2, d2a, d2b);
+                                pair_d2_x2<PER>(pk2(jA.x, jA.y), pk2(jA.z, jA.w), pk2(jB.x, jB.y), ix, iy,
+                                                iz, box, d2a, d2b);
                                 const int ca = (int)II - (int)slot, cb = ca - JSTEP;
                                 const bool h = (d2a < fmaxf(pi.w, jB.z) && ca != delta) ||
                                                (d2b < fmaxf(pi.w, jB.w) && cb != delta);
@@ -465,10 +464,9 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
                 }
                 const f32x2 gx = pk2(g[0][0], g[0][1]), gy = pk2(g[1][0], g[1][1]);
                 const f32x2 gz = pk2(g[2][0], g[2][1]);
-                const f32x2 d2 = add2_rn(add2_rn(mul2_rn(gx, gx), mul2_rn(gy, gy)), mul2_rn(gz, gz));
-                const float ra = fmaxf(qr[0], nlo.w), rb = fmaxf(qr[1], nlo.w);
                 float d2a, d2b, rra, rrb;
-                unpk2(d2, d2a, d2b);
+                sum_sq_x2(gx, gy, gz, d2a, d2b);
+                const float ra = fmaxf(qr[0], nlo.w), rb = fmaxf(qr[1], nlo.w);
                 unpk2(mul2_rn(pk2(ra, rb), pk2(ra, rb)), rra, rrb);
                 near = d2a <= rra || d2b <= rrb;
             } else {
