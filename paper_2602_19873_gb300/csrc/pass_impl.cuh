@@ -170,7 +170,7 @@ constexpr size_t pass_smem_per_warp()
     return (size_t)pass_stage_entries<KIND, HL>() * MJ *
                (sizeof(float4) + ((KIND == PASS_DENSITY || KIND == PASS_SPH || KIND == PASS_LJC) ? sizeof(float2) : 0)) +
            (HL ? (size_t)kSC * MJ * sizeof(float) : 0) +
-           (pass_i_in_smem<KIND, HL>() ? (size_t)kSC * M * (sizeof(float4) + sizeof(float)) : 0);
+           (pass_i_in_smem<KIND, HL>() ? (size_t)kSC * M * (sizeof(float4) + ((HL && KIND == PASS_DENSITY) ? sizeof(float2) : sizeof(float))) : 0);
 }
 
 // Resident blocks per SM the register budget is cut for: the scalar passes
@@ -238,14 +238,20 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
     float4 *sp = reinterpret_cast<float4 *>(pass_smem + (threadIdx.x >> 5) * pass_smem_per_warp<M, MJ, KIND, HL>());
     float2 *sa = reinterpret_cast<float2 *>(sp + SE * MJ);
     float *smi = AUX ? reinterpret_cast<float *>(sa + SE * MJ) : reinterpret_cast<float *>(sp + SE * MJ);
-    // ISM: own particle k*M + II at sip (x, y, z, r^2) and shv (1/h)
+    // ISM: own particle k*M + II at sip (x, y, z, r^2) and its 1/h in shm,
+    // with its mass beside it on a half-list density pass (1/h, m)
+    constexpr bool HM = HL && KIND == PASS_DENSITY;
     float4 *sip = reinterpret_cast<float4 *>(smi + (HL ? kSC * MJ : 0));
-    float *shv = reinterpret_cast<float *>(sip + (ISM ? kSC * M : 0));
+    float2 *shm = reinterpret_cast<float2 *>(sip + (ISM ? kSC * M : 0));
+    float *shv = reinterpret_cast<float *>(shm);
     // fixed-point scale of the half-list density (2^ex)
     const float hscale = (HL && KIND == PASS_DENSITY) ? __int_as_float((half_scale_exp(a.st->m_absmax) + 127) << 23) : 0.f;
     const unsigned lane = lane_id();
     const uint32_t II = lane % M;
     const uint32_t JJ0 = (lane / M) % MJ;
+    auto own_hm = [&](int k) {
+        return HM ? shm[k * M + II] : make_float2(shv[k * M + II], 0.f);
+    };
     // lanes that hold a distinct (i, j) pair; for M x MJ = 4 x 4 lanes 16..31 repeat
     const bool owner = (M * MJ >= 32) || lane < (uint32_t)(M * MJ);
 
@@ -272,7 +278,7 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
             hinv[k] = 1.f / pi[k].w;
             ci[k] = (KIND == PASS_SPH) ? a.aux[i].y : (KIND == PASS_LJC) ? a.p3 * a.aux[i].x : 0.f;
         }
-        if constexpr (HL && (KIND == PASS_DENSITY || KIND == PASS_SPH)) {
+        if constexpr (HL && KIND == PASS_SPH) {
             // masses of the own particles, for the j shares
             __syncwarp();
             if (lane < (uint32_t)M) {
@@ -286,12 +292,16 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
             if (lane < (uint32_t)M) {
 #pragma unroll
                 for (int k = 0; k < kSC; ++k) {
+                    const uint32_t i = (s * kSC + k) * M + II;
                     sip[k * M + II] = make_float4(pi[k].x, pi[k].y, pi[k].z, ri2[k]);
-                    shv[k * M + II] = hinv[k];
+                    if constexpr (HM)
+                        shm[k * M + II] = make_float2(hinv[k], a.aux[i].x);
+                    else
+                        shv[k * M + II] = hinv[k];
                 }
             }
         }
-        if constexpr (ISM || (HL && (KIND == PASS_DENSITY || KIND == PASS_SPH))) __syncwarp();
+        if constexpr (ISM || (HL && KIND == PASS_SPH)) __syncwarp();
         Acc<KIND> acc;
         // density and counts take the self pair i = j inside the loop when the
         // j-cluster holding i is listed against its i-cluster (d2 = 0, w(0) = 1);
@@ -374,9 +384,10 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
 #pragma unroll
             for (int tt = 0; tt < NP; ++tt) jmn[tt] = INFINITY;
             // one (i-cluster k, j particle) term per lane
-            // pik, hik: i particle (x, y, z; w = r^2 when in shared memory) and 1/h
-            auto term = [&](int k, const float4 &pik, float hik, const float4 &pj, const float2 &aj,
-                            uint32_t jj, int tt) {
+            // pik, hik, mik: i particle (x, y, z; w = r^2 when in shared memory),
+            // its 1/h and (half-list density) its mass
+            auto term = [&](int k, const float4 &pik, float hik, float mik, const float4 &pj,
+                            const float2 &aj, uint32_t jj, int tt) {
                 const uint32_t ii = (s * kSC + k) * M + II;
                 // canonical distance decides the pair; the sums use the
                 // accurate vector (identical unless wrapped)
@@ -389,7 +400,7 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                         const float e2 = PER ? d2_of(pair_dx_acc<PER>(pik, pj, box)) : d2;
                         const float r = sqrt_approx(e2);
                         if (ini) acc.b[k] += aj.x * spline_w_inside(r * hik);
-                        if (inj) jsh[tt] += smi[k * M + II] * spline_w_inside(r * aj.y);
+                        if (inj) jsh[tt] += mik * spline_w_inside(r * aj.y);
                     }
                 } else if constexpr (HL && KIND == PASS_COUNT) {
                     if (owner) {
@@ -528,10 +539,10 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                     for (int k = 0; k < kSC; ++k) {
                         if (!((me >> k) & 1u)) continue;
                         const float4 pik = ISM ? sip[k * M + II] : pi[k];
-                        const float hik = ISM ? shv[k * M + II] : hinv[k];
+                        const float2 hm = ISM ? own_hm(k) : make_float2(hinv[k], 0.f);
 #pragma unroll
                         for (int tt = 0; tt < NP; ++tt)
-                            term(k, pik, hik, pj[tt], aj[tt], Je * MJ + JJ0 + tt * JSTEP, tt);
+                            term(k, pik, hm.x, hm.y, pj[tt], aj[tt], Je * MJ + JJ0 + tt * JSTEP, tt);
                     }
                 } else {
 #pragma unroll
@@ -542,12 +553,35 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                         for (int k = 0; k < kSC; ++k)
                             if ((me >> k) & 1u) {
                                 const float4 pik = ISM ? sip[k * M + II] : pi[k];
-                                const float hik = ISM ? shv[k * M + II] : hinv[k];
-                                term(k, pik, hik, pj, aj, Je * MJ + JJ0 + tt * JSTEP, tt);
+                                const float2 hm = ISM ? own_hm(k) : make_float2(hinv[k], 0.f);
+                                term(k, pik, hm.x, hm.y, pj, aj, Je * MJ + JJ0 + tt * JSTEP, tt);
                             }
                     }
                 }
-                if constexpr (HL) {
+                if constexpr (HL && NP == 2 && (KIND == PASS_DENSITY || KIND == PASS_COUNT)) {
+                    if (js) {
+                        // sum each j particle's share over the M lanes of its i
+                        // particles in a fixed order: the first step trades the
+                        // lane's two shares with lane II ^ 1 (even lanes keep the
+                        // first j particle, odd lanes the second), two more steps
+                        // finish; lanes II = 0 and 1 then add one integer each
+                        const bool odd = II & 1u;
+                        if constexpr (KIND == PASS_DENSITY) {
+                            float v = (odd ? jsh[1] : jsh[0]) +
+                                      __shfl_xor_sync(0xffffffffu, odd ? jsh[0] : jsh[1], 1);
+#pragma unroll
+                            for (int o = 2; o < M; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                            if (II < 2u && v != 0.f)
+                                atomicAdd(&a.hsum[Je * MJ + JJ0 + II * JSTEP], fixed_of(v * hscale));
+                        } else {
+                            uint32_t v = (odd ? jcn[1] : jcn[0]) +
+                                         __shfl_xor_sync(0xffffffffu, odd ? jcn[0] : jcn[1], 1);
+#pragma unroll
+                            for (int o = 2; o < M; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                            if (II < 2u && v != 0u) atomicAdd(&a.hcnt[Je * MJ + JJ0 + II * JSTEP], v);
+                        }
+                    }
+                } else if constexpr (HL) {
                     if (js) {
                         // sum each j particle's share over the M lanes of its i
                         // particles (fixed order), one integer add per j particle
@@ -638,7 +672,7 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                 atomicAdd(&a.hf[3 * (size_t)i + 2], f64_of(acc.z[k]));
             } else if constexpr (KIND == PASS_DENSITY) {
                 const float self = took_self ? 0.f : a.aux[i].x;  // m_i w(0) = m_i
-                const float hk = ISM ? shv[k * M + II] : hinv[k];
+                const float hk = ISM ? own_hm(k).x : hinv[k];
                 a.out0[o] = (acc.v[k] + self) * (0.318309886183790672f * hk * hk * hk);
             } else if constexpr (KIND == PASS_COUNT) {
                 a.outc[o] = acc.v[k] - (took_self ? 1u : 0u);
