@@ -148,13 +148,23 @@ __device__ __forceinline__ void acc_end_block(Acc<KIND> &acc)
     }
 }
 
-// The density and count passes keep the super-cluster's own particles in
-// shared memory (position and r^2, 1/h) instead of registers, read once per
-// listed tile: 48 fewer registers per lane, so they run 4 blocks per SM with
-// few spills; their j particles are staged 16 entries at a time to leave
-// room for that.
+// The passes keep the super-cluster's own particles in shared memory
+// (position and r^2, 1/h and what the pass needs besides) instead of
+// registers, read once per listed tile: 48 or more fewer registers per lane,
+// so the scalar passes run 4 blocks per SM with few spills and the force
+// passes 3; the j particles are staged 16 entries at a time to leave room
+// for that.
 template <int KIND, bool HL>
-constexpr bool pass_i_in_smem() { return KIND == PASS_DENSITY || KIND == PASS_COUNT; }
+constexpr bool pass_i_in_smem() { return true; }
+
+// bytes per own particle beside (x, y, z, r^2): (1/h, m) on a half-list
+// density pass, (1/h, c_i, r_i, m_i) on the force passes, else 1/h
+template <int KIND, bool HL>
+constexpr size_t pass_own_extra_bytes()
+{
+    return (HL && KIND == PASS_DENSITY) ? 8
+           : (KIND == PASS_SPH || KIND == PASS_LJ || KIND == PASS_LJC) ? 16 : 4;
+}
 
 // list entries whose j particles are staged together
 template <int KIND, bool HL>
@@ -170,18 +180,18 @@ constexpr size_t pass_smem_per_warp()
     return (size_t)pass_stage_entries<KIND, HL>() * MJ *
                (sizeof(float4) + ((KIND == PASS_DENSITY || KIND == PASS_SPH || KIND == PASS_LJC) ? sizeof(float2) : 0)) +
            (HL ? (size_t)kSC * MJ * sizeof(float) : 0) +
-           (pass_i_in_smem<KIND, HL>() ? (size_t)kSC * M * (sizeof(float4) + ((HL && KIND == PASS_DENSITY) ? sizeof(float2) : sizeof(float))) : 0);
+           (pass_i_in_smem<KIND, HL>() ? (size_t)kSC * M * (sizeof(float4) + pass_own_extra_bytes<KIND, HL>()) : 0);
 }
 
-// Resident blocks per SM the register budget is cut for: the scalar passes
-// run at 64 registers (4 blocks of 256, some spills; measured faster than 3
-// blocks at 80), the vector passes keep 128; the half-list density pass
-// holds more per lane and runs 3 blocks at 80.
+// Resident blocks per SM the register budget is cut for (measured at the
+// benchmark sizes): the scalar passes run at 64 registers (4 blocks of 256;
+// 5 blocks were slower); the force passes at 128 (2 blocks) on half lists
+// and for LJ, at 85 (3 blocks) for SPH and LJ + Coulomb on full lists.
 template <int KIND, bool HL>
 constexpr int ps_min_blocks()
 {
-    return (HL && KIND == PASS_DENSITY) ? 4
-           : (KIND == PASS_DENSITY || KIND == PASS_COUNT || KIND == PASS_MIN) ? 4 : 2;
+    return (KIND == PASS_DENSITY || KIND == PASS_COUNT || KIND == PASS_MIN) ? 4
+           : (HL || KIND == PASS_LJ) ? 2 : 3;
 }
 
 // Nearest integer of x (ties away from zero) as a 64-bit two's complement
@@ -244,6 +254,7 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
     float4 *sip = reinterpret_cast<float4 *>(smi + (HL ? kSC * MJ : 0));
     float2 *shm = reinterpret_cast<float2 *>(sip + (ISM ? kSC * M : 0));
     float *shv = reinterpret_cast<float *>(shm);
+    float4 *sxv = reinterpret_cast<float4 *>(shm);  // force passes: (1/h, c_i, r_i, m_i)
     // fixed-point scale of the half-list density (2^ex)
     const float hscale = (HL && KIND == PASS_DENSITY) ? __int_as_float((half_scale_exp(a.st->m_absmax) + 127) << 23) : 0.f;
     const unsigned lane = lane_id();
@@ -278,14 +289,6 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
             hinv[k] = 1.f / pi[k].w;
             ci[k] = (KIND == PASS_SPH) ? a.aux[i].y : (KIND == PASS_LJC) ? a.p3 * a.aux[i].x : 0.f;
         }
-        if constexpr (HL && KIND == PASS_SPH) {
-            // masses of the own particles, for the j shares
-            __syncwarp();
-            if (lane < (uint32_t)M) {
-#pragma unroll
-                for (int k = 0; k < kSC; ++k) smi[k * M + II] = a.aux[(s * kSC + k) * M + II].x;
-            }
-        }
         if constexpr (ISM) {
             // own particles for the tile terms (written once per super-cluster)
             __syncwarp();
@@ -296,12 +299,14 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                     sip[k * M + II] = make_float4(pi[k].x, pi[k].y, pi[k].z, ri2[k]);
                     if constexpr (HM)
                         shm[k * M + II] = make_float2(hinv[k], a.aux[i].x);
+                    else if constexpr (FORCE)
+                        sxv[k * M + II] = make_float4(hinv[k], ci[k], ri[k], (HL && AUX) ? a.aux[i].x : 0.f);
                     else
                         shv[k * M + II] = hinv[k];
                 }
             }
         }
-        if constexpr (ISM || (HL && KIND == PASS_SPH)) __syncwarp();
+        if constexpr (ISM) __syncwarp();
         Acc<KIND> acc;
         // density and counts take the self pair i = j inside the loop when the
         // j-cluster holding i is listed against its i-cluster (d2 = 0, w(0) = 1);
@@ -386,8 +391,9 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
             // one (i-cluster k, j particle) term per lane
             // pik, hik, mik: i particle (x, y, z; w = r^2 when in shared memory),
             // its 1/h and (half-list density) its mass
-            auto term = [&](int k, const float4 &pik, float hik, float mik, const float4 &pj,
-                            const float2 &aj, uint32_t jj, int tt) {
+            // ex: the force passes' (1/h, c_i, r_i, m_i)
+            auto term = [&](int k, const float4 &pik, float hik, float mik, const float4 &ex,
+                            const float4 &pj, const float2 &aj, uint32_t jj, int tt) {
                 const uint32_t ii = (s * kSC + k) * M + II;
                 // canonical distance decides the pair; the sums use the
                 // accurate vector (identical unless wrapped)
@@ -415,31 +421,31 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                 } else if constexpr (KIND == PASS_COUNT) {
                     if (owner && d2 < pik.w) acc.v[k] += 1u;  // i = j included (see selfseen)
                 } else if constexpr (HL && KIND == PASS_MIN) {
-                    const bool ini = d2 < ri2[k];
+                    const bool ini = d2 < pik.w;
                     const bool inj = js && d2 < pj.w;
                     if (owner && ii != jj && (ini || inj)) {
-                        const float e2 = PER ? d2_of(pair_dx_acc<PER>(pi[k], pj, box)) : d2;
+                        const float e2 = PER ? d2_of(pair_dx_acc<PER>(pik, pj, box)) : d2;
                         if (ini) acc.v[k] = fminf(acc.v[k], e2);
                         if (inj) jmn[tt] = fminf(jmn[tt], e2);
                     }
                 } else if constexpr (KIND == PASS_MIN) {  // nearest gather neighbor
-                    if (owner && ii != jj && d2 < ri2[k]) {
-                        const float e2 = PER ? d2_of(pair_dx_acc<PER>(pi[k], pj, box)) : d2;
+                    if (owner && ii != jj && d2 < pik.w) {
+                        const float e2 = PER ? d2_of(pair_dx_acc<PER>(pik, pj, box)) : d2;
                         acc.v[k] = fminf(acc.v[k], e2);
                     }
                 } else if constexpr (KIND == PASS_SPH) {
                     const float rj = __fmul_rn(a.support, pj.w);
-                    const float rr = fmaxf(ri[k], rj);
+                    const float rr = fmaxf(ex.z, rj);
                     if (owner && ii != jj && d2 < __fmul_rn(rr, rr)) {
                         // a_i -= m_j (c_i gW_i + c_j gW_j) (x_i - x_j) / r
-                        const float3 dv = pair_dx_acc<PER>(pi[k], pj, box);
+                        const float3 dv = pair_dx_acc<PER>(pik, pj, box);
                         const float e2 = d2_of(dv);
                         const float ir = e2 > 0.f ? rsqrtf(e2) : 0.f;  // grad W(0) = 0
                         const float r = e2 * ir;
                         const float hji = 1.f / pj.w;
-                        const float gi = spline_dw(r * hinv[k]) * hinv[k] * hinv[k] * hinv[k] * hinv[k];
+                        const float gi = spline_dw(r * ex.x) * ex.x * ex.x * ex.x * ex.x;
                         const float gj = spline_dw(r * hji) * hji * hji * hji * hji;
-                        const float bsym = (ci[k] * gi + aj.y * gj) * 0.318309886183790672f * ir;
+                        const float bsym = (ex.y * gi + aj.y * gj) * 0.318309886183790672f * ir;
                         const float sc = aj.x * bsym;
                         // x_i - x_j = -dv
                         acc.bx[k] += sc * dv.x;
@@ -447,7 +453,7 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                         acc.bz[k] += sc * dv.z;
                         if constexpr (HL) {
                             if (js) {  // a_j -= m_i (same bracket) (x_j - x_i) / r
-                                const float sj = smi[k * M + II] * bsym;
+                                const float sj = ex.w * bsym;
                                 jfx[tt] -= sj * dv.x;
                                 jfy[tt] -= sj * dv.y;
                                 jfz[tt] -= sj * dv.z;
@@ -455,10 +461,10 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                         }
                     }
                 } else if constexpr (HL && KIND == PASS_LJ) {  // both particles, F_j = -F_ij
-                    const bool ini = d2 < ri2[k];
+                    const bool ini = d2 < pik.w;
                     const bool inj = js && d2 < pj.w;
                     if (owner && ii != jj && (ini || inj)) {
-                        const float3 dv = pair_dx_acc<PER>(pi[k], pj, box);
+                        const float3 dv = pair_dx_acc<PER>(pik, pj, box);
                         const float ir2 = 1.f / d2_of(dv);
                         const float s2 = a.p1 * a.p1 * ir2;
                         const float s6 = s2 * s2 * s2;
@@ -467,21 +473,21 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                         if (inj) { jfx[tt] += c * dv.x; jfy[tt] += c * dv.y; jfz[tt] += c * dv.z; }
                     }
                 } else if constexpr (HL && KIND == PASS_LJC) {  // both particles, F_j = -F_ij
-                    const bool ini = d2 < ri2[k];
+                    const bool ini = d2 < pik.w;
                     const bool inj = js && d2 < pj.w;
                     if (owner && ii != jj && (ini || inj)) {
-                        const float3 dv = pair_dx_acc<PER>(pi[k], pj, box);
+                        const float3 dv = pair_dx_acc<PER>(pik, pj, box);
                         const float ir = rsqrtf(d2_of(dv));
                         const float ir2 = ir * ir;
                         const float s2 = a.p1 * a.p1 * ir2;
                         const float s6 = s2 * s2 * s2;
-                        const float c = ir2 * (24.f * a.p0 * s6 * (2.f * s6 - 1.f) + ci[k] * aj.x * ir);
+                        const float c = ir2 * (24.f * a.p0 * s6 * (2.f * s6 - 1.f) + ex.y * aj.x * ir);
                         if (ini) { acc.bx[k] -= c * dv.x; acc.by[k] -= c * dv.y; acc.bz[k] -= c * dv.z; }
                         if (inj) { jfx[tt] += c * dv.x; jfy[tt] += c * dv.y; jfz[tt] += c * dv.z; }
                     }
                 } else if constexpr (KIND == PASS_LJ) {  // F_i += 24 eps (2 s^12/r^14 - s^6/r^8)(x_i - x_j)
-                    if (owner && ii != jj && d2 < ri2[k]) {
-                        const float3 dv = pair_dx_acc<PER>(pi[k], pj, box);
+                    if (owner && ii != jj && d2 < pik.w) {
+                        const float3 dv = pair_dx_acc<PER>(pik, pj, box);
                         const float ir2 = 1.f / d2_of(dv);
                         const float s2 = a.p1 * a.p1 * ir2;
                         const float s6 = s2 * s2 * s2;
@@ -491,13 +497,13 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                         acc.bz[k] -= c * dv.z;
                     }
                 } else {  // LJ + Coulomb: the LJ term plus kc q_i q_j (x_i - x_j) / r^3
-                    if (owner && ii != jj && d2 < ri2[k]) {
-                        const float3 dv = pair_dx_acc<PER>(pi[k], pj, box);
+                    if (owner && ii != jj && d2 < pik.w) {
+                        const float3 dv = pair_dx_acc<PER>(pik, pj, box);
                         const float ir = rsqrtf(d2_of(dv));
                         const float ir2 = ir * ir;
                         const float s2 = a.p1 * a.p1 * ir2;
                         const float s6 = s2 * s2 * s2;
-                        const float c = ir2 * (24.f * a.p0 * s6 * (2.f * s6 - 1.f) + ci[k] * aj.x * ir);
+                        const float c = ir2 * (24.f * a.p0 * s6 * (2.f * s6 - 1.f) + ex.y * aj.x * ir);
                         acc.bx[k] -= c * dv.x;
                         acc.by[k] -= c * dv.y;
                         acc.bz[k] -= c * dv.z;
@@ -539,10 +545,11 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                     for (int k = 0; k < kSC; ++k) {
                         if (!((me >> k) & 1u)) continue;
                         const float4 pik = ISM ? sip[k * M + II] : pi[k];
-                        const float2 hm = ISM ? own_hm(k) : make_float2(hinv[k], 0.f);
+                        const float4 ex = FORCE ? sxv[k * M + II] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        const float2 hm = FORCE ? make_float2(ex.x, ex.w) : ISM ? own_hm(k) : make_float2(hinv[k], 0.f);
 #pragma unroll
                         for (int tt = 0; tt < NP; ++tt)
-                            term(k, pik, hm.x, hm.y, pj[tt], aj[tt], Je * MJ + JJ0 + tt * JSTEP, tt);
+                            term(k, pik, hm.x, hm.y, ex, pj[tt], aj[tt], Je * MJ + JJ0 + tt * JSTEP, tt);
                     }
                 } else {
 #pragma unroll
@@ -553,8 +560,9 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                         for (int k = 0; k < kSC; ++k)
                             if ((me >> k) & 1u) {
                                 const float4 pik = ISM ? sip[k * M + II] : pi[k];
-                                const float2 hm = ISM ? own_hm(k) : make_float2(hinv[k], 0.f);
-                                term(k, pik, hm.x, hm.y, pj, aj, Je * MJ + JJ0 + tt * JSTEP, tt);
+                                const float4 ex = FORCE ? sxv[k * M + II] : make_float4(0.f, 0.f, 0.f, 0.f);
+                                const float2 hm = FORCE ? make_float2(ex.x, ex.w) : ISM ? own_hm(k) : make_float2(hinv[k], 0.f);
+                                term(k, pik, hm.x, hm.y, ex, pj, aj, Je * MJ + JJ0 + tt * JSTEP, tt);
                             }
                     }
                 }
