@@ -155,7 +155,7 @@ __device__ __forceinline__ void acc_end_block(Acc<KIND> &acc)
 // passes 3; the j particles are staged 16 entries at a time to leave room
 // for that.
 template <int KIND, bool HL>
-constexpr bool pass_i_in_smem() { return true; }
+constexpr bool pass_i_in_smem() { return !(KIND == PASS_LJ && !HL); }  // full-list LJ: measured faster in registers
 
 // bytes per own particle beside (x, y, z, r^2): (1/h, m) on a half-list
 // density pass, (1/h, c_i, r_i, m_i) on the force passes, else 1/h
@@ -544,8 +544,9 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
 #pragma unroll
                     for (int k = 0; k < kSC; ++k) {
                         if (!((me >> k) & 1u)) continue;
-                        const float4 pik = ISM ? sip[k * M + II] : pi[k];
-                        const float4 ex = FORCE ? sxv[k * M + II] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        const float4 pik = ISM ? sip[k * M + II] : make_float4(pi[k].x, pi[k].y, pi[k].z, ri2[k]);
+                        const float4 ex = !FORCE ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                          : ISM ? sxv[k * M + II] : make_float4(hinv[k], ci[k], ri[k], 0.f);
                         const float2 hm = FORCE ? make_float2(ex.x, ex.w) : ISM ? own_hm(k) : make_float2(hinv[k], 0.f);
 #pragma unroll
                         for (int tt = 0; tt < NP; ++tt)
@@ -559,8 +560,9 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
 #pragma unroll
                         for (int k = 0; k < kSC; ++k)
                             if ((me >> k) & 1u) {
-                                const float4 pik = ISM ? sip[k * M + II] : pi[k];
-                                const float4 ex = FORCE ? sxv[k * M + II] : make_float4(0.f, 0.f, 0.f, 0.f);
+                                const float4 pik = ISM ? sip[k * M + II] : make_float4(pi[k].x, pi[k].y, pi[k].z, ri2[k]);
+                                const float4 ex = !FORCE ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                                  : ISM ? sxv[k * M + II] : make_float4(hinv[k], ci[k], ri[k], 0.f);
                                 const float2 hm = FORCE ? make_float2(ex.x, ex.w) : ISM ? own_hm(k) : make_float2(hinv[k], 0.f);
                                 term(k, pik, hm.x, hm.y, ex, pj, aj, Je * MJ + JJ0 + tt * JSTEP, tt);
                             }
