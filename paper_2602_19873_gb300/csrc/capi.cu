@@ -418,6 +418,10 @@ nl_status do_prep(nl_list *nl, const float *x, const float *y, const float *z, c
                             nl->keys_alt.as<uint64_t>(), nl->vals_alt.as<uint32_t>(), N,
                             nl->sys_off.as<uint32_t>(), (uint32_t)nsys, nl->hist.as<uint32_t>(),
                             &dst->sort_stall, s));
+    // test knob NLGB_SORT_STALL=1: report a look-back wait of the key sort that
+    // gave up, without one, so that the error path runs on the host
+    if (const char *e = std::getenv("NLGB_SORT_STALL"))
+        if (e[0] == '1') CK(cudaMemsetAsync(&dst->sort_stall, 1, 1, s));
     CK(nl->mark(2, s));
     CK(launch_permute(npad, M, MJ, T, nl->vals.as<uint32_t>(), x, y, z, h, p->support,
                       nl->pos.as<float4>(), nl->perm_pad.as<uint32_t>(), nl->clo.as<float4>(),
