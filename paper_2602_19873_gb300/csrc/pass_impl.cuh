@@ -45,6 +45,21 @@ __device__ __forceinline__ float spline_w_inside(float q)
     return q < 1.f ? inner : outer;
 }
 
+// spline_w_inside of two arguments at once (packed products; inner part as
+// 1 - 0.75 q^2 (2 - q), the same polynomial in its own rounding order)
+__device__ __forceinline__ void spline_w_inside_x2(f32x2 q, float &w0, float &w1)
+{
+    const f32x2 a = sub2_rn(pk2(2.f, 2.f), q);  // 2 - q
+    const f32x2 t = mul2_rn(mul2_rn(q, q), a);
+    const f32x2 a3 = mul2_rn(mul2_rn(a, a), a);
+    float q0, q1, t0, t1, o0, o1;
+    unpk2(q, q0, q1);
+    unpk2(t, t0, t1);
+    unpk2(a3, o0, o1);
+    w0 = q0 < 1.f ? fmaf(-0.75f, t0, 1.f) : 0.25f * o0;
+    w1 = q1 < 1.f ? fmaf(-0.75f, t1, 1.f) : 0.25f * o1;
+}
+
 // cubic spline shape w(q) (support q < 2) and its derivative
 __device__ __forceinline__ float spline_w(float q)
 {
@@ -405,8 +420,11 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                     if (owner && (ini || inj)) {
                         const float e2 = PER ? d2_of(pair_dx_acc<PER>(pik, pj, box)) : d2;
                         const float r = sqrt_approx(e2);
-                        if (ini) acc.b[k] += aj.x * spline_w_inside(r * hik);
-                        if (inj) jsh[tt] += mik * spline_w_inside(r * aj.y);
+                        // both sides' kernel values in one packed evaluation
+                        float wi, wj;
+                        spline_w_inside_x2(mul2_rn(pk2(r, r), pk2(hik, aj.y)), wi, wj);
+                        if (ini) acc.b[k] += aj.x * wi;
+                        if (inj) jsh[tt] += mik * wj;
                     }
                 } else if constexpr (HL && KIND == PASS_COUNT) {
                     if (owner) {
@@ -548,9 +566,23 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                         const float4 ex = !FORCE ? make_float4(0.f, 0.f, 0.f, 0.f)
                                           : ISM ? sxv[k * M + II] : make_float4(hinv[k], ci[k], ri[k], 0.f);
                         const float2 hm = FORCE ? make_float2(ex.x, ex.w) : ISM ? own_hm(k) : make_float2(hinv[k], 0.f);
+                        if constexpr (!HL && !PER && KIND == PASS_DENSITY && NP == 2) {
+                            // full-list density on open systems: the lane's two
+                            // pairs share one branch and one packed kernel evaluation
+                            const float d2a = pair_d2<PER>(pik, pj[0], box), d2b = pair_d2<PER>(pik, pj[1], box);
+                            const bool ina = owner && d2a < pik.w, inb = owner && d2b < pik.w;  // i = j included
+                            if (ina || inb) {
+                                float wa, wb;
+                                spline_w_inside_x2(mul2_rn(pk2(sqrt_approx(d2a), sqrt_approx(d2b)), pk2(hm.x, hm.x)),
+                                                   wa, wb);
+                                if (ina) acc.b[k] += aj[0].x * wa;
+                                if (inb) acc.b[k] += aj[1].x * wb;
+                            }
+                        } else {
 #pragma unroll
-                        for (int tt = 0; tt < NP; ++tt)
-                            term(k, pik, hm.x, hm.y, ex, pj[tt], aj[tt], Je * MJ + JJ0 + tt * JSTEP, tt);
+                            for (int tt = 0; tt < NP; ++tt)
+                                term(k, pik, hm.x, hm.y, ex, pj[tt], aj[tt], Je * MJ + JJ0 + tt * JSTEP, tt);
+                        }
                     }
                 } else {
 #pragma unroll
