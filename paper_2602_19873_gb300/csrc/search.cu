@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
         // Stackless pre-order walk of the system's subtree; nodes are read in
         // coalesced chunks of 32 consecutive nodes staged in shared memory.
         uint32_t v = vroot, cb = 0;
-        bool have = false;
+        bool have = false, past = false;
         while (v < vend) {
             if (!have || v - cb >= 32u) {
                 cb = v;
@@ -442,7 +442,10 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
             const float4 nlo = S.nlo[v - cb];
             const float4 nhi = S.nhi[v - cb];
             const uint32_t skip = (uint32_t)__float_as_int(nhi.w);
-            if (HALF && (uint32_t)S.nrg[v - cb].y <= base) {  // wholly before the own particles
+            // wholly before the own particles: only nodes ahead of the first
+            // accepted leaf can be (that leaf holds particle base, and every
+            // later node in pre-order holds later particles)
+            if (HALF && !past && (uint32_t)S.nrg[v - cb].y <= base) {
                 v = skip > v ? skip : v + 1;
                 continue;
             }
@@ -484,6 +487,7 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(SearchArgs a, SearchCt
             }
             // leaf: queue its j-clusters not queued yet (leaves can share one)
             const int2 rg = S.nrg[v - cb];
+            past = true;
             int Jlo = max(rg.x / MJ, lastJ + 1);
             const int Jhi = (rg.y - 1) / MJ;
             ++lvis;
