@@ -45,9 +45,11 @@ __device__ __forceinline__ float spline_w_inside(float q)
     return q < 1.f ? inner : outer;
 }
 
-// spline_w_inside of two arguments at once (packed products; inner part as
-// 1 - 0.75 q^2 (2 - q), the same polynomial in its own rounding order)
-__device__ __forceinline__ void spline_w_inside_x2(f32x2 q, float &w0, float &w1)
+// 4 w(q) of two arguments q < 2 at once (packed products; inner part as
+// 4 - 3 q^2 (2 - q), outer (2 - q)^3): four times the spline shape, exactly
+// (scaling by 4 commutes with rounding), so sums of m 4w are exactly four
+// times the sums of m w and the caller scales by 1/4 once at the end
+__device__ __forceinline__ void spline_w4_inside_x2(f32x2 q, float &w0, float &w1)
 {
     const f32x2 a = sub2_rn(pk2(2.f, 2.f), q);  // 2 - q
     const f32x2 t = mul2_rn(mul2_rn(q, q), a);
@@ -56,8 +58,8 @@ __device__ __forceinline__ void spline_w_inside_x2(f32x2 q, float &w0, float &w1
     unpk2(q, q0, q1);
     unpk2(t, t0, t1);
     unpk2(a3, o0, o1);
-    w0 = q0 < 1.f ? fmaf(-0.75f, t0, 1.f) : 0.25f * o0;
-    w1 = q1 < 1.f ? fmaf(-0.75f, t1, 1.f) : 0.25f * o1;
+    w0 = q0 < 1.f ? fmaf(-3.f, t0, 4.f) : o0;
+    w1 = q1 < 1.f ? fmaf(-3.f, t1, 4.f) : o1;
 }
 
 // cubic spline shape w(q) (support q < 2) and its derivative
@@ -271,7 +273,13 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
     float *shv = reinterpret_cast<float *>(shm);
     float4 *sxv = reinterpret_cast<float4 *>(shm);  // force passes: (1/h, c_i, r_i, m_i)
     // fixed-point scale of the half-list density (2^ex)
-    const float hscale = (HL && KIND == PASS_DENSITY) ? __int_as_float((half_scale_exp(a.st->m_absmax) + 127) << 23) : 0.f;
+    // density sums taken in units of 4 w (the packed spline; WSC = 4) or w
+    constexpr bool W4 = (HL && KIND == PASS_DENSITY) || (!HL && !PER && KIND == PASS_DENSITY && NP == 2);
+    constexpr float WSC = W4 ? 4.f : 1.f;
+    // fixed-point scale of the half-list density (2^ex), per unit of the sums
+    const float hscale = (HL && KIND == PASS_DENSITY)
+                             ? __int_as_float((half_scale_exp(a.st->m_absmax) + 127) << 23) / WSC
+                             : 0.f;
     const unsigned lane = lane_id();
     const uint32_t II = lane % M;
     const uint32_t JJ0 = (lane / M) % MJ;
@@ -422,7 +430,7 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                         const float r = sqrt_approx(e2);
                         // both sides' kernel values in one packed evaluation
                         float wi, wj;
-                        spline_w_inside_x2(mul2_rn(pk2(r, r), pk2(hik, aj.y)), wi, wj);
+                        spline_w4_inside_x2(mul2_rn(pk2(r, r), pk2(hik, aj.y)), wi, wj);
                         if (ini) acc.b[k] += aj.x * wi;
                         if (inj) jsh[tt] += mik * wj;
                     }
@@ -573,7 +581,7 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                             const bool ina = owner && d2a < pik.w, inb = owner && d2b < pik.w;  // i = j included
                             if (ina || inb) {
                                 float wa, wb;
-                                spline_w_inside_x2(mul2_rn(pk2(sqrt_approx(d2a), sqrt_approx(d2b)), pk2(hm.x, hm.x)),
+                                spline_w4_inside_x2(mul2_rn(pk2(sqrt_approx(d2a), sqrt_approx(d2b)), pk2(hm.x, hm.x)),
                                                    wa, wb);
                                 if (ina) acc.b[k] += aj[0].x * wa;
                                 if (inb) acc.b[k] += aj[1].x * wb;
@@ -704,7 +712,7 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
             // nonzero (d2 = 0 < r^2)
             const bool took_self = ((selfseen >> k) & 1u) && (ISM ? sip[k * M + II].w : ri2[k]) > 0.f;
             if constexpr (HL && KIND == PASS_DENSITY) {
-                const float self = took_self ? 0.f : a.aux[i].x;  // m_i w(0) = m_i
+                const float self = took_self ? 0.f : WSC * a.aux[i].x;  // m_i w(0) = m_i
                 atomicAdd(&a.hsum[i], fixed_of((acc.v[k] + self) * hscale));
             } else if constexpr (HL && KIND == PASS_COUNT) {
                 atomicAdd(&a.hcnt[i], acc.v[k] - (took_self ? 1u : 0u));
@@ -713,9 +721,9 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                 atomicAdd(&a.hf[3 * (size_t)i + 1], f64_of(acc.y[k]));
                 atomicAdd(&a.hf[3 * (size_t)i + 2], f64_of(acc.z[k]));
             } else if constexpr (KIND == PASS_DENSITY) {
-                const float self = took_self ? 0.f : a.aux[i].x;  // m_i w(0) = m_i
+                const float self = took_self ? 0.f : WSC * a.aux[i].x;  // m_i w(0) = m_i
                 const float hk = ISM ? own_hm(k).x : hinv[k];
-                a.out0[o] = (acc.v[k] + self) * (0.318309886183790672f * hk * hk * hk);
+                a.out0[o] = (acc.v[k] + self) * (1.f / WSC) * (0.318309886183790672f * hk * hk * hk);
             } else if constexpr (KIND == PASS_COUNT) {
                 a.outc[o] = acc.v[k] - (took_self ? 1u : 0u);
             } else if constexpr (HL && KIND == PASS_MIN) {
