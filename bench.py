@@ -35,11 +35,12 @@ ALU_OPS_PER_DENSITY_SIDE = 12    # gather pair in range: square root, scale, spl
 ALGO_BYTES_PER_PARTICLE = 145    # keygen 20 + sort 24 + permute 49 + octree 2 + search 19 + density 31
 # DRAM bytes (read + write) of one k_search launch per particle, from an ncu
 # capture on this generator at 2^21 particles (8x8 clusters, leaf bucket 256,
-# half list: packed tile and node tests), 44.9 MB + 0.9 MB, scaled by the
+# half list: packed tile and node tests, the range test of the half search
+# ending at the first accepted leaf), 44.87 MB + 1.13 MB, scaled by the
 # particle count (the traffic grows with the particles).  Valid for that kernel
 # version only; a list kind without a capture of the current kernel reports no
 # traffic.
-SEARCH_DRAM_BYTES_PER_PARTICLE = {"half": 45.8e6 / 2097152}
+SEARCH_DRAM_BYTES_PER_PARTICLE = {"half": 46.0e6 / 2097152}
 
 
 def peaks():
