@@ -229,6 +229,18 @@ __device__ __forceinline__ unsigned long long fixed_of(float x)
     return (b >> 31) ? (0ull - q) : q;
 }
 
+// The same for 0 <= x < 2^63 in two 32-bit conversions: hi = floor(x / 2^32)
+// (exact: x / 2^32 is a float), then the remainder x - hi 2^32, exact in
+// FP32 (below 2^32 it is x itself; above, a multiple of ulp(x) >= 2^9 below
+// 2^32), rounded to the nearest integer (ties to even; a remainder of x >=
+// 2^32 is already an integer)
+__device__ __forceinline__ unsigned long long fixed_of_nonneg(float x)
+{
+    const uint32_t hi = __float2uint_rz(__fmul_rn(x, 0x1p-32f));
+    const uint32_t lo = __float2uint_rn(__fmaf_rn(-__uint2float_rn(hi), 0x1p32f, x));
+    return ((unsigned long long)hi << 32) | lo;
+}
+
 // The FP64 value of x with integer operations only (exact for normal x;
 // zero and subnormals, below 1.2e-38, give 0; inf and NaN stay so).
 __device__ __forceinline__ double f64_of(float x)
@@ -621,8 +633,11 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                                       __shfl_xor_sync(0xffffffffu, odd ? jsh[0] : jsh[1], 1);
 #pragma unroll
                             for (int o = 2; o < M; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                            if (II < 2u && v != 0.f)
-                                atomicAdd(&a.hsum[Je * MJ + JJ0 + II * JSTEP], fixed_of(v * hscale));
+                            // a share is a sum of m 4w >= 0 (up to a rounding of
+                            // the square root at the edge of the support, where
+                            // w is below 1e-20: clamped to 0)
+                            if (II < 2u && v > 0.f)
+                                atomicAdd(&a.hsum[Je * MJ + JJ0 + II * JSTEP], fixed_of_nonneg(v * hscale));
                         } else {
                             uint32_t v = (odd ? jcn[1] : jcn[0]) +
                                          __shfl_xor_sync(0xffffffffu, odd ? jcn[0] : jcn[1], 1);
