@@ -197,7 +197,8 @@ constexpr size_t pass_smem_per_warp()
     return (size_t)pass_stage_entries<KIND, HL>() * MJ *
                (sizeof(float4) + ((KIND == PASS_DENSITY || KIND == PASS_SPH || KIND == PASS_LJC) ? sizeof(float2) : 0)) +
            (HL ? (size_t)kSC * MJ * sizeof(float) : 0) +
-           (pass_i_in_smem<KIND, HL>() ? (size_t)kSC * M * (sizeof(float4) + pass_own_extra_bytes<KIND, HL>()) : 0);
+           (pass_i_in_smem<KIND, HL>() ? (size_t)kSC * M * (sizeof(float4) + pass_own_extra_bytes<KIND, HL>()) : 0) +
+           (KIND == PASS_DENSITY ? (size_t)2 * kSC * 32 * sizeof(float) : 0);
 }
 
 // Resident blocks per SM the register budget is cut for (measured at the
@@ -284,6 +285,11 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
     float2 *shm = reinterpret_cast<float2 *>(sip + (ISM ? kSC * M : 0));
     float *shv = reinterpret_cast<float *>(shm);
     float4 *sxv = reinterpret_cast<float4 *>(shm);  // force passes: (1/h, c_i, r_i, m_i)
+    // density: the running Kahan sums (v, c) of the 8 i-clusters, lane-minor,
+    // updated once per block of 32 entries and kept out of the registers
+    float *skv = reinterpret_cast<float *>(pass_smem + (threadIdx.x >> 5) * pass_smem_per_warp<M, MJ, KIND, HL>() +
+                                           pass_smem_per_warp<M, MJ, KIND, HL>() -
+                                           (KIND == PASS_DENSITY ? 2 * kSC * 32 * sizeof(float) : 0));
     // fixed-point scale of the half-list density (2^ex)
     // density sums taken in units of 4 w (the packed spline; WSC = 4) or w
     constexpr bool W4 = (HL && KIND == PASS_DENSITY) || (!HL && !PER && KIND == PASS_DENSITY && NP == 2);
@@ -352,7 +358,8 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
 #pragma unroll
         for (int k = 0; k < kSC; ++k) {
             if constexpr (KIND == PASS_DENSITY) {
-                acc.v[k] = 0.f; acc.c[k] = 0.f;
+                skv[k * 32 + lane] = 0.f;
+                skv[(kSC + k) * 32 + lane] = 0.f;
             } else if constexpr (KIND == PASS_COUNT) {
                 acc.v[k] = 0;
             } else if constexpr (KIND == PASS_MIN) {
@@ -691,7 +698,26 @@ __global__ void __launch_bounds__(PS_THREADS, (ps_min_blocks<KIND, HL>())) k_pas
                     }
                 }
             }
-            acc_end_block<KIND>(acc);
+            if constexpr (KIND == PASS_DENSITY) {
+                // the block partial into the running sum, Kahan-compensated
+#pragma unroll
+                for (int k = 0; k < kSC; ++k) {
+                    const float v = skv[k * 32 + lane], c = skv[(kSC + k) * 32 + lane];
+                    const float y = __fsub_rn(acc.b[k], c);
+                    const float t = __fadd_rn(v, y);
+                    skv[(kSC + k) * 32 + lane] = __fsub_rn(__fsub_rn(t, v), y);
+                    skv[k * 32 + lane] = t;
+                }
+            } else {
+                acc_end_block<KIND>(acc);
+            }
+        }
+        if constexpr (KIND == PASS_DENSITY) {
+#pragma unroll
+            for (int k = 0; k < kSC; ++k) {
+                acc.v[k] = skv[k * 32 + lane];
+                acc.c[k] = skv[(kSC + k) * 32 + lane];
+            }
         }
 
         // combine lanes holding the same i particle, write in caller order
