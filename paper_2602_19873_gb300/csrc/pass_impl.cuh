@@ -11,8 +11,9 @@
 // (J, mask) entry the lanes hold one i particle of each of the 8 i-clusters
 // (lane % M) and 1..8 of the MJ particles of j-cluster J, and accumulate per
 // i-cluster in registers; masked-off i-clusters cost nothing (warp-uniform
-// branches).  The j particles of 32 entries are staged in shared memory.
-// The self pair is excluded on the fly by index (Sec. II-A).
+// branches).  The j particles of 16 or 32 entries are staged in shared memory
+// (16 where the super-cluster's own particles sit there too).  The self pair
+// is excluded on the fly by index (Sec. II-A).
 #pragma once
 #include "nl_internal.cuh"
 
@@ -118,7 +119,10 @@ __device__ __forceinline__ uint32_t decode_block(const uint32_t *body, int compr
 // block of 32 list entries go to a plain FP32 partial (b*), and each
 // partial is added to the running sum with Kahan compensation (density)
 // or plainly (forces), so the rounding error stays near that of ~32*NP
-// terms however long the neighbor list is.
+// terms however long the neighbor list is.  The density pass keeps its
+// running sums and compensations (v, c) in shared memory instead (they are
+// touched once per block), which frees their registers; v and c here serve
+// only the final combination across lanes.
 template <int KIND>
 struct Acc;
 template <>
